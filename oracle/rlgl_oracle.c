@@ -1,0 +1,351 @@
+/*
+ * RLGL oracle -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, slow, obviously-correct FP64 CPU restatement of the Red Light
+ * Green Light method (Avrachenkov, Brown, Litvak, "Red Light Green Light
+ * Method for Solving Large Markov Chains", J. Sci. Comput. 93:18, 2022).
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load it. It shares no code with the CUDA library.
+ *
+ * Notation follows Sec. 2.1: cash C_t, history H_t, moved cash M_t, green
+ * set G_t, transition matrix P = (p_ij) given by its out-links (CSR).
+ *
+ * Parity pins (see tests/test_oracle_pins.py): Example 3 and the two tables
+ * of Example 9 (Sec. 3.3), power-iteration equivalence (Sec. 2.3.1), the
+ * cash-balance invariant (Eq. recursion_H_res), the two-block mean-field
+ * contraction factors (Eqs. CG1, CG2), the three-block divergence (Theorem
+ * 12), GTH against brute-force solves, closed forms d_i / sum d and 1/N.
+ * Every function below is pinned by at least one of them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { SCHED_ALL_GREEN = 0, SCHED_THRESHOLD = 1, SCHED_TOPFRAC = 2, SCHED_MASK = 3 };
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOTSTOCHASTIC = 2, OR_EDEGENERATE = 5, OR_ENOCONV = 6 };
+
+/*
+ * Transition probabilities from raw weights (Sec. 2.1: P is row-stochastic).
+ * p_e = w_e / sum of w over row i (sum in CSR order), or 1/deg_i when w is
+ * NULL, so that a repeated edge i->j carries multiplicity/deg_i in total.
+ * Returns OR_ENOTSTOCHASTIC for an empty row or a non-positive weight.
+ */
+int oracle_transition_probs(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const float* w, double* p) {
+    (void)col;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t b = row_ptr[i], e = row_ptr[i + 1];
+        if (e <= b) return OR_ENOTSTOCHASTIC;
+        if (w) {
+            double s = 0.0;
+            for (int64_t k = b; k < e; ++k) {
+                if (!(w[k] > 0.0f) || !isfinite(w[k])) return OR_ENOTSTOCHASTIC;
+                s += (double)w[k];
+            }
+            for (int64_t k = b; k < e; ++k) p[k] = (double)w[k] / s;
+        } else {
+            double d = (double)(e - b);
+            for (int64_t k = b; k < e; ++k) p[k] = 1.0 / d;
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * The update of Eqs. recursion_H and recursion_C for a given moved-cash
+ * vector M:  C <- C - M + M P,  H <- H + M.  First every mover's cash M_i
+ * leaves it, then it is routed to its out-neighbours in proportion to p_ij
+ * (rows in increasing i, each row in CSR order), then the history grows.
+ */
+static void apply_moved_cash(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                             const double* p, const double* M, double* C, double* H) {
+    for (int64_t i = 0; i < n; ++i) C[i] -= M[i];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) C[col[k]] += M[i] * p[k];
+    for (int64_t i = 0; i < n; ++i) H[i] += M[i];
+}
+
+/*
+ * One synchronous RLGL move for a given green set (Eq. recursion_M:
+ * M_t = C_t I(G_t), i.e. M_i = C_i for i in G and 0 otherwise; then
+ * apply_moved_cash). What a green node sends is its cash at the start of
+ * the step. stats (nullable) receives {|G|, sum_{i in G} deg_i, sum |M_i|}.
+ */
+void oracle_move(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* p,
+                 const uint8_t* green, double* C, double* H, double* stats) {
+    double* M = (double*)calloc((size_t)n, sizeof(double));
+    double cnt = 0.0, edges = 0.0, mabs = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (green[i]) {
+            M[i] = C[i];
+            cnt += 1.0;
+            edges += (double)(row_ptr[i + 1] - row_ptr[i]);
+            mabs += fabs(M[i]);
+        }
+    apply_moved_cash(n, row_ptr, col, p, M, C, H);
+    free(M);
+    if (stats) {
+        stats[0] = cnt;
+        stats[1] = edges;
+        stats[2] = mabs;
+    }
+}
+
+/*
+ * Step 0 (Eq. init; Alg. 1 lines (1)-(3)): C_0 = 0, H_0 = 0, G_0 = [N] and
+ * the moved cash is the given distribution M_0 (uniform 1/N when m0 is
+ * NULL), not C_0. Afterwards H = H_1 = M_0 and C = C_1 = -M_0 (I - P).
+ */
+void oracle_initial_step(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const double* p, const double* m0, double* C, double* H) {
+    double* M = (double*)malloc((size_t)n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        M[i] = m0 ? m0[i] : 1.0 / (double)n;
+        C[i] = 0.0;
+        H[i] = 0.0;
+    }
+    apply_moved_cash(n, row_ptr, col, p, M, C, H);
+    free(M);
+}
+
+static int cmp_desc(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x < y) - (x > y);
+}
+
+/*
+ * Green-light schedules (Sec. 6, cash-dependent heuristics), in the
+ * synchronous data-parallel form:
+ *   ALL_GREEN : G = [N]                           (power iteration, Sec. 2.3.1)
+ *   THRESHOLD : G = {i : |C_i| >= theta, C_i != 0}, with
+ *               theta = scale * (sum_j |C_j|^r / N)^(1/r) from this same C
+ *               (the threshold theta_t(r) of RLGL_Theta), or theta = the
+ *               given absolute value when abs_theta > 0;
+ *   TOPFRAC   : k = ceil(f N); theta = the k-th largest |C_i|;
+ *               G = {i : |C_i| >= theta, C_i != 0} (ties all included;
+ *               RLGL_MaxC widened to "large, not necessarily largest");
+ *   MASK      : G = {i : mask_i != 0}.
+ * Zero-cash nodes are left out of the cash-dependent sets; moving zero cash
+ * changes nothing. Writes green[] and returns theta (0 for ALL_GREEN/MASK).
+ */
+double oracle_select(int64_t n, const double* C, int32_t sched, double theta_scale,
+                     int32_t r, double abs_theta, double top_frac, const uint8_t* mask,
+                     uint8_t* green) {
+    double theta = 0.0;
+    if (sched == SCHED_ALL_GREEN) {
+        for (int64_t i = 0; i < n; ++i) green[i] = 1;
+        return 0.0;
+    }
+    if (sched == SCHED_MASK) {
+        for (int64_t i = 0; i < n; ++i) green[i] = mask[i] ? 1 : 0;
+        return 0.0;
+    }
+    if (sched == SCHED_THRESHOLD) {
+        if (abs_theta > 0.0) {
+            theta = abs_theta;
+        } else {
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j) s += (r == 1) ? fabs(C[j]) : pow(fabs(C[j]), (double)r);
+            theta = (r == 1) ? theta_scale * (s / (double)n)
+                             : theta_scale * pow(s / (double)n, 1.0 / (double)r);
+        }
+    } else { /* SCHED_TOPFRAC */
+        int64_t k = (int64_t)ceil(top_frac * (double)n);
+        if (k < 1) k = 1;
+        if (k > n) k = n;
+        double* a = (double*)malloc((size_t)n * sizeof(double));
+        for (int64_t j = 0; j < n; ++j) a[j] = fabs(C[j]);
+        qsort(a, (size_t)n, sizeof(double), cmp_desc);
+        theta = a[k - 1];
+        free(a);
+    }
+    for (int64_t i = 0; i < n; ++i) green[i] = (C[i] != 0.0 && fabs(C[i]) >= theta) ? 1 : 0;
+    return theta;
+}
+
+double oracle_l1(int64_t n, const double* x) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += fabs(x[i]);
+    return s;
+}
+
+double oracle_sum(int64_t n, const double* x) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += x[i];
+    return s;
+}
+
+/*
+ * ||C - C_0 - H (P - I)||_1 : the cash-balance identity H_t + C_t =
+ * H_t P + C_0 (Eq. recursion_H_res). c0 may be NULL (C_0 = 0).
+ */
+double oracle_invariant_residual(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                 const double* p, const double* C, const double* H,
+                                 const double* c0) {
+    double* r = (double*)calloc((size_t)n, sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) r[col[k]] += H[i] * p[k];
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double hp_minus_h = r[j] - H[j];
+        s += fabs(C[j] - (c0 ? c0[j] : 0.0) - hp_minus_h);
+    }
+    free(r);
+    return s;
+}
+
+/*
+ * Algorithm 1. State (C, H) holds C_t, H_t on entry (t >= 1, normally
+ * straight after oracle_initial_step, i.e. t = 1) and on exit.
+ * Loop, for t = 1, 2, ...:
+ *   if |H_t 1| <= 1e-12 sum|H_t|            -> OR_EDEGENERATE (Sec. 2.1: the
+ *                                              estimate is undefined);
+ *   if t >= 2 and ||C_t||_1 / |H_t 1| < tol -> OR_OK   (Alg. 1 line (7));
+ *   if max_steps moves were made           -> OR_ENOCONV;
+ *   choose G_t from C_t; move.
+ * safety_every > 0 makes every safety_every-th move all-green.
+ * mask (MASK schedule) holds `mask_period` green sets of n bytes, used
+ * cyclically. When check != NULL, the per-step invariants are checked and
+ * their worst values stored: check[0] = max |sum C| / (1 + sum|M|),
+ * check[1] = max growth of ||C||_1 relative to (1 + sum|M|) (it never grows,
+ * Theorem 6's proof), check[2] = max invariant residual / sum|H| (every
+ * check_every steps when check_every > 0).
+ * out[0] = moves made, out[1] = ||C||_1/|H 1| at exit, out[2] = edge pushes
+ * (sum over moves of sum_{i in G} deg_i), out[3] = H 1.
+ */
+int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* p,
+                 int32_t sched, double theta_scale, int32_t r, double abs_theta,
+                 double top_frac, const uint8_t* mask, int64_t mask_period,
+                 int64_t safety_every, double tol, int64_t max_steps, double* C, double* H,
+                 int64_t check_every, double* check, double* out) {
+    uint8_t* green = (uint8_t*)malloc((size_t)n);
+    int64_t moves = 0;
+    double pushes = 0.0;
+    int status = OR_ENOCONV;
+    if (check) check[0] = check[1] = check[2] = 0.0;
+    for (int64_t t = 1;; ++t) {
+        double l1 = oracle_l1(n, C), hs = oracle_sum(n, H), habs = oracle_l1(n, H);
+        if (out) { out[1] = (hs != 0.0) ? l1 / fabs(hs) : INFINITY; out[3] = hs; }
+        if (fabs(hs) <= 1e-12 * habs || habs == 0.0) { status = OR_EDEGENERATE; break; }
+        if (t >= 2 && l1 / fabs(hs) < tol) { status = OR_OK; break; }
+        if (moves >= max_steps) { status = OR_ENOCONV; break; }
+        int32_t s = sched;
+        if (safety_every > 0 && (moves + 1) % safety_every == 0) s = SCHED_ALL_GREEN;
+        const uint8_t* mk = (s == SCHED_MASK) ? mask + (size_t)((moves % mask_period) * n) : NULL;
+        oracle_select(n, C, s, theta_scale, r, abs_theta, top_frac, mk, green);
+        double st[3];
+        oracle_move(n, row_ptr, col, p, green, C, H, st);
+        ++moves;
+        pushes += st[1];
+        if (check) {
+            double scale = 1.0 + st[2];
+            double sc = fabs(oracle_sum(n, C)) / scale;
+            double growth = (oracle_l1(n, C) - l1) / scale;
+            if (sc > check[0]) check[0] = sc;
+            if (growth > check[1]) check[1] = growth;
+            if (check_every > 0 && moves % check_every == 0) {
+                double ir = oracle_invariant_residual(n, row_ptr, col, p, C, H, NULL) /
+                            oracle_l1(n, H);
+                if (ir > check[2]) check[2] = ir;
+            }
+        }
+    }
+    if (out) { out[0] = (double)moves; out[2] = pushes; }
+    free(green);
+    return status;
+}
+
+/* Estimate pi_hat = H / (H 1) (Eq. pi_hat). Returns OR_EDEGENERATE when
+ * |H 1| <= 1e-12 sum |H|. */
+int oracle_estimate(int64_t n, const double* H, double* pi) {
+    double hs = oracle_sum(n, H), habs = oracle_l1(n, H);
+    if (fabs(hs) <= 1e-12 * habs || habs == 0.0) return OR_EDEGENERATE;
+    for (int64_t i = 0; i < n; ++i) pi[i] = H[i] / hs;
+    return OR_OK;
+}
+
+/*
+ * Reference stationary law by power iteration, pi_{t+1} = pi_t P (the PI
+ * reference method of Sec. 6), run until ||pi_t - pi_{t+1}||_1 <= tol or
+ * maxit iterations; the reference vector used by the paper to measure errors
+ * is obtained this way. The product is taken in pull form over the
+ * in-links (each output entry is one sum, in a fixed order), so running it
+ * on several threads gives the same bits as on one. pi holds the start
+ * vector on entry (uniform when pi[0] < 0) and the result on exit.
+ * Returns the iterations made; *delta_out = last ||pi_t - pi_{t+1}||_1.
+ */
+int64_t oracle_power_iteration(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                               const double* p, double tol, int64_t maxit, int32_t nthreads,
+                               double* pi, double* delta_out) {
+    int64_t nnz = row_ptr[n];
+    int64_t* t_ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* t_src = (int32_t*)malloc((size_t)nnz * sizeof(int32_t));
+    double* t_p = (double*)malloc((size_t)nnz * sizeof(double));
+    int64_t* cur = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    double* nxt = (double*)malloc((size_t)n * sizeof(double));
+    for (int64_t k = 0; k < nnz; ++k) t_ptr[col[k] + 1]++;
+    for (int64_t j = 0; j < n; ++j) t_ptr[j + 1] += t_ptr[j];
+    memcpy(cur, t_ptr, (size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t q = cur[col[k]]++;
+            t_src[q] = (int32_t)i;
+            t_p[q] = p[k];
+        }
+    if (pi[0] < 0.0)
+        for (int64_t i = 0; i < n; ++i) pi[i] = 1.0 / (double)n;
+    int64_t it = 0;
+    double delta = INFINITY;
+    while (it < maxit) {
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+        for (int64_t j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int64_t q = t_ptr[j]; q < t_ptr[j + 1]; ++q) s += pi[t_src[q]] * t_p[q];
+            nxt[j] = s;
+        }
+        delta = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            delta += fabs(nxt[j] - pi[j]);
+            pi[j] = nxt[j];
+        }
+        ++it;
+        if (delta <= tol) break;
+    }
+    if (delta_out) *delta_out = delta;
+    free(t_ptr); free(t_src); free(t_p); free(cur); free(nxt);
+    return it;
+}
+
+/*
+ * Grassmann-Taksar-Heyman state reduction (the exact method cited in
+ * Sec. 1.1, Grassmann, Taksar, Heyman 1985): Gaussian elimination on the
+ * dense row-stochastic matrix A (n x n, row-major, overwritten) that uses
+ * no subtractions. For k = n-1 .. 1: s = sum_{j<k} a_kj; a_ik /= s (i<k);
+ * a_ij += a_ik a_kj (i,j<k). Back substitution: x_0 = 1,
+ * x_j = sum_{i<j} x_i a_ij; pi = x / sum x.
+ * Returns OR_OK, or OR_EINVAL when some s is 0 (reducible chain).
+ */
+int oracle_gth(int64_t n, double* A, double* pi) {
+    for (int64_t k = n - 1; k >= 1; --k) {
+        double s = 0.0;
+        for (int64_t j = 0; j < k; ++j) s += A[k * n + j];
+        if (!(s > 0.0)) return OR_EINVAL;
+        for (int64_t i = 0; i < k; ++i) A[i * n + k] /= s;
+        for (int64_t i = 0; i < k; ++i) {
+            double aik = A[i * n + k];
+            if (aik == 0.0) continue;
+            for (int64_t j = 0; j < k; ++j) A[i * n + j] += aik * A[k * n + j];
+        }
+    }
+    pi[0] = 1.0;
+    double tot = 1.0;
+    for (int64_t j = 1; j < n; ++j) {
+        double x = 0.0;
+        for (int64_t i = 0; i < j; ++i) x += pi[i] * A[i * n + j];
+        pi[j] = x;
+        tot += x;
+    }
+    for (int64_t j = 0; j < n; ++j) pi[j] /= tot;
+    return OR_OK;
+}
