@@ -1,0 +1,507 @@
+"""Benchmark: time to L1 error 1e-6 and edge-pushes/s of the RLGL green-light
+sweep on one GB300, RLGL threshold schedule vs all-green (power iteration),
+as a fraction of the HBM roofline.
+
+Workload (default): R-MAT scale 20 (N = 2^20 nodes, 16 * 2^20 R-MAT edges,
+a,b,c,d = .57,.19,.19,.05, seeded relabelling, plus the cycle i->i+1 and
+self-loops: nnz = 18,874,368), p_ij = multiplicity / out-degree, column
+indices int32, cash FP32 and history FP64 (MIXED precision). Synthetic,
+seeded inputs stand in for the paper's web graphs.
+
+One bench step = one complete solve of that chain from step 0 to L1 error
+<= 1e-6 against the FP64 oracle's stationary law, with the headline
+schedule (RLGL threshold, theta = mean |C|): step 0, T* moves (T* found by
+an untimed calibration run), the estimate pi_hat = H / (H 1). The chain is
+resident in HBM; L2 (129 MB) is flushed between timed steps by writing a
+512 MB buffer. value = edge-pushes/s (links used by the moves, the paper's
+unit of work); ms_per_step = the time to L1 1e-6.
+
+Oracle leg (host cores, untimed for the GPU numbers): the FP64 oracle's
+power iteration gives the reference stationary law that defines "L1 error";
+a bounded sample of oracle moves gives the CPU baseline.
+
+--impl reference times the FP64 CPU oracle on the same workload and metric.
+With torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the solve of one chain is not sharded); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to L1 err 1e-6 & edge-pushes/s, RLGL sched vs all-green, % HBM peak"
+UNIT = "edge-pushes/s"
+ERR_TARGET = 1e-6
+KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh")
+
+WORKLOADS = {
+    # name: (scale, edge_factor, weighted, precision)
+    "rmat20": dict(scale=20, edge_factor=16, weighted=False, precision="mixed",
+                   desc="R-MAT scale 20 (N=2^20, 16*2^20 R-MAT edges + cycle + self-loops), "
+                        "p=1/outdeg, FP32 cash, FP64 history"),
+    "rmat24": dict(scale=24, edge_factor=16, weighted=True, precision="mixed",
+                   desc="R-MAT scale 24 (N=2^24, 16*2^24 R-MAT edges + cycle + self-loops), "
+                        "weights U(0,1], FP32 cash, FP64 history"),
+    "rmat16": dict(scale=16, edge_factor=16, weighted=False, precision="mixed",
+                   desc="R-MAT scale 16 (small case)"),
+}
+
+
+# ----------------------------------------------------------- distributed
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ workload
+
+def make_workload(name: str, seed: int = 1):
+    from paper_2008_02710_gb300 import synth
+    w = WORKLOADS[name]
+    csr = synth.rmat_chain(w["scale"], w["edge_factor"], seed=seed, weighted=w["weighted"])
+    return csr, w
+
+
+def oracle_reference(csr, tol=1e-11, maxit=50000):
+    """Oracle leg: the FP64 oracle's power iteration (host cores) gives the
+    reference stationary law that defines the L1 error."""
+    import oracle
+    p = oracle.transition_probs(csr)
+    t = time.time()
+    pi, it, delta = oracle.power_iteration(csr, p, tol=tol, maxit=maxit, nthreads=os.cpu_count() or 1)
+    return pi, dict(iterations=it, delta=delta, seconds=time.time() - t, cores=os.cpu_count())
+
+
+def oracle_cpu_sample(csr, budget_s=15.0, min_moves=2):
+    """Oracle leg: the FP64 oracle as it stands (one core), RLGL threshold
+    moves from step 0 for about budget_s seconds; edge-pushes/s."""
+    import oracle
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    moves, pushes, t0 = 0, 0.0, time.time()
+    while moves < min_moves or time.time() - t0 < budget_s:
+        info = oracle.solve(csr, p, C, H, sched=oracle.THRESHOLD, tol=0.0, max_steps=1,
+                            check_every=-1)
+        moves += info["moves"]
+        pushes += info["pushes"]
+        if info["moves"] == 0:
+            break
+    dt = time.time() - t0
+    return dict(value=pushes / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"first {moves} RLGL-threshold moves of the oracle from step 0 on this "
+                       f"workload ({pushes:.3e} edge-pushes in {dt:.1f} s, 1 thread)")
+
+
+# ------------------------------------------------------------------ GPU
+
+class GpuRun:
+    def __init__(self, csr, wl, device):
+        import torch
+        from paper_2008_02710_gb300.rlgl import Chain
+        self.torch = torch
+        self.device = device
+        self.stream = torch.cuda.Stream(device=device)
+        self.csr = csr
+        self.wl = wl
+        self.chain = Chain(csr, precision=wl["precision"], stream=self.stream)
+        self.pi_dev = torch.empty(csr.n, dtype=torch.float64, device=device)
+        self.flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def err(self, ref_dev) -> float:
+        self.chain.estimate(self.pi_dev)
+        with self.torch.cuda.stream(self.stream):
+            e = (self.pi_dev - ref_dev).abs().sum()
+        return float(e.item())
+
+    def calibrate(self, sched, theta, ref_dev, max_moves=20000):
+        """Untimed: the first move count T* with L1 error <= 1e-6."""
+        ch = self.chain
+        ch.reset()
+        traj = []
+        for k in range(1, max_moves + 1):
+            ch.step(sched, theta, info=False)
+            e = self.err(ref_dev)
+            if k <= 3 or k % 25 == 0:
+                traj.append((k, e))
+            if e <= ERR_TARGET:
+                traj.append((k, e))
+                return k, e, traj
+        return None, e, traj
+
+    def flush_l2(self):
+        with self.torch.cuda.stream(self.stream):
+            self.flush_buf.fill_(1.0)
+
+    def timed_solves(self, sched, theta, tstar, steps, warmup):
+        """Each step: step 0, T* moves in one device-side loop, estimate."""
+        torch = self.torch
+        ch = self.chain
+        times, infos = [], []
+        for i in range(warmup + steps):
+            self.flush_l2()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(self.stream)
+            ch.reset()
+            info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
+            ch.estimate(self.pi_dev)
+            ev1.record(self.stream)
+            ev1.synchronize()
+            if i >= warmup:
+                times.append(ev0.elapsed_time(ev1))
+                infos.append(info)
+        return times, infos
+
+    def kernel_profile(self, sched, theta, tstar):
+        """Eager moves with CUDA events around every kernel on the context's
+        stream; returns per-class (ms, launches) and algorithmic bytes."""
+        ch = self.chain
+        csr = self.csr
+        n, nnz = csr.n, csr.nnz
+        cash = 4 if self.wl["precision"] == "mixed" else 8
+        has_w = csr.w is not None
+        ch.reset()
+        ch.profile(2)
+        ch.profile(1)
+        bytes_push = bytes_pull = 0.0
+        npush = npull = 0
+        for _ in range(tstar):
+            info = ch.step(sched, theta, info=True)
+            E, G = info["edges_pushed"], info["green"]
+            if info["mode"] == 1:
+                npush += 1
+                bytes_push += E * (4 + (4 if has_w else 0) + cash) + G * (8 + 8 + cash)
+            elif info["mode"] == 2:
+                npull += 1
+                bytes_pull += nnz * (4 + (4 if has_w else 0) + cash) + n * (8 + 2 * cash)
+        kt = ch.kernel_times()
+        ch.profile(0)
+        # the info=True path adds one stats launch per move: remove it
+        ms_stats, n_stats = kt["stats"]
+        kt["stats"] = (ms_stats * 0.5, n_stats // 2)
+        return kt, dict(push=(bytes_push, npush), pull=(bytes_pull, npull))
+
+    def e2e(self, sched, theta, tstar, steps, warmup):
+        """Through the public API with host buffers: every step uploads the
+        chain from pinned host memory (create), solves, and reads pi back."""
+        torch = self.torch
+        from paper_2008_02710_gb300.rlgl import Chain
+        from paper_2008_02710_gb300 import synth
+        csr = self.csr
+        pinned = synth.CSR(csr.n, torch.from_numpy(csr.row_ptr).pin_memory(),
+                           torch.from_numpy(csr.col).pin_memory(),
+                           None if csr.w is None else torch.from_numpy(csr.w).pin_memory())
+        pi_host = torch.empty(csr.n, dtype=torch.float64).pin_memory()
+        h2d = pinned.row_ptr.numel() * 8 + pinned.col.numel() * 4 + (0 if csr.w is None else csr.nnz * 4)
+        times, pushes = [], []
+        for i in range(warmup + steps):
+            torch.cuda.synchronize(self.device)
+            t0 = time.perf_counter()
+            with Chain(pinned, precision=self.wl["precision"], stream=self.stream) as ch:
+                info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
+                ch.estimate(pi_host)
+            t1 = time.perf_counter()
+            if i >= warmup:
+                times.append(t1 - t0)
+                pushes.append(info["edges_pushed"])
+        return times, pushes, h2d, csr.n * 8
+
+
+def traffic_from_profiles(kernel_cls, workload):
+    """ncu DRAM bytes per launch of the dominant kernel, when a committed
+    summary exists for the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = source_hash()
+    ent = data.get(f"{workload}:{kernel_cls}")
+    if not ent or ent.get("source_sha") != h:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("rlgl.cu", "rlgl_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- main
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist(ws, "nccl")
+    csr, wl = make_workload(args.workload)
+    # oracle leg: reference stationary law (host cores)
+    ref, ref_info = oracle_reference(csr)
+    ref_dev = torch.from_numpy(ref).to(device)
+    g = GpuRun(csr, wl, device)
+    sched_theta = {"threshold": 0.0, "all_green": 0.0, "topfrac": 0.01}
+    cal = {}
+    for s in ("threshold", "all_green", "topfrac"):
+        if s != "threshold" and args.skip_compare:
+            continue
+        tstar, e, traj = g.calibrate(s, sched_theta[s], ref_dev, max_moves=args.max_moves)
+        cal[s] = dict(tstar=tstar, err=e, traj=traj)
+    head = args.sched
+    if cal[head]["tstar"] is None:
+        raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves")
+    tstar = cal[head]["tstar"]
+
+    # kernel profile (eager, CUDA events on the context stream)
+    kt, alg = g.kernel_profile(head, sched_theta[head], tstar)
+
+    # comparison schedules (timed the same way, fewer repetitions)
+    compare = {}
+    for s in ("all_green", "topfrac"):
+        if s in cal and cal[s]["tstar"]:
+            ts, inf = g.timed_solves(s, sched_theta[s], cal[s]["tstar"], max(2, args.steps // 2), 2)
+            compare[s] = dict(tstar=cal[s]["tstar"], ms=float(np.median(ts)),
+                              edges=inf[0]["edges_pushed"], err=cal[s]["err"])
+
+    # timed region: headline schedule
+    clocks = ClockSampler(local)
+    barrier(dist)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    times, infos = g.timed_solves(head, sched_theta[head], tstar, args.steps, args.warmup)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(dist)
+    # final error of the timed run's estimate
+    final_err = float((g.pi_dev - ref_dev).abs().sum().item())
+    total_ms = float(np.sum(times))
+    total_ms_max = max_over_ranks(dist, total_ms, device)
+    pushes = float(sum(i["edges_pushed"] for i in infos))
+    pushes_all = sum_over_ranks(dist, pushes, device)
+    value = pushes_all / (total_ms_max / 1e3)
+    ms_per_step = total_ms_max / args.steps
+    iters = infos[0]["iterations"]
+
+    # e2e through the public API with host buffers
+    et, ep, h2d, d2h = g.e2e(head, sched_theta[head], tstar, max(2, args.steps // 2), 1)
+    e2e_t = max_over_ranks(dist, float(np.sum(et)), device)
+    e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
+
+    # roofline of the dominant kernel class
+    dom = max(("push", "pull"), key=lambda k: kt[k][0])
+    ms_dom, n_dom = kt[dom]
+    bytes_dom, n_alg = alg[dom]
+    peak, peak_src = measured_peaks()
+    achieved = (bytes_dom / max(n_alg, 1)) / ((ms_dom / max(n_dom, 1)) / 1e3) / 1e9 if n_dom else None
+    kernels_per_iter = {"threshold": 4, "all_green": 4, "topfrac": 7}[head] + (3 if wl["precision"] == "mixed" else 0)
+    launches = args.steps * (kernels_per_iter * iters + 1 + 5 + 2)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 cash / f64 history" if wl["precision"] == "mixed" else "f64",
+        "data": "synthetic (seeded R-MAT; stands in for the paper's web graphs)",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
+                   "schedule": head, "precision": wl["precision"], "tstar_moves": tstar,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "time_to_err_ms": {head: ms_per_step, **{k: v["ms"] for k, v in compare.items()}},
+        "moves_to_err": {k: v["tstar"] for k, v in cal.items()},
+        "edge_pushes_to_err": {head: infos[0]["edges_pushed"], **{k: v["edges"] for k, v in compare.items()}},
+        "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step) if "all_green" in compare else None,
+        "final_l1_err": final_err,
+        "reference": {"kind": "oracle power iteration (FP64, host)", **ref_info},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": traffic_from_profiles(dom, args.workload),
+                     "launches": n_dom, "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
+                     "alg_bytes_per_launch": bytes_dom / max(n_alg, 1)},
+        "kernel_ms": {k: v[0] for k, v in kt.items()},
+        "kernel_launches": {k: v[1] for k, v in kt.items()},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * e2e_t / len(et)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_cpu_sample(csr, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on the host cores on the same workload."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    csr, wl = make_workload(args.workload)
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    times, pushes = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        info = oracle.solve(csr, p, C, H, sched=oracle.THRESHOLD, tol=0.0,
+                            max_steps=args.ref_moves, check_every=-1)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            pushes.append(info["pushes"])
+    value = float(np.sum(pushes) / np.sum(times))
+    sample = (f"{args.ref_moves} RLGL-threshold moves of the FP64 oracle per step, continuing "
+              f"from step 0 on this workload, 1 thread")
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
+                   "schedule": "threshold", "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--sched", choices=["threshold", "topfrac", "all_green"], default="threshold")
+    ap.add_argument("--max-moves", type=int, default=20000)
+    ap.add_argument("--skip-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-moves", type=int, default=2)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

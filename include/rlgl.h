@@ -1,0 +1,218 @@
+/*
+ * rlgl.h -- C ABI of librlgl: the data-parallel green-light cash-push sweep
+ * of the Red Light Green Light (RLGL) method on one GPU (sm_103a).
+ *
+ * Method (Avrachenkov, Brown, Litvak, "Red Light Green Light Method for
+ * Solving Large Markov Chains"): for an ergodic chain with row-stochastic
+ * P on [N], find pi* = pi* P, sum pi* = 1 (Sec. 2.1). Every node i holds cash
+ * C_i (any sign, total zero) and history H_i. At each step a set G_t of
+ * nodes gets the green light; each green node adds its cash to its history
+ * and routes it along its out-edges in proportion to p_ij, then its cash is
+ * zero (Eqs. recursion_M, recursion_H, recursion_C; Alg. 1). The estimate is
+ * pi_hat = H / (H 1) (Eq. pi_hat). All-green is power iteration (Sec. 2.3.1).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an rlgl_status. No exception crosses the ABI, and no
+ *    device code traps or asserts; a failing call leaves a message for
+ *    rlgl_last_error(ctx).
+ *  - Pointers marked (memspace) are host pointers when the accompanying
+ *    rlgl_memspace is RLGL_HOST and device pointers (this GPU) when it is
+ *    RLGL_DEVICE. Input arrays are copied into buffers owned by the context;
+ *    the caller keeps ownership of everything it passes and may free it once
+ *    the call returns. Outputs go to caller-allocated buffers.
+ *  - A context owns all its device memory and works on one CUDA stream. Calls
+ *    on one context are not thread-safe; different contexts are independent.
+ *  - Node indices are 0-based; n < 2^27 and nnz < 2^37.
+ */
+#ifndef RLGL_H
+#define RLGL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlgl_ctx rlgl_ctx; /* opaque; owns all its device memory */
+
+typedef enum {
+    RLGL_OK = 0,
+    RLGL_EINVAL = 1,          /* bad argument or malformed CSR */
+    RLGL_ENOTSTOCHASTIC = 2,  /* a row has no out-edge, or a weight is <= 0 or not finite */
+    RLGL_ENOMEM = 3,          /* device or pinned host allocation failed */
+    RLGL_ECUDA = 4,           /* a CUDA runtime call failed (message in rlgl_last_error) */
+    RLGL_EDEGENERATE = 5,     /* |H 1| <= 1e-12 sum|H|: pi_hat undefined (Sec. 2.1, Example 3) */
+    RLGL_ENOCONV = 6,         /* max_steps moves made without reaching tol */
+    RLGL_ETIMEOUT = 7         /* the solve exceeded its wall-clock limit (params.time_limit_s) */
+} rlgl_status;
+
+/* Green-light schedules (Sec. 6 heuristics, synchronous data-parallel form).
+ *  ALL_GREEN : G = [N] (power iteration, Sec. 2.3.1).
+ *  THRESHOLD : G = {i : |C_i| >= theta, C_i != 0} (RLGL_Theta's test). theta
+ *              = the call's theta when > 0, else
+ *              params.theta_scale * (sum_j |C_j|^r / N)^(1/r) from the same C.
+ *  TOPFRAC   : k = ceil(f N) with f = the call's theta when in (0,1], else
+ *              params.top_frac; theta = k-th largest |C_i|, exact;
+ *              G = {i : |C_i| >= theta, C_i != 0} (ties included; RLGL_MaxC
+ *              widened to a fraction).
+ *  MASK      : G = the current set from rlgl_set_masks (cycled).
+ *  LINK_THRESHOLD : the THRESHOLD test applied to the cash per out-link,
+ *              v_i = |C_i| / d_i (d_i = out-degree counting repeats):
+ *              G = {i : v_i >= theta, C_i != 0}, theta = the call's theta when
+ *              > 0, else params.theta_scale * (sum_j v_j^r / N)^(1/r). Moving
+ *              node i costs d_i links, the paper's unit of work (Sec. 6), so v_i
+ *              is the cash moved per link used. */
+typedef enum {
+    RLGL_ALL_GREEN = 0,
+    RLGL_THRESHOLD = 1,
+    RLGL_TOPFRAC = 2,
+    RLGL_MASK = 3,
+    RLGL_LINK_THRESHOLD = 4
+} rlgl_schedule;
+
+/* FP64: cash, moved cash and history in FP64.
+ * MIXED: cash and per-edge products in FP32, history and every reduction in
+ * FP64; the cash is re-derived in FP64 from the history, C = C_0 + H (P - I)
+ * (Eq. recursion_H_res), whenever ||C||_1 has fallen by params.refresh_factor
+ * since the last re-derivation and always before a solve reports
+ * convergence. */
+typedef enum { RLGL_FP64 = 0, RLGL_MIXED = 1 } rlgl_precision;
+
+typedef enum { RLGL_HOST = 0, RLGL_DEVICE = 1 } rlgl_memspace;
+
+typedef struct {
+    double theta_scale;     /* THRESHOLD auto-theta multiplier (default 1) */
+    int32_t r;              /* exponent r of theta_t(r) (default 1) */
+    double top_frac;        /* TOPFRAC fraction when the call's theta is not in (0,1] (default 0.01) */
+    double pull_crossover;  /* a move whose green edges reach this fraction of nnz pulls over
+                               the in-links instead of pushing (default 0.25) */
+    int32_t safety_every;   /* every K-th move of a solve is all-green (0 = never, default) */
+    double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-3; 0 = only at the end) */
+    double time_limit_s;    /* wall-clock limit of one rlgl_solve, checked on the device (default 600) */
+} rlgl_params;
+
+typedef struct {
+    int64_t green;          /* |G_t| */
+    int64_t edges_pushed;   /* sum_{i in G_t} deg_i: links used by the move (Sec. 6) */
+    int32_t mode;           /* 0 none, 1 push over out-links, 2 pull over in-links */
+    double theta;           /* threshold used (THRESHOLD / TOPFRAC), else 0 */
+    double l1_cash;         /* ||C_{t+1}||_1 after the move */
+    double sum_cash;        /* sum C_{t+1} (zero up to rounding) */
+    double sum_hist;        /* H_{t+1} 1 */
+} rlgl_step_info;
+
+typedef struct {
+    int64_t moves;          /* moves made by this call */
+    int64_t edges_pushed;   /* links used by those moves */
+    int64_t green_total;    /* sum of |G_t| */
+    int64_t push_moves, pull_moves, refreshes;
+    int64_t iterations;     /* device-loop iterations (moves + re-derivation-only passes + the final test) */
+    double resid;           /* ||C||_1 / |H 1| at exit (Alg. 1's stopping quantity) */
+    double l1_cash, sum_hist;
+} rlgl_solve_info;
+
+/* Fills p with the defaults listed in rlgl_params. */
+rlgl_status rlgl_default_params(rlgl_params* p);
+
+/*
+ * Creates a context for the chain given by its out-links (CSR), uploads it,
+ * builds the in-link (CSC) copy used by pull moves and residuals, and
+ * performs step 0 (Eq. init; Alg. 1 lines (1)-(3)): H = H_1 = M_0 and
+ * C = C_1 = -M_0 (I - P), total zero.
+ *   n, nnz   : nodes and edges; row i's out-edges are col[row_ptr[i] ..
+ *              row_ptr[i+1]-1].
+ *   row_ptr  : (src) int64 [n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col      : (src) int32 [nnz], 0 <= col < n. Repeated (i, j) pairs add.
+ *   w        : (src) float [nnz] raw positive weights, p_ij = w_ij / sum_k w_ik;
+ *              NULL means unit weights, p_ij = multiplicity / out-degree.
+ *   m0       : (src) double [n], the step-0 distribution M_0; NULL = uniform 1/N.
+ *   prec     : RLGL_FP64 or RLGL_MIXED.
+ *   src      : memspace of row_ptr, col, w, m0.
+ *   stream   : cudaStream_t to work on (NULL: the context creates its own).
+ * Every row needs at least one out-edge (else RLGL_ENOTSTOCHASTIC).
+ */
+rlgl_status rlgl_create(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                        const float* w, const double* m0, rlgl_precision prec,
+                        rlgl_memspace src, void* stream, rlgl_ctx** out);
+
+/*
+ * As rlgl_create, but starts from a given state (c, h) (src memspace, double
+ * [n] each; checkpoint resume) instead of step 0. C_0 := c - h (P - I) is
+ * recorded so that the invariant of Eq. recursion_H_res is checked against
+ * it. Returns RLGL_EINVAL when |sum c| > 1e-12 max(1, ||c||_1).
+ */
+rlgl_status rlgl_create_from_state(int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col, const float* w, const double* c,
+                                   const double* h, rlgl_precision prec, rlgl_memspace src,
+                                   void* stream, rlgl_ctx** out);
+
+/* Step 0 again with a new M_0 (src memspace, double [n]; NULL = uniform),
+ * keeping the uploaded chain. Clears the recorded C_0. */
+rlgl_status rlgl_reset(rlgl_ctx* ctx, const double* m0, rlgl_memspace src);
+
+/* Green sets for RLGL_MASK: `period` sets of n bytes (nonzero = green),
+ * row-major, used cyclically from the first one on. src memspace. */
+rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period,
+                           rlgl_memspace src);
+
+/*
+ * One synchronous move (Alg. 1 lines (6), (2), (3)): choose G_t from the
+ * current cash by the schedule, then C <- C - M_t (I - P), H <- H + M_t with
+ * M_t = C_t I(G_t). theta: see rlgl_schedule. info may be NULL (then the call
+ * does not wait for the GPU); when given, the call synchronises and fills it.
+ */
+rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_step_info* info);
+
+/*
+ * Algorithm 1 until t >= 2 and ||C_t||_1 / |H_t 1| < tol (line (7)), or
+ * max_steps moves (RLGL_ENOCONV), or a degenerate history (RLGL_EDEGENERATE).
+ * The whole loop runs on the device as one CUDA graph with a conditional
+ * while-node: no host round trip per move. tol = 0 with max_steps = T makes
+ * exactly T moves. Synchronises before returning; info may be NULL.
+ * 1 <= max_steps <= 10^8 (else RLGL_EINVAL).
+ */
+rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                       int64_t max_steps, rlgl_solve_info* info);
+
+/* pi_hat = H / (H 1) (Eq. pi_hat), FP64, into pi_out (dst memspace, double
+ * [n]). RLGL_EDEGENERATE when |H 1| <= 1e-12 sum|H| (pi_out untouched). */
+rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst);
+
+/* Current (C_t, H_t) as FP64 (dst memspace; either pointer may be NULL). */
+rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace dst);
+
+/* ||C_t - C_0 - H_t (P - I)||_1 in FP64 (Eq. recursion_H_res): zero up to
+ * rounding on the FP64 path; the accumulated FP32 drift on the MIXED path. */
+rlgl_status rlgl_invariant_residual(rlgl_ctx* ctx, double* l1);
+
+/* Re-derives C = C_0 + H (P - I) in FP64 (rounded to the cash type) and
+ * returns the residual it removed in *l1_before (nullable). */
+rlgl_status rlgl_refresh(rlgl_ctx* ctx, double* l1_before);
+
+rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p);
+rlgl_status rlgl_get_params(const rlgl_ctx* ctx, rlgl_params* p);
+
+/* Per-kernel-class device time (ms) and launch counts accumulated while
+ * profiling is on (rlgl_profile(ctx, 1)): eager moves then record a CUDA
+ * event pair around every kernel on the context's stream. Classes, in order:
+ * 0 stats, 1 select, 2 push, 3 pull, 4 top-k select, 5 refresh.
+ * ms[6], launches[6]. rlgl_profile(ctx, 0) stops and clears nothing;
+ * rlgl_profile(ctx, 2) clears. */
+rlgl_status rlgl_profile(rlgl_ctx* ctx, int32_t mode);
+rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches);
+
+/* The CUDA stream the context works on (cudaStream_t). */
+void* rlgl_stream(const rlgl_ctx* ctx);
+
+/* Last error message of ctx (or of the calling thread when ctx is NULL). */
+const char* rlgl_last_error(const rlgl_ctx* ctx);
+const char* rlgl_status_string(rlgl_status s);
+
+/* Frees the context and all its device memory (NULL is a no-op). */
+void rlgl_destroy(rlgl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLGL_H */

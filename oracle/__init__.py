@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALL_GREEN, THRESHOLD, TOPFRAC, MASK = 0, 1, 2, 3
+ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOTSTOCHASTIC", 5: "EDEGENERATE", 6: "ENOCONV"}
 
 
@@ -52,7 +52,7 @@ def _load():
             L.oracle_initial_step.restype = None
             L.oracle_initial_step.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.oracle_select.restype = dbl
-            L.oracle_select.argtypes = [i64, vp, i32, dbl, i32, dbl, dbl, vp, vp]
+            L.oracle_select.argtypes = [i64, vp, vp, i32, dbl, i32, dbl, dbl, vp, vp]
             L.oracle_l1.restype = dbl
             L.oracle_l1.argtypes = [i64, vp]
             L.oracle_sum.restype = dbl
@@ -101,13 +101,17 @@ def initial_step(csr, p, m0: Optional[np.ndarray] = None):
 
 
 def select(C, sched: int, theta_scale: float = 1.0, r: int = 1, abs_theta: float = 0.0,
-           top_frac: float = 0.01, mask=None):
-    """Green set of the schedule for cash C: returns (green uint8[n], theta)."""
+           top_frac: float = 0.01, mask=None, row_ptr=None):
+    """Green set of the schedule for cash C: returns (green uint8[n], theta).
+    row_ptr (the CSR offsets) is needed by LINK_THRESHOLD only."""
     L = _load()
     C = _f64(C)
     green = np.empty(C.shape[0], dtype=np.uint8)
     mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
-    th = L.oracle_select(C.shape[0], _p(C), sched, theta_scale, r, abs_theta, top_frac,
+    rp = None if row_ptr is None else np.ascontiguousarray(row_ptr, dtype=np.int64)
+    if sched == LINK_THRESHOLD and rp is None:
+        raise ValueError("LINK_THRESHOLD needs row_ptr")
+    th = L.oracle_select(C.shape[0], _p(rp), _p(C), sched, theta_scale, r, abs_theta, top_frac,
                          _p(mk), _p(green))
     return green, th
 

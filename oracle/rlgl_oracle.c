@@ -22,7 +22,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { SCHED_ALL_GREEN = 0, SCHED_THRESHOLD = 1, SCHED_TOPFRAC = 2, SCHED_MASK = 3 };
+enum { SCHED_ALL_GREEN = 0, SCHED_THRESHOLD = 1, SCHED_TOPFRAC = 2, SCHED_MASK = 3,
+       SCHED_LINK_THRESHOLD = 4 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOTSTOCHASTIC = 2, OR_EDEGENERATE = 5, OR_ENOCONV = 6 };
 
 /*
@@ -122,16 +123,27 @@ static int cmp_desc(const void* a, const void* b) {
  *               theta = scale * (sum_j |C_j|^r / N)^(1/r) from this same C
  *               (the threshold theta_t(r) of RLGL_Theta), or theta = the
  *               given absolute value when abs_theta > 0;
+ *   LINK_THRESHOLD : the same test on the cash per out-link, v_i = |C_i| / d_i
+ *               (d_i = out-degree counting repeats): G = {i : v_i >= theta,
+ *               C_i != 0}, theta = scale * (sum_j v_j^r / N)^(1/r) or the given
+ *               value. A move of node i costs d_i links (the cost unit of
+ *               Sec. 6 and Sec. 4.2), so v_i is the cash moved per link used;
  *   TOPFRAC   : k = ceil(f N); theta = the k-th largest |C_i|;
  *               G = {i : |C_i| >= theta, C_i != 0} (ties all included;
  *               RLGL_MaxC widened to "large, not necessarily largest");
  *   MASK      : G = {i : mask_i != 0}.
  * Zero-cash nodes are left out of the cash-dependent sets; moving zero cash
- * changes nothing. Writes green[] and returns theta (0 for ALL_GREEN/MASK).
+ * changes nothing. row_ptr is read only by LINK_THRESHOLD. Writes green[] and
+ * returns theta (0 for ALL_GREEN/MASK).
  */
-double oracle_select(int64_t n, const double* C, int32_t sched, double theta_scale,
-                     int32_t r, double abs_theta, double top_frac, const uint8_t* mask,
-                     uint8_t* green) {
+static double select_value(int32_t sched, const int64_t* row_ptr, const double* C, int64_t i) {
+    if (sched == SCHED_LINK_THRESHOLD) return fabs(C[i]) / (double)(row_ptr[i + 1] - row_ptr[i]);
+    return fabs(C[i]);
+}
+
+double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t sched,
+                     double theta_scale, int32_t r, double abs_theta, double top_frac,
+                     const uint8_t* mask, uint8_t* green) {
     double theta = 0.0;
     if (sched == SCHED_ALL_GREEN) {
         for (int64_t i = 0; i < n; ++i) green[i] = 1;
@@ -141,12 +153,15 @@ double oracle_select(int64_t n, const double* C, int32_t sched, double theta_sca
         for (int64_t i = 0; i < n; ++i) green[i] = mask[i] ? 1 : 0;
         return 0.0;
     }
-    if (sched == SCHED_THRESHOLD) {
+    if (sched == SCHED_THRESHOLD || sched == SCHED_LINK_THRESHOLD) {
         if (abs_theta > 0.0) {
             theta = abs_theta;
         } else {
             double s = 0.0;
-            for (int64_t j = 0; j < n; ++j) s += (r == 1) ? fabs(C[j]) : pow(fabs(C[j]), (double)r);
+            for (int64_t j = 0; j < n; ++j) {
+                double v = select_value(sched, row_ptr, C, j);
+                s += (r == 1) ? v : pow(v, (double)r);
+            }
             theta = (r == 1) ? theta_scale * (s / (double)n)
                              : theta_scale * pow(s / (double)n, 1.0 / (double)r);
         }
@@ -160,7 +175,8 @@ double oracle_select(int64_t n, const double* C, int32_t sched, double theta_sca
         theta = a[k - 1];
         free(a);
     }
-    for (int64_t i = 0; i < n; ++i) green[i] = (C[i] != 0.0 && fabs(C[i]) >= theta) ? 1 : 0;
+    for (int64_t i = 0; i < n; ++i)
+        green[i] = (C[i] != 0.0 && select_value(sched, row_ptr, C, i) >= theta) ? 1 : 0;
     return theta;
 }
 
@@ -233,7 +249,7 @@ int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const do
         int32_t s = sched;
         if (safety_every > 0 && (moves + 1) % safety_every == 0) s = SCHED_ALL_GREEN;
         const uint8_t* mk = (s == SCHED_MASK) ? mask + (size_t)((moves % mask_period) * n) : NULL;
-        oracle_select(n, C, s, theta_scale, r, abs_theta, top_frac, mk, green);
+        oracle_select(n, row_ptr, C, s, theta_scale, r, abs_theta, top_frac, mk, green);
         double st[3];
         oracle_move(n, row_ptr, col, p, green, C, H, st);
         ++moves;

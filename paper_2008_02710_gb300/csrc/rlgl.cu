@@ -1,0 +1,824 @@
+// librlgl: C ABI (include/rlgl.h) over the RLGL sweep kernels.
+//
+// The host side only validates arguments, owns device memory, enqueues
+// kernels on the context's stream and reads results back; every step of a
+// move runs in the kernels of rlgl_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rlgl.h"
+#include "rlgl_kernels.cuh"
+
+using namespace rlgl;
+
+namespace {
+
+thread_local char g_thread_err[512] = "";
+
+enum KClass { KC_STATS = 0, KC_SELECT, KC_PUSH, KC_PULL, KC_TOPK, KC_REFRESH, KC_N };
+
+struct ProfEv {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rlgl_ctx {
+    long long n = 0, nnz = 0;
+    int prec = RLGL_FP64;
+    bool has_w = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, sms = 0;
+    // chain
+    long long* row_ptr = nullptr;
+    int* col = nullptr;
+    float* w = nullptr;
+    double* s = nullptr;
+    int* deg = nullptr;
+    long long* t_ptr = nullptr;
+    int* t_src = nullptr;
+    float* t_w = nullptr;
+    long long* tile_r = nullptr;
+    long long* tile_e = nullptr;
+    long long ntiles = 0;
+    // state and scratch
+    void* c = nullptr;       // cash, float (MIXED) or double (FP64)
+    double* H = nullptr;
+    void* mt = nullptr;      // dense moved cash m~ (cash type)
+    double* y = nullptr;     // residual accumulator, all-zero at rest
+    double* hsrc = nullptr;  // H_i s_i for residual pulls
+    double* c0 = nullptr;    // recorded C_0 (rlgl_create_from_state), else null
+    long long* f_eoff = nullptr;
+    long long* f_base = nullptr;
+    void* f_m = nullptr;
+    int* chunk_row = nullptr;
+    double* part = nullptr;
+    unsigned char* masks = nullptr;
+    long long n_masks = 0;
+    unsigned int* err = nullptr;
+    DevState* st = nullptr;
+    DevState* host_st = nullptr;  // pinned mirror
+    Control* host_ctl = nullptr;  // pinned
+    rlgl_params params{};
+    // launch shapes
+    int grid_nodes = 1, grid_select = 1, grid_push = 1, grid_pull = 1;
+    // solve graphs, one per schedule
+    cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // profiling
+    int profiling = 0;
+    std::vector<ProfEv> prof;
+    double prof_ms[KC_N] = {0};
+    long long prof_n[KC_N] = {0};
+    char err_msg[512] = "";
+};
+
+// ------------------------------------------------------------------ errors
+
+static rlgl_status fail(rlgl_ctx* ctx, rlgl_status s, const char* fmt, ...) {
+    char* buf = ctx ? ctx->err_msg : g_thread_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    if (ctx) snprintf(g_thread_err, sizeof g_thread_err, "%s", ctx->err_msg);
+    return s;
+}
+
+#define CK(ctx, call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? RLGL_ENOMEM : RLGL_ECUDA,   \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKL(ctx) CK(ctx, cudaGetLastError())
+
+#define TRY(expr)                      \
+    do {                               \
+        rlgl_status s_ = (expr);       \
+        if (s_ != RLGL_OK) return s_;  \
+    } while (0)
+
+template <typename P>
+static rlgl_status dalloc(rlgl_ctx* ctx, P** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    CK(ctx, cudaMalloc((void**)p, count * sizeof(P)));
+    return RLGL_OK;
+}
+
+static size_t cash_size(const rlgl_ctx* ctx) {
+    return ctx->prec == RLGL_MIXED ? sizeof(float) : sizeof(double);
+}
+
+// ------------------------------------------------------------- profiling
+
+static rlgl_status prof_begin(rlgl_ctx* ctx, int cls, ProfEv* ev) {
+    if (!ctx->profiling) return RLGL_OK;
+    ev->cls = cls;
+    CK(ctx, cudaEventCreate(&ev->a));
+    CK(ctx, cudaEventCreate(&ev->b));
+    CK(ctx, cudaEventRecord(ev->a, ctx->stream));
+    return RLGL_OK;
+}
+
+static rlgl_status prof_end(rlgl_ctx* ctx, ProfEv* ev) {
+    if (!ctx->profiling) return RLGL_OK;
+    CK(ctx, cudaEventRecord(ev->b, ctx->stream));
+    ctx->prof.push_back(*ev);
+    return RLGL_OK;
+}
+
+static rlgl_status prof_collect(rlgl_ctx* ctx) {
+    if (ctx->prof.empty()) return RLGL_OK;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& e : ctx->prof) {
+        float ms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&ms, e.a, e.b));
+        ctx->prof_ms[e.cls] += ms;
+        ctx->prof_n[e.cls] += 1;
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    ctx->prof.clear();
+    return RLGL_OK;
+}
+
+// ------------------------------------------------------------ enqueueing
+
+// When capturing (graph) no profiling events are recorded.
+struct Launch {
+    rlgl_ctx* ctx;
+    bool capture;
+};
+
+#define LAUNCH(L, cls, kernel_expr)                          \
+    do {                                                     \
+        ProfEv ev_{};                                        \
+        if (!(L).capture) TRY(prof_begin((L).ctx, cls, &ev_)); \
+        kernel_expr;                                         \
+        CKL((L).ctx);                                        \
+        if (!(L).capture) TRY(prof_end((L).ctx, &ev_));       \
+    } while (0)
+
+template <typename T>
+static rlgl_status enqueue_refresh(Launch L) {
+    rlgl_ctx* ctx = L.ctx;
+    const int n = (int)ctx->n;
+    LAUNCH(L, KC_REFRESH,
+           (k_refresh_src<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, ctx->s, n,
+                                                                          ctx->hsrc, ctx->st)));
+    if (ctx->has_w)
+        LAUNCH(L, KC_REFRESH,
+               (k_pull<double, double, true, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+                   ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e,
+                   ctx->ntiles, ctx->st)));
+    else
+        LAUNCH(L, KC_REFRESH,
+               (k_pull<double, double, false, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+                   ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e,
+                   ctx->ntiles, ctx->st)));
+    LAUNCH(L, KC_REFRESH,
+           (k_refresh_apply<T><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+               (T*)ctx->c, ctx->H, ctx->y, ctx->c0, n, ctx->st, ctx->part)));
+    return RLGL_OK;
+}
+
+// One iteration of Alg. 1 on the device: [refresh] stats [top-k] select
+// push pull. Every kernel checks the device state and returns at once when
+// it has nothing to do, so the same sequence serves eager steps and the
+// captured solve loop.
+template <typename T>
+static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long cond, int use_cond) {
+    rlgl_ctx* ctx = L.ctx;
+    const int n = (int)ctx->n;
+    if (ctx->prec == RLGL_MIXED && L.capture) TRY(enqueue_refresh<T>(L));
+    LAUNCH(L, KC_STATS,
+           (k_stats<T><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>((const T*)ctx->c, ctx->deg, n,
+                                                                       ctx->st, ctx->part, cond, use_cond)));
+    if (sched == RLGL_TOPFRAC) {
+        const int bits = KeyOf<T>::bits;
+        for (int hi = bits; hi > 0; hi -= kRadixBits) {
+            int width = hi >= kRadixBits ? kRadixBits : hi;
+            int shift = hi - width;
+            LAUNCH(L, KC_TOPK,
+                   (k_radix_pass<T><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+                       (const T*)ctx->c, n, ctx->st, shift, width)));
+        }
+    }
+    LAUNCH(L, KC_SELECT,
+           (k_select<T><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
+               (T*)ctx->c, ctx->H, ctx->s, ctx->row_ptr, ctx->deg, ctx->masks, n, (T*)ctx->mt, ctx->f_eoff,
+               ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st, ctx->part)));
+    if (ctx->has_w)
+        LAUNCH(L, KC_PUSH,
+               (k_push<T, true><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
+                   ctx->chunk_row, ctx->st)));
+    else
+        LAUNCH(L, KC_PUSH,
+               (k_push<T, false><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
+                   ctx->chunk_row, ctx->st)));
+    if (ctx->has_w)
+        LAUNCH(L, KC_PULL,
+               (k_pull<T, T, true, 0><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, (const T*)ctx->mt, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r,
+                   ctx->tile_e, ctx->ntiles, ctx->st)));
+    else
+        LAUNCH(L, KC_PULL,
+               (k_pull<T, T, false, 0><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, (const T*)ctx->mt, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r,
+                   ctx->tile_e, ctx->ntiles, ctx->st)));
+    return RLGL_OK;
+}
+
+static rlgl_status iteration(rlgl_ctx* ctx, bool capture, int sched, unsigned long long cond,
+                             int use_cond) {
+    Launch L{ctx, capture};
+    if (ctx->prec == RLGL_MIXED) return enqueue_iteration<float>(L, sched, cond, use_cond);
+    return enqueue_iteration<double>(L, sched, cond, use_cond);
+}
+
+static rlgl_status forced_refresh(rlgl_ctx* ctx, bool apply) {
+    k_set_refresh_flags<<<1, 1, 0, ctx->stream>>>(ctx->st, 1, apply ? 1 : 0);
+    CKL(ctx);
+    Launch L{ctx, false};
+    if (ctx->prec == RLGL_MIXED) return enqueue_refresh<float>(L);
+    return enqueue_refresh<double>(L);
+}
+
+static void drop_graphs(rlgl_ctx* ctx) {
+    for (auto& g : ctx->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+static rlgl_status read_state(rlgl_ctx* ctx) {
+    CK(ctx, cudaMemcpyAsync(ctx->host_st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLGL_OK;
+}
+
+static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, double tol,
+                         long long max_steps, int solving) {
+    memset(c, 0, sizeof *c);
+    c->tol = tol;
+    c->theta_arg = theta;
+    c->theta_scale = ctx->params.theta_scale;
+    c->top_frac = ctx->params.top_frac;
+    c->pull_crossover = ctx->params.pull_crossover;
+    c->refresh_factor = ctx->params.refresh_factor;
+    c->time_limit_ns = ctx->params.time_limit_s * 1e9;
+    c->max_steps = max_steps;
+    c->max_iters = 2 * max_steps + 16;
+    c->nnz = ctx->nnz;
+    c->sched = sched;
+    c->r = ctx->params.r;
+    c->safety_every = solving ? ctx->params.safety_every : 0;
+    c->solving = solving;
+    c->mixed = ctx->prec == RLGL_MIXED;
+    c->n_masks = (int)(ctx->n_masks > 0 ? ctx->n_masks : 1);
+}
+
+__global__ void k_begin(DevState* st) {
+    st->done = 0;
+    st->status = 0;
+    st->iters = 0;
+    st->solve_moves = 0;
+    st->skip_move = 0;
+    st->mode = 0;
+    st->want_refresh = 0;
+    st->force_refresh = 0;
+    st->apply_refresh = 0;
+    st->green = 0;
+    st->edges = 0;
+}
+
+static rlgl_status begin(rlgl_ctx* ctx, int sched, double theta, double tol, long long max_steps,
+                         int solving) {
+    fill_control(ctx, ctx->host_ctl, sched, theta, tol, max_steps, solving);
+    CK(ctx, cudaMemcpyAsync(&ctx->st->ctl, ctx->host_ctl, sizeof(Control), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    k_begin<<<1, 1, 0, ctx->stream>>>(ctx->st);
+    CKL(ctx);
+    return RLGL_OK;
+}
+
+// --------------------------------------------------------------- create
+
+static rlgl_status upload(rlgl_ctx* ctx, void* dst, const void* src, size_t bytes, rlgl_memspace sp) {
+    if (bytes == 0) return RLGL_OK;
+    CK(ctx, cudaMemcpyAsync(dst, src, bytes,
+                            sp == RLGL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            ctx->stream));
+    return RLGL_OK;
+}
+
+static int grid_for(long long work, int per_block, int cap) {
+    long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// Exclusive prefix sum in place over x[0..m) (x[m-1] then holds the total of
+// the first m-1 inputs); used on counts laid out as cnt[j + 1].
+static rlgl_status device_inclusive_scan(rlgl_ctx* ctx, long long* x, long long m) {
+    long long nb = (m + kNodesPerIter - 1) / kNodesPerIter;
+    long long* tot = nullptr;
+    TRY(dalloc(ctx, &tot, (size_t)nb));
+    k_scan_blocks<<<(unsigned)nb, kThreads, 0, ctx->stream>>>(x, m, tot);
+    CKL(ctx);
+    k_scan_tot<<<1, kThreads, 0, ctx->stream>>>(tot, nb);
+    CKL(ctx);
+    k_scan_add<<<(unsigned)nb, kThreads, 0, ctx->stream>>>(x, m, tot);
+    CKL(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(tot);
+    return RLGL_OK;
+}
+
+static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) {
+    const long long n = ctx->n;
+    if (m0) {
+        TRY(upload(ctx, ctx->H, m0, (size_t)n * sizeof(double), sp));
+    } else {
+        std::vector<double> u((size_t)n, 1.0 / (double)n);
+        CK(ctx, cudaMemcpyAsync(ctx->H, u.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    // C = 0 then C = C_0 + H (P - I) with H = M_0 and no recorded C_0: the
+    // result of step 0, C_1 = -M_0 (I - P).
+    if (ctx->c0) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->c0);
+        ctx->c0 = nullptr;
+        drop_graphs(ctx);  // captured launches hold the C_0 pointer
+    }
+    CK(ctx, cudaMemsetAsync(ctx->c, 0, (size_t)n * cash_size(ctx), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream));
+    TRY(forced_refresh(ctx, true));
+    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
+    CKL(ctx);
+    TRY(read_state(ctx));
+    return RLGL_OK;
+}
+
+static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                                 const float* w, rlgl_precision prec, rlgl_memspace src,
+                                 void* stream, rlgl_ctx** out) {
+    if (!out) return fail(nullptr, RLGL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (1ll << kCountBits)) return fail(nullptr, RLGL_EINVAL, "n=%lld out of range [1, 2^27)", (long long)n);
+    if (nnz < 1 || nnz >= (1ll << 37)) return fail(nullptr, RLGL_EINVAL, "nnz=%lld out of range", (long long)nnz);
+    if (!row_ptr || !col) return fail(nullptr, RLGL_EINVAL, "row_ptr/col is NULL");
+    if (prec != RLGL_FP64 && prec != RLGL_MIXED) return fail(nullptr, RLGL_EINVAL, "bad precision");
+    if (src != RLGL_HOST && src != RLGL_DEVICE) return fail(nullptr, RLGL_EINVAL, "bad memspace");
+    rlgl_ctx* ctx = new (std::nothrow) rlgl_ctx();
+    if (!ctx) return fail(nullptr, RLGL_ENOMEM, "host allocation failed");
+    *out = ctx;  // freed by the caller wrapper on failure
+    ctx->n = n;
+    ctx->nnz = nnz;
+    ctx->prec = prec;
+    ctx->has_w = (w != nullptr);
+    rlgl_default_params(&ctx->params);
+    CK(ctx, cudaGetDevice(&ctx->device));
+    CK(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        CK(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    const int cap = ctx->sms * 8 < kMaxGrid ? ctx->sms * 8 : kMaxGrid;
+    ctx->grid_nodes = grid_for(n, kThreads, cap);
+    ctx->grid_select = grid_for(n, kNodesPerIter, cap);
+    ctx->grid_push = ctx->sms * 4;
+    ctx->grid_pull = ctx->sms * 8;
+    const size_t cs = cash_size(ctx);
+
+    TRY(dalloc(ctx, &ctx->row_ptr, (size_t)n + 1));
+    TRY(dalloc(ctx, &ctx->col, (size_t)nnz));
+    if (ctx->has_w) TRY(dalloc(ctx, &ctx->w, (size_t)nnz));
+    TRY(dalloc(ctx, &ctx->s, (size_t)n));
+    TRY(dalloc(ctx, &ctx->deg, (size_t)n));
+    TRY(dalloc(ctx, &ctx->t_ptr, (size_t)n + 1));
+    TRY(dalloc(ctx, &ctx->t_src, (size_t)nnz));
+    if (ctx->has_w) TRY(dalloc(ctx, &ctx->t_w, (size_t)nnz));
+    ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;
+    TRY(dalloc(ctx, &ctx->tile_r, (size_t)ctx->ntiles + 1));
+    TRY(dalloc(ctx, &ctx->tile_e, (size_t)ctx->ntiles + 1));
+    CK(ctx, cudaMalloc(&ctx->c, (size_t)n * cs));
+    TRY(dalloc(ctx, &ctx->H, (size_t)n));
+    CK(ctx, cudaMalloc(&ctx->mt, (size_t)n * cs));
+    TRY(dalloc(ctx, &ctx->y, (size_t)n));
+    TRY(dalloc(ctx, &ctx->hsrc, (size_t)n));
+    TRY(dalloc(ctx, &ctx->f_eoff, (size_t)n));
+    TRY(dalloc(ctx, &ctx->f_base, (size_t)n));
+    CK(ctx, cudaMalloc(&ctx->f_m, (size_t)n * cs));
+    TRY(dalloc(ctx, &ctx->chunk_row, (size_t)(nnz / kPushChunk + 2)));
+    TRY(dalloc(ctx, &ctx->part, (size_t)(4 * kMaxGrid + 8)));
+    TRY(dalloc(ctx, &ctx->err, 1));
+    TRY(dalloc(ctx, &ctx->st, 1));
+    CK(ctx, cudaMallocHost((void**)&ctx->host_st, sizeof(DevState)));
+    CK(ctx, cudaMallocHost((void**)&ctx->host_ctl, sizeof(Control)));
+    CK(ctx, cudaMemsetAsync(ctx->y, 0, (size_t)n * sizeof(double), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(unsigned int), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream));
+
+    TRY(upload(ctx, ctx->row_ptr, row_ptr, ((size_t)n + 1) * sizeof(long long), src));
+    TRY(upload(ctx, ctx->col, col, (size_t)nnz * sizeof(int), src));
+    if (ctx->has_w) TRY(upload(ctx, ctx->w, w, (size_t)nnz * sizeof(float), src));
+
+    const int gv = grid_for(nnz, kThreads, ctx->sms * 16);
+    k_validate<<<gv, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->col, ctx->w, n, nnz, ctx->err);
+    CKL(ctx);
+    unsigned int err = 0;
+    CK(ctx, cudaMemcpyAsync(&err, ctx->err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (err & 1u) return fail(ctx, RLGL_EINVAL, "row_ptr is not a valid CSR offset array");
+    if (err & 4u) return fail(ctx, RLGL_EINVAL, "a column index is outside [0, n)");
+    if (err & 2u) return fail(ctx, RLGL_ENOTSTOCHASTIC, "a row has no out-edge (P must be stochastic)");
+    if (err & 8u) return fail(ctx, RLGL_ENOTSTOCHASTIC, "a weight is not positive and finite");
+
+    const int gn = grid_for(n, kThreads, ctx->sms * 16);
+    const int gw = grid_for(n * 32, kThreads, ctx->sms * 16);
+    k_row_scale<<<gn, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->w, n, ctx->s, ctx->deg);
+    CKL(ctx);
+    // In-link (CSC) copy: counts, scan, scatter.
+    long long* cursor = nullptr;
+    TRY(dalloc(ctx, &cursor, (size_t)n + 1));
+    CK(ctx, cudaMemsetAsync(ctx->t_ptr, 0, ((size_t)n + 1) * sizeof(long long), ctx->stream));
+    k_count_in<<<gv, kThreads, 0, ctx->stream>>>(ctx->col, nnz, ctx->t_ptr);
+    CKL(ctx);
+    rlgl_status sc = device_inclusive_scan(ctx, ctx->t_ptr, n + 1);
+    if (sc != RLGL_OK) { cudaFree(cursor); return sc; }
+    CK(ctx, cudaMemcpyAsync(cursor, ctx->t_ptr, ((size_t)n + 1) * sizeof(long long),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    k_scatter_in<<<gw, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->col, ctx->w, n, cursor,
+                                                    ctx->t_src, ctx->t_w);
+    CKL(ctx);
+    const int gt = grid_for(ctx->ntiles + 1, kThreads, ctx->sms * 16);
+    k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
+                                                      ctx->tile_e);
+    CKL(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(cursor);
+    return RLGL_OK;
+}
+
+extern "C" {
+
+rlgl_status rlgl_default_params(rlgl_params* p) {
+    if (!p) return RLGL_EINVAL;
+    p->theta_scale = 1.0;
+    p->r = 1;
+    p->top_frac = 0.01;
+    p->pull_crossover = 0.25;
+    p->safety_every = 0;
+    p->refresh_factor = 1e-3;
+    p->time_limit_s = 600.0;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_create(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                        const float* w, const double* m0, rlgl_precision prec, rlgl_memspace src,
+                        void* stream, rlgl_ctx** out) {
+    rlgl_ctx* ctx = nullptr;
+    rlgl_status s = create_common(n, nnz, row_ptr, col, w, prec, src, stream, &ctx);
+    if (s == RLGL_OK) s = set_step0(ctx, m0, src);
+    if (s != RLGL_OK) {
+        if (ctx) snprintf(g_thread_err, sizeof g_thread_err, "%s", ctx->err_msg);
+        rlgl_destroy(ctx);
+        if (out) *out = nullptr;
+        return s;
+    }
+    *out = ctx;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_create_from_state(int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col, const float* w, const double* c,
+                                   const double* h, rlgl_precision prec, rlgl_memspace src,
+                                   void* stream, rlgl_ctx** out) {
+    if (!c || !h) return fail(nullptr, RLGL_EINVAL, "c/h is NULL");
+    rlgl_ctx* ctx = nullptr;
+    rlgl_status s = create_common(n, nnz, row_ptr, col, w, prec, src, stream, &ctx);
+    auto bail = [&](rlgl_status st) {
+        if (ctx) snprintf(g_thread_err, sizeof g_thread_err, "%s", ctx->err_msg);
+        rlgl_destroy(ctx);
+        if (out) *out = nullptr;
+        return st;
+    };
+    if (s != RLGL_OK) return bail(s);
+    // Check the total of c on the host, then record C_0 = c - h (P - I).
+    std::vector<double> hc((size_t)n);
+    if (src == RLGL_DEVICE) {
+        if (cudaMemcpy(hc.data(), c, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(ctx, RLGL_ECUDA, "reading c failed"));
+    } else {
+        memcpy(hc.data(), c, (size_t)n * sizeof(double));
+    }
+    double tot = 0.0, l1 = 0.0;
+    for (double v : hc) { tot += v; l1 += fabs(v); }
+    if (fabs(tot) > 1e-12 * (l1 > 1.0 ? l1 : 1.0))
+        return bail(fail(ctx, RLGL_EINVAL, "sum of c is %g, not zero", tot));
+    if ((s = upload(ctx, ctx->H, h, (size_t)n * sizeof(double), src)) != RLGL_OK) return bail(s);
+    if ((s = dalloc(ctx, &ctx->c0, (size_t)n)) != RLGL_OK) return bail(s);
+    if (cudaMemcpyAsync(ctx->c0, hc.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, RLGL_ECUDA, "upload of c failed"));
+    // y = H P by the residual pull (forced, measuring), then C_0 and C.
+    k_set_refresh_flags<<<1, 1, 0, ctx->stream>>>(ctx->st, 1, 0);
+    k_refresh_src<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, ctx->s, (int)n, ctx->hsrc, ctx->st);
+    if (ctx->has_w)
+        k_pull<double, double, true, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles, ctx->st);
+    else
+        k_pull<double, double, false, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles, ctx->st);
+    if (ctx->prec == RLGL_MIXED)
+        k_record_c0<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->c0, ctx->H, ctx->y, (float*)ctx->c, (int)n, ctx->st);
+    else
+        k_record_c0<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->c0, ctx->H, ctx->y, (double*)ctx->c, (int)n, ctx->st);
+    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
+    if (cudaGetLastError() != cudaSuccess) return bail(fail(ctx, RLGL_ECUDA, "launch failed"));
+    // The cash is exactly what was given (fresh), and a resumed state counts
+    // as t >= 2 for the stopping rule.
+    int one = 1;
+    long long mv = 1;
+    if (cudaMemcpyAsync(&ctx->st->fresh, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&ctx->st->moves, &mv, sizeof mv, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&ctx->st->l1_refresh, &l1, sizeof l1, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, RLGL_ECUDA, "state init failed"));
+    if ((s = read_state(ctx)) != RLGL_OK) return bail(s);
+    *out = ctx;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_reset(rlgl_ctx* ctx, const double* m0, rlgl_memspace src) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    return set_step0(ctx, m0, src);
+}
+
+rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period, rlgl_memspace src) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (!masks || period < 1) return fail(ctx, RLGL_EINVAL, "masks is NULL or period < 1");
+    if (ctx->masks) { cudaFree(ctx->masks); ctx->masks = nullptr; }
+    TRY(dalloc(ctx, &ctx->masks, (size_t)(period * ctx->n)));
+    TRY(upload(ctx, ctx->masks, masks, (size_t)(period * ctx->n), src));
+    ctx->n_masks = period;
+    static const long long zero = 0;
+    CK(ctx, cudaMemcpyAsync(&ctx->st->mask_cursor, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);  // captured launches hold the mask pointer
+    return RLGL_OK;
+}
+
+static rlgl_status check_sched(rlgl_ctx* ctx, rlgl_schedule sched) {
+    if (sched < RLGL_ALL_GREEN || sched > RLGL_LINK_THRESHOLD)
+        return fail(ctx, RLGL_EINVAL, "bad schedule %d", (int)sched);
+    if (sched == RLGL_MASK && !ctx->masks) return fail(ctx, RLGL_EINVAL, "RLGL_MASK needs rlgl_set_masks");
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_step_info* info) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(check_sched(ctx, sched));
+    TRY(begin(ctx, sched, theta, 0.0, 1, 0));
+    TRY(iteration(ctx, false, sched, 0ull, 0));
+    if (info) {
+        TRY(read_state(ctx));
+        DevState* h = ctx->host_st;
+        info->green = h->green;
+        info->edges_pushed = h->edges;
+        info->mode = h->mode;
+        info->theta = h->theta;
+        // statistics of the new cash
+        TRY(begin(ctx, sched, theta, 0.0, 1, 0));
+        Launch L{ctx, false};
+        if (ctx->prec == RLGL_MIXED)
+            LAUNCH(L, KC_STATS, (k_stats<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+                                    (const float*)ctx->c, ctx->deg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0)));
+        else
+            LAUNCH(L, KC_STATS, (k_stats<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+                                    (const double*)ctx->c, ctx->deg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0)));
+        TRY(read_state(ctx));
+        info->l1_cash = h->l1;
+        info->sum_cash = h->sum;
+        info->sum_hist = h->hsum;
+    }
+    return RLGL_OK;
+}
+
+static rlgl_status build_graph(rlgl_ctx* ctx, int sched) {
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+    // cudaGraphNodeParams holds a union without a default constructor:
+    // build it in zeroed storage.
+    alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+    memset(pbuf, 0, sizeof pbuf);
+    cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(pbuf);
+    p->type = cudaGraphNodeTypeConditional;
+    p->conditional.handle = handle;
+    p->conditional.type = cudaGraphCondTypeWhile;
+    p->conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, p);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+    cudaGraph_t body = p->conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+    rlgl_status s = iteration(ctx, true, sched, (unsigned long long)handle, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(ctx->stream, &captured);
+    if (s != RLGL_OK) { cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e);
+    ctx->graph[sched] = exec;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                       int64_t max_steps, rlgl_solve_info* info) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(check_sched(ctx, sched));
+    if (max_steps < 1 || max_steps > 100000000ll) return fail(ctx, RLGL_EINVAL, "max_steps out of range");
+    if (!(tol >= 0.0)) return fail(ctx, RLGL_EINVAL, "tol must be >= 0");
+    if (!ctx->graph[sched]) TRY(build_graph(ctx, sched));
+    TRY(read_state(ctx));
+    DevState before = *ctx->host_st;
+    TRY(begin(ctx, sched, theta, tol, max_steps, 1));
+    CK(ctx, cudaGraphLaunch(ctx->graph[sched], ctx->stream));
+    TRY(read_state(ctx));
+    DevState* h = ctx->host_st;
+    if (info) {
+        info->moves = h->solve_moves;
+        info->edges_pushed = h->tot_edges - before.tot_edges;
+        info->green_total = h->tot_green - before.tot_green;
+        info->push_moves = h->push_moves - before.push_moves;
+        info->pull_moves = h->pull_moves - before.pull_moves;
+        info->refreshes = h->refreshes - before.refreshes;
+        info->iterations = h->iters;
+        info->resid = h->hsum != 0.0 ? h->l1 / fabs(h->hsum) : INFINITY;
+        info->l1_cash = h->l1;
+        info->sum_hist = h->hsum;
+    }
+    switch (h->status) {
+        case ST_OK: return RLGL_OK;
+        case ST_DEGENERATE: return fail(ctx, RLGL_EDEGENERATE, "degenerate history: |H 1| ~ 0");
+        case ST_NOCONV: return fail(ctx, RLGL_ENOCONV, "no convergence in %lld moves", (long long)max_steps);
+        case ST_TIMEOUT: return fail(ctx, RLGL_ETIMEOUT, "solve exceeded its time limit");
+        default: return fail(ctx, RLGL_ECUDA, "unexpected device status %d", h->status);
+    }
+}
+
+rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (!pi_out) return fail(ctx, RLGL_EINVAL, "pi_out is NULL");
+    const int n = (int)ctx->n;
+    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->st, ctx->part, 0);
+    CKL(ctx);
+    double sums[2];
+    CK(ctx, cudaMemcpyAsync(sums, ctx->part + 2 * kMaxGrid, sizeof sums, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!(fabs(sums[0]) > 1e-12 * sums[1]) || sums[1] == 0.0)
+        return fail(ctx, RLGL_EDEGENERATE, "degenerate history: H 1 = %g, sum|H| = %g", sums[0], sums[1]);
+    double* out = pi_out;
+    if (dst == RLGL_HOST) out = ctx->hsrc;  // staging (all scratch, rewritten before use)
+    k_scale<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->part + 2 * kMaxGrid, out);
+    CKL(ctx);
+    if (dst == RLGL_HOST)
+        CK(ctx, cudaMemcpyAsync(pi_out, out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace dst) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    const int n = (int)ctx->n;
+    if (c) {
+        double* out = (dst == RLGL_HOST) ? ctx->hsrc : c;
+        if (ctx->prec == RLGL_MIXED)
+            k_to_double<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>((const float*)ctx->c, n, out);
+        else
+            k_to_double<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>((const double*)ctx->c, n, out);
+        CKL(ctx);
+        if (dst == RLGL_HOST)
+            CK(ctx, cudaMemcpyAsync(c, out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (h)
+        CK(ctx, cudaMemcpyAsync(h, ctx->H, (size_t)n * sizeof(double),
+                                dst == RLGL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_invariant_residual(rlgl_ctx* ctx, double* l1) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(forced_refresh(ctx, false));
+    TRY(read_state(ctx));
+    if (l1) *l1 = ctx->host_st->resid_l1;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_refresh(rlgl_ctx* ctx, double* l1_before) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(forced_refresh(ctx, true));
+    TRY(read_state(ctx));
+    if (l1_before) *l1_before = ctx->host_st->resid_l1;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
+    if (!ctx || !p) return fail(ctx, RLGL_EINVAL, "NULL argument");
+    if (!(p->theta_scale > 0.0) || p->r < 1 || !(p->top_frac > 0.0 && p->top_frac <= 1.0) ||
+        !(p->pull_crossover >= 0.0) || p->safety_every < 0 || !(p->refresh_factor >= 0.0 && p->refresh_factor < 1.0) ||
+        !(p->time_limit_s > 0.0))
+        return fail(ctx, RLGL_EINVAL, "parameter out of range");
+    ctx->params = *p;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_get_params(const rlgl_ctx* ctx, rlgl_params* p) {
+    if (!ctx || !p) return RLGL_EINVAL;
+    *p = ctx->params;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_profile(rlgl_ctx* ctx, int32_t mode) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (mode == 2) {
+        TRY(prof_collect(ctx));
+        for (int i = 0; i < KC_N; ++i) { ctx->prof_ms[i] = 0.0; ctx->prof_n[i] = 0; }
+        return RLGL_OK;
+    }
+    ctx->profiling = mode ? 1 : 0;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(prof_collect(ctx));
+    for (int i = 0; i < KC_N; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (launches) launches[i] = ctx->prof_n[i];
+    }
+    return RLGL_OK;
+}
+
+void* rlgl_stream(const rlgl_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+const char* rlgl_last_error(const rlgl_ctx* ctx) { return ctx ? ctx->err_msg : g_thread_err; }
+
+const char* rlgl_status_string(rlgl_status s) {
+    switch (s) {
+        case RLGL_OK: return "RLGL_OK";
+        case RLGL_EINVAL: return "RLGL_EINVAL";
+        case RLGL_ENOTSTOCHASTIC: return "RLGL_ENOTSTOCHASTIC";
+        case RLGL_ENOMEM: return "RLGL_ENOMEM";
+        case RLGL_ECUDA: return "RLGL_ECUDA";
+        case RLGL_EDEGENERATE: return "RLGL_EDEGENERATE";
+        case RLGL_ENOCONV: return "RLGL_ENOCONV";
+        case RLGL_ETIMEOUT: return "RLGL_ETIMEOUT";
+    }
+    return "unknown status";
+}
+
+void rlgl_destroy(rlgl_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto& g : ctx->graph)
+        if (g) cudaGraphExecDestroy(g);
+    void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->deg, ctx->t_ptr, ctx->t_src, ctx->t_w,
+                   ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
+                   ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
+                   ctx->err, ctx->st};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (ctx->host_st) cudaFreeHost(ctx->host_st);
+    if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+"""Python binding of librlgl (include/rlgl.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts
+numpy arrays / torch tensors into pointers and status codes into
+exceptions. It never computes any part of a move itself and has no CPU
+fallback: if the library cannot be loaded, importing the functions raises.
+
+Names follow the C ABI: ``create``, ``step``, ``solve``, ``estimate``, ...
+and the ``Chain`` class wraps one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD = 0, 1, 2, 3, 4
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+SCHEDULES = {"all_green": ALL_GREEN, "threshold": THRESHOLD, "topfrac": TOPFRAC, "mask": MASK,
+             "link_threshold": LINK_THRESHOLD}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh")
+
+_STATUS = {0: "RLGL_OK", 1: "RLGL_EINVAL", 2: "RLGL_ENOTSTOCHASTIC", 3: "RLGL_ENOMEM",
+           4: "RLGL_ECUDA", 5: "RLGL_EDEGENERATE", 6: "RLGL_ENOCONV", 7: "RLGL_ETIMEOUT"}
+
+
+class RLGLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("theta_scale", ctypes.c_double), ("r", ctypes.c_int32),
+                ("top_frac", ctypes.c_double), ("pull_crossover", ctypes.c_double),
+                ("safety_every", ctypes.c_int32), ("refresh_factor", ctypes.c_double),
+                ("time_limit_s", ctypes.c_double)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("green", ctypes.c_int64), ("edges_pushed", ctypes.c_int64),
+                ("mode", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("l1_cash", ctypes.c_double), ("sum_cash", ctypes.c_double),
+                ("sum_hist", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("moves", ctypes.c_int64), ("edges_pushed", ctypes.c_int64),
+                ("green_total", ctypes.c_int64), ("push_moves", ctypes.c_int64),
+                ("pull_moves", ctypes.c_int64), ("refreshes", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("resid", ctypes.c_double), ("l1_cash", ctypes.c_double),
+                ("sum_hist", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_I64, _I32, _D, _VP = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+_ST = ctypes.c_int
+SIGNATURES = {
+    "rlgl_default_params": (_ST, [ctypes.POINTER(Params)]),
+    "rlgl_create": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _I32, _I32, _VP, ctypes.POINTER(_VP)]),
+    "rlgl_create_from_state": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _I32, _I32, _VP,
+                                     ctypes.POINTER(_VP)]),
+    "rlgl_reset": (_ST, [_VP, _VP, _I32]),
+    "rlgl_set_masks": (_ST, [_VP, _VP, _I64, _I32]),
+    "rlgl_step": (_ST, [_VP, _I32, _D, ctypes.POINTER(StepInfo)]),
+    "rlgl_solve": (_ST, [_VP, _I32, _D, _D, _I64, ctypes.POINTER(SolveInfo)]),
+    "rlgl_estimate": (_ST, [_VP, _VP, _I32]),
+    "rlgl_get_state": (_ST, [_VP, _VP, _VP, _I32]),
+    "rlgl_invariant_residual": (_ST, [_VP, ctypes.POINTER(_D)]),
+    "rlgl_refresh": (_ST, [_VP, ctypes.POINTER(_D)]),
+    "rlgl_set_params": (_ST, [_VP, ctypes.POINTER(Params)]),
+    "rlgl_get_params": (_ST, [_VP, ctypes.POINTER(Params)]),
+    "rlgl_profile": (_ST, [_VP, _I32]),
+    "rlgl_kernel_times": (_ST, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "rlgl_stream": (_VP, [_VP]),
+    "rlgl_last_error": (ctypes.c_char_p, [_VP]),
+    "rlgl_status_string": (ctypes.c_char_p, [_ST]),
+    "rlgl_destroy": (None, [_VP]),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Loads librlgl.so (building it with nvcc when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"CUDA library not built: {_build.LIB}")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(lib, ctx, status):
+    if status != 0:
+        msg = lib.rlgl_last_error(ctx)
+        raise RLGLError(status, msg.decode() if msg else "")
+
+
+def _ptr(a, dtype=None):
+    """(pointer, memspace, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, HOST, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if dtype is not None:
+                a = a.to(dtype=dtype)
+            a = a.contiguous()
+            return a.data_ptr(), (DEVICE if a.is_cuda else HOST), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, HOST, arr
+
+
+def _np_dtype(t):
+    import torch
+    return {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
+            np.float64: torch.float64, np.uint8: torch.uint8}[t]
+
+
+class Chain:
+    """One chain on the GPU: wraps an rlgl_ctx.
+
+    csr: an object with n, row_ptr (int64), col (int32), w (float32 or None);
+    numpy arrays (copied from host) or CUDA torch tensors (copied on device).
+    """
+
+    def __init__(self, csr, m0=None, precision="fp64", stream=None, c=None, h=None):
+        self.lib = load()
+        self.n = int(csr.n)
+        self.nnz = int(csr.row_ptr[-1])
+        self.precision = precision
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        is_torch = _is_torch(csr.row_ptr)
+        cv = (lambda t: _np_dtype(t)) if is_torch else (lambda t: t)
+        rp, sp, k1 = _ptr(csr.row_ptr, cv(np.int64))
+        cp, _, k2 = _ptr(csr.col, cv(np.int32))
+        wp, _, k3 = _ptr(csr.w, cv(np.float32))
+        sptr = _stream_ptr(stream)
+        out = _VP()
+        if c is not None:
+            c_p, _, k4 = _ptr(c, cv(np.float64))
+            h_p, _, k5 = _ptr(h, cv(np.float64))
+            st = self.lib.rlgl_create_from_state(self.n, self.nnz, rp, cp, wp, c_p, h_p, prec, sp,
+                                                 sptr, ctypes.byref(out))
+        else:
+            m_p, _, k4 = _ptr(m0, cv(np.float64))
+            st = self.lib.rlgl_create(self.n, self.nnz, rp, cp, wp, m_p, prec, sp, sptr,
+                                      ctypes.byref(out))
+        _check(self.lib, None, st)
+        self.ctx = out.value
+
+    # ---------------------------------------------------------------- API
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.rlgl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, st):
+        _check(self.lib, self.ctx, st)
+
+    @property
+    def stream(self) -> int:
+        return int(self.lib.rlgl_stream(self.ctx) or 0)
+
+    def reset(self, m0=None):
+        p, sp, keep = _ptr(m0, np.float64 if not _is_torch(m0) else None)
+        self._c(self.lib.rlgl_reset(self.ctx, p, sp))
+
+    def set_masks(self, masks):
+        masks = masks if _is_torch(masks) else np.ascontiguousarray(masks, dtype=np.uint8)
+        period = int(np.prod(masks.shape)) // self.n
+        p, sp, keep = _ptr(masks)
+        self._c(self.lib.rlgl_set_masks(self.ctx, p, period, sp))
+
+    def step(self, schedule="threshold", theta: float = 0.0, info: bool = True):
+        si = StepInfo()
+        self._c(self.lib.rlgl_step(self.ctx, _sched(schedule), float(theta),
+                                   ctypes.byref(si) if info else None))
+        return si.asdict() if info else None
+
+    def solve(self, schedule="threshold", theta: float = 0.0, tol: float = 1e-12,
+              max_steps: int = 100000, raise_on_noconv: bool = True):
+        si = SolveInfo()
+        st = self.lib.rlgl_solve(self.ctx, _sched(schedule), float(theta), float(tol),
+                                 int(max_steps), ctypes.byref(si))
+        res = si.asdict()
+        res["status"] = _STATUS.get(st, st)
+        # ENOCONV / EDEGENERATE / ETIMEOUT end a solve normally; raise only
+        # when asked to
+        if st != 0 and (raise_on_noconv or st not in (5, 6, 7)):
+            self._c(st)
+        return res
+
+    def estimate(self, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.float64)
+        p, sp, keep = _ptr(out)
+        self._c(self.lib.rlgl_estimate(self.ctx, p, sp))
+        return out
+
+    def get_state(self):
+        c = np.empty(self.n)
+        h = np.empty(self.n)
+        self._c(self.lib.rlgl_get_state(self.ctx, c.ctypes.data, h.ctypes.data, HOST))
+        return c, h
+
+    def invariant_residual(self) -> float:
+        v = ctypes.c_double()
+        self._c(self.lib.rlgl_invariant_residual(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def refresh(self) -> float:
+        v = ctypes.c_double()
+        self._c(self.lib.rlgl_refresh(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def get_params(self) -> Params:
+        p = Params()
+        self._c(self.lib.rlgl_get_params(self.ctx, ctypes.byref(p)))
+        return p
+
+    def set_params(self, **kw):
+        p = self.get_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._c(self.lib.rlgl_set_params(self.ctx, ctypes.byref(p)))
+
+    def profile(self, mode: int):
+        self._c(self.lib.rlgl_profile(self.ctx, int(mode)))
+
+    def kernel_times(self):
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_int64 * 6)()
+        self._c(self.lib.rlgl_kernel_times(self.ctx, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def _is_torch(a) -> bool:
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _sched(s) -> int:
+    return SCHEDULES[s] if isinstance(s, str) else int(s)
+
+
+def default_params() -> Params:
+    p = Params()
+    _check(load(), None, load().rlgl_default_params(ctypes.byref(p)))
+    return p

@@ -125,7 +125,8 @@ def test_initial_cash_is_m0_times_P_minus_I():
 
 # ------------------------------------------------------------ invariants
 
-@pytest.mark.parametrize("sched", [oracle.ALL_GREEN, oracle.THRESHOLD, oracle.TOPFRAC])
+@pytest.mark.parametrize("sched", [oracle.ALL_GREEN, oracle.THRESHOLD, oracle.TOPFRAC,
+                                   oracle.LINK_THRESHOLD])
 def test_invariants_every_step(sched):
     """sum C = 0, ||C||_1 never grows, C = H(P - I) at every step."""
     csr = synth.tiny_chain(300, seed=7)
@@ -176,7 +177,8 @@ def test_gth_two_state_closed_form():
     assert np.allclose(pi, [b / (a + b), a / (a + b)], atol=1e-16, rtol=0)
 
 
-@pytest.mark.parametrize("sched", [oracle.ALL_GREEN, oracle.THRESHOLD, oracle.TOPFRAC])
+@pytest.mark.parametrize("sched", [oracle.ALL_GREEN, oracle.THRESHOLD, oracle.TOPFRAC,
+                                   oracle.LINK_THRESHOLD])
 def test_tiny_chain_1000_against_gth(sched):
     """The N = 1000 tiny chain: RLGL to ||C||_1/H1 < 1e-12 agrees with GTH."""
     csr = synth.tiny_chain(1000, seed=1)
@@ -354,6 +356,9 @@ def test_selection_hand_worked_cases():
             g, th = oracle.select(case["cash"], oracle.THRESHOLD, theta_scale=case["param"], r=1)
         elif case["sched"] == "threshold_r2":
             g, th = oracle.select(case["cash"], oracle.THRESHOLD, theta_scale=case["param"], r=2)
+        elif case["sched"] == "link_r1":
+            g, th = oracle.select(case["cash"], oracle.LINK_THRESHOLD, theta_scale=case["param"],
+                                  r=1, row_ptr=np.array([0, 3, 4, 6, 10]))
         else:
             g, th = oracle.select(case["cash"], oracle.TOPFRAC, top_frac=case["param"])
         assert sorted(np.nonzero(g)[0].tolist()) == case["green"], case
