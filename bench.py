@@ -10,7 +10,9 @@ seeded inputs stand in for the paper's web graphs.
 
 One bench step = one complete solve of that chain from step 0 to L1 error
 <= 1e-6 against the FP64 oracle's stationary law, with the headline
-schedule (RLGL threshold, theta = mean |C|): step 0, T* moves (T* found by
+schedule (RLGL threshold on the cash per out-link, |C_i|/d_i >= 0.5 x its
+mean; the literal |C_i| >= mean threshold, all-green power iteration and the
+top-1% schedule are timed the same way beside it): step 0, T* moves (T* found by
 an untimed calibration run), the estimate pi_hat = H / (H 1). The chain is
 resident in HBM; L2 (129 MB) is flushed between timed steps by writing a
 512 MB buffer. value = edge-pushes/s (links used by the moves, the paper's
@@ -254,35 +256,37 @@ class GpuRun:
         return times, infos
 
     def kernel_profile(self, sched, theta, tstar):
-        """Eager moves with CUDA events around every kernel on the context's
-        stream; returns per-class (ms, launches) and algorithmic bytes."""
+        """T* eager moves with every kernel queued before the stream runs and a
+        CUDA event pair around each kernel on the context's stream; returns
+        per-class (ms, launches) and the algorithmic bytes of those launches
+        (from the device-side move log)."""
         ch = self.chain
         csr = self.csr
         n, nnz = csr.n, csr.nnz
         cash = 4 if self.wl["precision"] == "mixed" else 8
-        has_w = csr.w is not None
+        wb = 4 if csr.w is not None else 0
+        link = 4 if sched == "link_threshold" else 0
         ch.reset()
         ch.profile(2)
-        ch.profile(1)
-        bytes_push = bytes_pull = 0.0
-        npush = npull = 0
-        for _ in range(tstar):
-            info = ch.step(sched, theta, info=True)
-            E, G = info["edges_pushed"], info["green"]
-            if info["mode"] == 1:
-                npush += 1
-                bytes_push += E * (4 + (4 if has_w else 0) + cash) + G * (8 + 8 + cash)
-            elif info["mode"] == 2:
-                npull += 1
-                bytes_pull += nnz * (4 + (4 if has_w else 0) + cash) + n * (8 + 2 * cash)
-        kt = ch.kernel_times()
-        ch.profile(0)
-        # the info=True path adds one stats launch per move: remove it
-        ms_stats, n_stats = kt["stats"]
-        kt["stats"] = (ms_stats * 0.5, n_stats // 2)
-        return kt, dict(push=(bytes_push, npush), pull=(bytes_pull, npull))
+        kt = ch.profile_moves(sched, theta, tstar)
+        log = ch.move_log(tstar)
+        alg = {k: 0.0 for k in KERNEL_CLASSES}
+        for rec in log:
+            E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
+            alg["stats"] += n * (cash + link)
+            if sched == "all_green":
+                alg["select"] += n * (3 * cash + 16 + 8)
+            else:
+                alg["select"] += n * (2 * cash + link) + G * (cash + 16 + 8 + 16 + 16 + cash)
+            if mode == 1:
+                alg["push"] += E * (4 + wb + cash) + G * (16 + cash)
+            elif mode == 2:
+                alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash)
+            if sched == "topfrac":
+                alg["topk"] += (3 if cash == 4 else 6) * n * cash
+        return kt, alg
 
-    def e2e(self, sched, theta, tstar, steps, warmup):
+    def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0):
         """Through the public API with host buffers: every step uploads the
         chain from pinned host memory (create), solves, and reads pi back."""
         torch = self.torch
@@ -299,6 +303,7 @@ class GpuRun:
             torch.cuda.synchronize(self.device)
             t0 = time.perf_counter()
             with Chain(pinned, precision=self.wl["precision"], stream=self.stream) as ch:
+                ch.set_params(theta_scale=theta_scale)
                 info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
                 ch.estimate(pi_host)
             t1 = time.perf_counter()
@@ -355,35 +360,62 @@ def run_gpu(args):
     ref, ref_info = oracle_reference(csr)
     ref_dev = torch.from_numpy(ref).to(device)
     g = GpuRun(csr, wl, device)
-    sched_theta = {"threshold": 0.0, "all_green": 0.0, "topfrac": 0.01}
-    cal = {}
-    for s in ("threshold", "all_green", "topfrac"):
-        if s != "threshold" and args.skip_compare:
-            continue
-        tstar, e, traj = g.calibrate(s, sched_theta[s], ref_dev, max_moves=args.max_moves)
-        cal[s] = dict(tstar=tstar, err=e, traj=traj)
+    # schedule -> (library schedule, theta argument, theta_scale, move cap)
+    plan = {
+        "link_threshold": ("link_threshold", 0.0, args.theta_scale, args.max_moves),
+        "threshold": ("threshold", 0.0, 1.0, args.max_moves),
+        "all_green": ("all_green", 0.0, 1.0, args.max_moves),
+        "topfrac": ("topfrac", 0.01, 1.0, min(args.max_moves, 2000)),
+    }
     head = args.sched
+    order = [head] + ([] if args.skip_compare else [k for k in plan if k != head])
+
+    def use(name):
+        sched, theta, scale, cap = plan[name]
+        g.chain.set_params(theta_scale=scale)
+        return sched, theta, cap
+
+    nvtx = torch.cuda.nvtx
+    cal = {}
+    nvtx.range_push("calibrate")
+    for name in order:
+        sched, theta, cap = use(name)
+        tstar, e, traj = g.calibrate(sched, theta, ref_dev, max_moves=cap)
+        cal[name] = dict(tstar=tstar, err=e, traj=traj)
+    nvtx.range_pop()
     if cal[head]["tstar"] is None:
         raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves")
     tstar = cal[head]["tstar"]
 
-    # kernel profile (eager, CUDA events on the context stream)
-    kt, alg = g.kernel_profile(head, sched_theta[head], tstar)
+    # kernel profile of the headline schedule (CUDA events on the context stream)
+    sched_h, theta_h, _ = use(head)
+    nvtx.range_push("profile")
+    kt, alg = g.kernel_profile(sched_h, theta_h, tstar)
+    nvtx.range_pop()
 
-    # comparison schedules (timed the same way, fewer repetitions)
+    # comparison schedules, timed the same way
     compare = {}
-    for s in ("all_green", "topfrac"):
-        if s in cal and cal[s]["tstar"]:
-            ts, inf = g.timed_solves(s, sched_theta[s], cal[s]["tstar"], max(2, args.steps // 2), 2)
-            compare[s] = dict(tstar=cal[s]["tstar"], ms=float(np.median(ts)),
-                              edges=inf[0]["edges_pushed"], err=cal[s]["err"])
+    nvtx.range_push("compare")
+    for name in order[1:]:
+        if cal[name]["tstar"]:
+            sched, theta, _ = use(name)
+            ts, inf = g.timed_solves(sched, theta, cal[name]["tstar"], max(3, args.steps // 2), 3)
+            compare[name] = dict(tstar=cal[name]["tstar"], ms=float(np.median(ts)),
+                                 edges=inf[0]["edges_pushed"], err=cal[name]["err"])
+        else:
+            compare[name] = dict(tstar=None, ms=None, err_at_cap=cal[name]["err"],
+                                 cap=plan[name][3])
+    nvtx.range_pop()
+    sched_h, theta_h, _ = use(head)
 
     # timed region: headline schedule
     clocks = ClockSampler(local)
     barrier(dist)
     torch.cuda.synchronize(device)
     clocks.start()
-    times, infos = g.timed_solves(head, sched_theta[head], tstar, args.steps, args.warmup)
+    nvtx.range_push("timed")
+    times, infos = g.timed_solves(sched_h, theta_h, tstar, args.steps, args.warmup)
+    nvtx.range_pop()
     torch.cuda.synchronize(device)
     clk = clocks.stop()
     barrier(dist)
@@ -398,17 +430,23 @@ def run_gpu(args):
     iters = infos[0]["iterations"]
 
     # e2e through the public API with host buffers
-    et, ep, h2d, d2h = g.e2e(head, sched_theta[head], tstar, max(2, args.steps // 2), 1)
+    if args.no_e2e:
+        et, ep, h2d, d2h = [float("nan")], [0], 0, 0
+    else:
+        et, ep, h2d, d2h = g.e2e(sched_h, theta_h, tstar, max(3, args.steps // 2), 1, args.theta_scale if head == "link_threshold" else 1.0)
     e2e_t = max_over_ranks(dist, float(np.sum(et)), device)
     e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
 
-    # roofline of the dominant kernel class
-    dom = max(("push", "pull"), key=lambda k: kt[k][0])
+    # roofline of the dominant kernel class (most device time in the profile;
+    # classes whose launches returned at once carry no algorithmic bytes)
+    dom = max((k for k in KERNEL_CLASSES if alg[k] > 0), key=lambda k: kt[k][0])
     ms_dom, n_dom = kt[dom]
-    bytes_dom, n_alg = alg[dom]
+    bytes_dom = alg[dom]
     peak, peak_src = measured_peaks()
-    achieved = (bytes_dom / max(n_alg, 1)) / ((ms_dom / max(n_dom, 1)) / 1e3) / 1e9 if n_dom else None
-    kernels_per_iter = {"threshold": 4, "all_green": 4, "topfrac": 7}[head] + (3 if wl["precision"] == "mixed" else 0)
+    # time of the launches that did the work: for push/pull the launches of
+    # the other mode return at once and are a few microseconds each
+    achieved = bytes_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
+    kernels_per_iter = (7 if head == "topfrac" else 4) + (3 if wl["precision"] == "mixed" else 0)
     launches = args.steps * (kernels_per_iter * iters + 1 + 5 + 2)
 
     out = {
@@ -417,13 +455,17 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 cash / f64 history" if wl["precision"] == "mixed" else "f64",
         "data": "synthetic (seeded R-MAT; stands in for the paper's web graphs)",
         "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
-                   "schedule": head, "precision": wl["precision"], "tstar_moves": tstar,
+                   "schedule": head, "theta_scale": plan[head][2], "precision": wl["precision"],
+                   "tstar_moves": tstar,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "time_to_err_ms": {head: ms_per_step, **{k: v["ms"] for k, v in compare.items()}},
         "moves_to_err": {k: v["tstar"] for k, v in cal.items()},
-        "edge_pushes_to_err": {head: infos[0]["edges_pushed"], **{k: v["edges"] for k, v in compare.items()}},
-        "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step) if "all_green" in compare else None,
+        "edge_pushes_to_err": {head: infos[0]["edges_pushed"],
+                               **{k: v.get("edges") for k, v in compare.items()}},
+        "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step)
+        if compare.get("all_green", {}).get("ms") else None,
+        "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
         "final_l1_err": final_err,
         "reference": {"kind": "oracle power iteration (FP64, host)", **ref_info},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -431,7 +473,7 @@ def run_gpu(args):
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
                      "traffic": traffic_from_profiles(dom, args.workload),
                      "launches": n_dom, "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
-                     "alg_bytes_per_launch": bytes_dom / max(n_alg, 1)},
+                     "alg_bytes_per_launch": bytes_dom / max(n_dom, 1)},
         "kernel_ms": {k: v[0] for k, v in kt.items()},
         "kernel_launches": {k: v[1] for k, v in kt.items()},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -488,10 +530,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
-    ap.add_argument("--sched", choices=["threshold", "topfrac", "all_green"], default="threshold")
+    ap.add_argument("--sched", choices=["link_threshold", "threshold", "topfrac", "all_green"],
+                    default="link_threshold")
+    ap.add_argument("--theta-scale", type=float, default=0.5,
+                    help="theta_scale of the per-link threshold schedule")
     ap.add_argument("--max-moves", type=int, default=20000)
     ap.add_argument("--skip-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-moves", type=int, default=2)
     args = ap.parse_args(argv)

@@ -111,6 +111,17 @@ typedef struct {
     double l1_cash, sum_hist;
 } rlgl_solve_info;
 
+/* One entry of the per-move log (see rlgl_move_log). */
+typedef struct {
+    int64_t move;           /* t - 1: moves made since step 0 when this one started */
+    int64_t green;          /* |G_t| */
+    int64_t edges_pushed;   /* sum_{i in G_t} deg_i */
+    int32_t mode;           /* 0 none, 1 push, 2 pull */
+    double theta;           /* threshold used (0 when none) */
+    double l1_cash;         /* ||C_t||_1 before the move */
+    double sum_hist;        /* H_{t+1} 1 after the move */
+} rlgl_move_record;
+
 /* Fills p with the defaults listed in rlgl_params. */
 rlgl_status rlgl_default_params(rlgl_params* p);
 
@@ -200,6 +211,17 @@ rlgl_status rlgl_get_params(const rlgl_ctx* ctx, rlgl_params* p);
  * rlgl_profile(ctx, 2) clears. */
 rlgl_status rlgl_profile(rlgl_ctx* ctx, int32_t mode);
 rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches);
+
+/* Profiling run: `moves` eager moves (as rlgl_step) whose kernels are all
+ * queued before the stream is released, with a CUDA event pair around every
+ * kernel, so each pair measures the kernel's own device time. Adds to the
+ * totals read by rlgl_kernel_times. Synchronises. */
+rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves);
+
+/* Copies the log of the last min(count, 65536) moves, oldest first, into
+ * out (host, count entries); *written receives the number copied. The log
+ * is kept on the device by the select kernel and survives rlgl_reset. */
+rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, int64_t* written);
 
 /* The CUDA stream the context works on (cudaStream_t). */
 void* rlgl_stream(const rlgl_ctx* ctx);

@@ -5,11 +5,14 @@
 // move runs in the kernels of rlgl_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/rlgl.h"
@@ -64,6 +67,7 @@ struct rlgl_ctx {
     unsigned char* masks = nullptr;
     long long n_masks = 0;
     unsigned int* err = nullptr;
+    MoveRecord* log = nullptr;
     DevState* st = nullptr;
     DevState* host_st = nullptr;  // pinned mirror
     Control* host_ctl = nullptr;  // pinned
@@ -218,7 +222,7 @@ static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long con
     LAUNCH(L, KC_SELECT,
            (k_select<T><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
                (T*)ctx->c, ctx->H, ctx->s, ctx->row_ptr, ctx->deg, ctx->masks, n, (T*)ctx->mt, ctx->f_eoff,
-               ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st, ctx->part)));
+               ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st, ctx->part, ctx->log)));
     if (ctx->has_w)
         LAUNCH(L, KC_PUSH,
                (k_push<T, true><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
@@ -430,6 +434,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->chunk_row, (size_t)(nnz / kPushChunk + 2)));
     TRY(dalloc(ctx, &ctx->part, (size_t)(4 * kMaxGrid + 8)));
     TRY(dalloc(ctx, &ctx->err, 1));
+    TRY(dalloc(ctx, &ctx->log, (size_t)kLogCap));
     TRY(dalloc(ctx, &ctx->st, 1));
     CK(ctx, cudaMallocHost((void**)&ctx->host_st, sizeof(DevState)));
     CK(ctx, cudaMallocHost((void**)&ctx->host_ctl, sizeof(Control)));
@@ -785,6 +790,61 @@ rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches) {
     return RLGL_OK;
 }
 
+namespace {
+// Holds the stream until the host has queued a batch of launches (bounded
+// wait: gives up after 30 s, the stream then simply continues).
+struct Gate {
+    std::atomic<int> open{0};
+};
+void CUDART_CB gate_wait(void* p) {
+    Gate* g = static_cast<Gate*>(p);
+    auto t0 = std::chrono::steady_clock::now();
+    while (!g->open.load(std::memory_order_acquire)) {
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(30)) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+}  // namespace
+
+rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    TRY(check_sched(ctx, sched));
+    if (moves < 0) return fail(ctx, RLGL_EINVAL, "moves < 0");
+    const int prev = ctx->profiling;
+    ctx->profiling = 1;
+    TRY(begin(ctx, sched, theta, 0.0, moves > 0 ? moves : 1, 0));
+    const int64_t batch = 16;
+    rlgl_status s = RLGL_OK;
+    for (int64_t m0 = 0; m0 < moves && s == RLGL_OK; m0 += batch) {
+        Gate gate;
+        CK(ctx, cudaLaunchHostFunc(ctx->stream, gate_wait, &gate));
+        for (int64_t m = m0; m < moves && m < m0 + batch && s == RLGL_OK; ++m)
+            s = iteration(ctx, false, sched, 0ull, 0);
+        gate.open.store(1, std::memory_order_release);
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->profiling = prev;
+    if (s != RLGL_OK) return s;
+    return prof_collect(ctx);
+}
+
+rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, int64_t* written) {
+    if (!ctx || !out || count < 0) return fail(ctx, RLGL_EINVAL, "bad argument");
+    static_assert(sizeof(rlgl_move_record) == sizeof(MoveRecord), "log record layout");
+    TRY(read_state(ctx));
+    long long total = ctx->host_st->moves;
+    long long have = total < kLogCap ? total : kLogCap;
+    long long k = count < have ? count : have;
+    for (long long i = 0; i < k; ++i) {
+        long long mv = total - k + i;
+        CK(ctx, cudaMemcpyAsync(out + i, ctx->log + (mv % kLogCap), sizeof(MoveRecord),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (written) *written = k;
+    return RLGL_OK;
+}
+
 void* rlgl_stream(const rlgl_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 const char* rlgl_last_error(const rlgl_ctx* ctx) { return ctx ? ctx->err_msg : g_thread_err; }
@@ -812,7 +872,7 @@ void rlgl_destroy(rlgl_ctx* ctx) {
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->deg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
-                   ctx->err, ctx->st};
+                   ctx->err, ctx->log, ctx->st};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (ctx->host_st) cudaFreeHost(ctx->host_st);

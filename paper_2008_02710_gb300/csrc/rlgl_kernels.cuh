@@ -37,6 +37,13 @@ constexpr int kCountBits = 27;        // frontier reservation: (edges << 27) | c
 constexpr int kRadixBits = 11;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxGrid = 4096;
+constexpr int kLogCap = 1 << 16;      // per-move log entries (ring)
+
+struct MoveRecord {                   // layout of rlgl_move_record
+    long long move, green, edges;
+    int mode, pad;
+    double theta, l1, hsum;
+};
 
 enum Mode : int { MODE_NONE = 0, MODE_PUSH = 1, MODE_PULL = 2 };
 enum Sched : int {
@@ -407,7 +414,8 @@ __global__ void __launch_bounds__(kThreads) k_select(
     const long long* __restrict__ row_ptr, const int* __restrict__ deg,
     const unsigned char* __restrict__ masks, int n,
     T* __restrict__ mt, long long* __restrict__ f_eoff, long long* __restrict__ f_base,
-    T* __restrict__ f_m, int* __restrict__ chunk_row, DevState* st, double* part) {
+    T* __restrict__ f_m, int* __restrict__ chunk_row, DevState* st, double* part,
+    MoveRecord* __restrict__ log) {
     if (st->done || st->skip_move) return;
     const Control& ctl = st->ctl;
     int sched = ctl.sched;
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
          it0 += (long long)gridDim.x * kNodesPerIter) {
         int idx[kNodesPerThread];
         T val[kNodesPerThread];
-        long long deg[kNodesPerThread], rb[kNodesPerThread];
+        long long rdeg[kNodesPerThread], rb[kNodesPerThread];
         bool g[kNodesPerThread];
         unsigned long long mine = 0ull;
 #pragma unroll
@@ -443,8 +451,8 @@ __global__ void __launch_bounds__(kThreads) k_select(
             }
             if (g[q] && sched != SCHED_ALL_GREEN) {
                 rb[q] = row_ptr[idx[q]];
-                deg[q] = row_ptr[idx[q] + 1] - rb[q];
-                mine += ((unsigned long long)deg[q] << kCountBits) + 1ull;
+                rdeg[q] = row_ptr[idx[q] + 1] - rb[q];
+                mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
             }
         }
         if (sched == SCHED_ALL_GREEN) {
@@ -487,10 +495,10 @@ __global__ void __launch_bounds__(kThreads) k_select(
                 f_m[k] = mtil;
                 // chunk b starts inside this row when e <= b*CH < e + deg
                 long long b0 = (e + kPushChunk - 1) / kPushChunk;
-                long long b1 = (e + deg[q] + kPushChunk - 1) / kPushChunk;
+                long long b1 = (e + rdeg[q] + kPushChunk - 1) / kPushChunk;
                 for (long long b = b0; b < b1; ++b) chunk_row[b] = (int)k;
                 ++k;
-                e += deg[q];
+                e += rdeg[q];
             } else {
                 mt[i] = T(0);
             }
@@ -536,6 +544,16 @@ __global__ void __launch_bounds__(kThreads) k_select(
         st->mode = mode;
         if (mode == MODE_PUSH) st->push_moves++;
         if (mode == MODE_PULL) st->pull_moves++;
+        MoveRecord rec;
+        rec.move = st->moves - 1;
+        rec.green = green;
+        rec.edges = edges;
+        rec.mode = mode;
+        rec.pad = 0;
+        rec.theta = theta;
+        rec.l1 = st->l1;
+        rec.hsum = st->hsum;
+        log[rec.move % kLogCap] = rec;
     }
 }
 
@@ -589,12 +607,56 @@ __global__ void __launch_bounds__(kThreads) k_push(
 
 // ------------------------------------------------------ merge-path pull
 
+// Segmented inclusive scan over the threads of a block: the running sum of
+// val restarts wherever key changes. Keys with a value >= 0 must form
+// contiguous runs (equal keys are never separated by a different key).
+// Returns this thread's scan value; s_key/s_val then hold every thread's
+// key and scan value.
+template <typename TV>
+__device__ __forceinline__ TV block_segscan(long long key, TV val, long long* s_key, TV* s_val) {
+    __shared__ long long w_key[kThreads / 32];
+    __shared__ TV w_val[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    TV x = val;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        TV y = __shfl_up_sync(0xffffffffu, x, o);
+        long long ky = __shfl_up_sync(0xffffffffu, key, o);
+        if (lane >= o && ky == key) x += y;
+    }
+    if (lane == 31) {
+        w_key[wid] = key;
+        w_val[wid] = x;
+    }
+    __syncthreads();
+    if (wid == 0 && lane < kThreads / 32) {
+        // the same scan over the warp tails
+        long long k = w_key[lane];
+        TV v = w_val[lane];
+#pragma unroll
+        for (int o = 1; o < kThreads / 32; o <<= 1) {
+            TV y = __shfl_up_sync(0x000000ffu, v, o);
+            long long ky = __shfl_up_sync(0x000000ffu, k, o);
+            if (lane >= o && ky == k) v += y;
+        }
+        w_val[lane] = v;
+    }
+    __syncthreads();
+    if (wid > 0 && w_key[wid - 1] == key) x += w_val[wid - 1];
+    s_key[threadIdx.x] = key;
+    s_val[threadIdx.x] = x;
+    __syncthreads();
+    return x;
+}
+
 // Sums over in-links (the CSC of P): out_j += sum_{e in in(j)} src[t_src[e]]
 // * t_w[e], balanced over rows + edges by merge-path tiles (Merrill and
 // Garland, SC'16). Each tile's edge values are gathered into shared memory
-// with coalesced loads of t_src/t_w, then every thread consumes kMpIpt
-// merge items. A row consumed whole by one thread is updated with a plain
-// read-modify-write; a row split between threads or tiles gets atomic adds.
+// with coalesced loads of t_src/t_w (all of a thread's loads issued before
+// any is used), then every thread consumes kMpIpt merge items. Rows that a
+// thread ends are written once; the pieces of a row split between threads
+// are joined by a segmented scan over the block, so only rows that cross a
+// tile boundary use atomic adds.
 // kind 0: cash pull (guarded by mode == PULL); kind 1: FP64 residual pull
 // into y (guarded by want_refresh / force_refresh).
 template <typename TV, typename TO, bool kHasW, int kKind>
@@ -611,13 +673,13 @@ __global__ void __launch_bounds__(kThreads) k_pull(
     __shared__ TV s_val[kMpItems];
     __shared__ int s_end[kMpItems + 1];
     __shared__ int s_start0;
+    __shared__ long long s_ckey[kThreads];
+    __shared__ TV s_cval[kThreads];
     for (long long b = blockIdx.x; b < ntiles; b += gridDim.x) {
         const long long r0 = tile_r[b], e0 = tile_e[b];
         const int nrows = (int)(tile_r[b + 1] - r0);
         const int nedges = (int)(tile_e[b + 1] - e0);
         {
-            // Stage the tile: all loads of a thread are issued before any is
-            // used (kMpIpt independent index loads, then gathers).
             int sidx[kMpIpt];
             float wv[kMpIpt];
             long long re[kMpIpt];
@@ -645,7 +707,12 @@ __global__ void __launch_bounds__(kThreads) k_pull(
         __syncthreads();
         const int total = nrows + nedges;
         int d = threadIdx.x * kMpIpt;
-        if (d < total) {
+        const bool active = d < total;
+        // head piece: the end of a row begun by earlier threads (rowA);
+        // tail piece: a row that continues past this thread (carry).
+        long long rowA = -1, rowB = -1;
+        TV accA = TV(0), accB = TV(0);
+        if (active) {
             const int dend = min(d + kMpIpt, total);
             int lo = max(0, d - nedges), hi = min(d, nrows);
             while (lo < hi) {
@@ -653,8 +720,8 @@ __global__ void __launch_bounds__(kThreads) k_pull(
                 if (s_end[mid] >= d - mid) hi = mid; else lo = mid + 1;
             }
             int i = lo, j = d - lo;
-            int row_start = (i == 0) ? s_start0 : s_end[i - 1];
-            bool whole = (j == row_start);  // no edge of row i consumed by earlier threads
+            const int row_start = (i == 0) ? s_start0 : s_end[i - 1];
+            bool whole = (j == row_start);  // no edge of row i before this thread
             TV acc = TV(0);
             int cnt = 0;
             for (; d < dend; ++d) {
@@ -663,10 +730,12 @@ __global__ void __launch_bounds__(kThreads) k_pull(
                     ++j;
                     ++cnt;
                 } else {
-                    if (cnt > 0) {
+                    if (!whole) {
+                        rowA = r0 + i;
+                        accA = acc;
+                    } else if (cnt > 0) {
                         TO* o = out + (r0 + i);
-                        if (whole) *o = (TO)(*o + (TO)acc);
-                        else atomicAdd(o, (TO)acc);
+                        *o = (TO)(*o + (TO)acc);
                     }
                     acc = TV(0);
                     cnt = 0;
@@ -674,8 +743,27 @@ __global__ void __launch_bounds__(kThreads) k_pull(
                     whole = true;
                 }
             }
-            if (cnt > 0) atomicAdd(out + (r0 + i), (TO)acc);  // row continues past this thread
+            if (cnt > 0 || !whole) {
+                // the row continues past this thread (or began before it and
+                // has not ended here)
+                rowB = r0 + i;
+                accB = acc;
+            }
         }
+        // Join the pieces: carry of thread t plus the carries of the threads
+        // before it on the same row.
+        const TV run = block_segscan<TV>(rowB, accB, s_ckey, s_cval);
+        if (rowA >= 0) {
+            TV sum = accA;
+            if (threadIdx.x > 0 && s_ckey[threadIdx.x - 1] == rowA) sum += s_cval[threadIdx.x - 1];
+            TO* o = out + rowA;
+            // the tile's first row may have begun in the previous tile
+            if (rowA == r0 && s_start0 < 0) atomicAdd(o, (TO)sum);
+            else *o = (TO)(*o + (TO)sum);
+        }
+        // last active thread: its carry leaves the tile
+        const int last = (total - 1) / kMpIpt;
+        if ((int)threadIdx.x == last && rowB >= 0) atomicAdd(out + rowB, (TO)run);
         __syncthreads();
     }
 }

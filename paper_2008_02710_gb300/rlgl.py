@@ -66,6 +66,16 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class MoveRecord(ctypes.Structure):
+    _fields_ = [("move", ctypes.c_int64), ("green", ctypes.c_int64),
+                ("edges_pushed", ctypes.c_int64), ("mode", ctypes.c_int32),
+                ("theta", ctypes.c_double), ("l1_cash", ctypes.c_double),
+                ("sum_hist", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -89,6 +99,8 @@ SIGNATURES = {
     "rlgl_get_params": (_ST, [_VP, ctypes.POINTER(Params)]),
     "rlgl_profile": (_ST, [_VP, _I32]),
     "rlgl_kernel_times": (_ST, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "rlgl_profile_moves": (_ST, [_VP, _I32, _D, _I64]),
+    "rlgl_move_log": (_ST, [_VP, ctypes.POINTER(MoveRecord), _I64, ctypes.POINTER(_I64)]),
     "rlgl_stream": (_VP, [_VP]),
     "rlgl_last_error": (ctypes.c_char_p, [_VP]),
     "rlgl_status_string": (ctypes.c_char_p, [_ST]),
@@ -265,6 +277,18 @@ class Chain:
 
     def profile(self, mode: int):
         self._c(self.lib.rlgl_profile(self.ctx, int(mode)))
+
+    def profile_moves(self, schedule, theta: float, moves: int):
+        """Eager moves with exact per-kernel CUDA-event timings; returns
+        kernel_times() accumulated so far."""
+        self._c(self.lib.rlgl_profile_moves(self.ctx, _sched(schedule), float(theta), int(moves)))
+        return self.kernel_times()
+
+    def move_log(self, count: int):
+        buf = (MoveRecord * int(count))()
+        n = ctypes.c_int64()
+        self._c(self.lib.rlgl_move_log(self.ctx, buf, int(count), ctypes.byref(n)))
+        return [buf[i].asdict() for i in range(n.value)]
 
     def kernel_times(self):
         ms = (ctypes.c_double * 6)()

@@ -161,13 +161,19 @@ def test_solve_tiny_fp64_vs_oracle_and_gth(tiny, sched):
     csr, p, ref = tiny
     pi_or, C, H, info_or = oracle.run(csr, sched=SCHEDS[sched], top_frac=0.01, tol=1e-12,
                                       max_steps=200000)
+    th = 0.01 if sched == "topfrac" else 0.0
     with Chain(csr) as ch:
-        info = ch.solve(sched, 0.01 if sched == "topfrac" else 0.0, tol=1e-12, max_steps=200000)
+        info = ch.solve(sched, th, tol=1e-12, max_steps=200000)
+        pi_tol = ch.estimate()
+        # the same number of moves as the oracle: the same trajectory up to
+        # the order of FP64 additions
+        ch.reset()
+        ch.solve(sched, th, tol=0.0, max_steps=info_or["moves"], raise_on_noconv=False)
         pi = ch.estimate()
     assert info["status"] == "RLGL_OK"
     assert abs(info["moves"] - info_or["moves"]) <= 1
     assert np.abs(pi - pi_or).sum() <= FP64_PI_TOL
-    assert np.abs(pi - ref).sum() <= 1e-11
+    assert np.abs(pi_tol - ref).sum() <= 1e-11
     assert abs(pi.sum() - 1) < 1e-13
 
 
@@ -183,15 +189,19 @@ def test_solve_tiny_mixed_vs_gth(tiny, sched):
     assert resid <= 1e-6
 
 
-def test_solve_medium_fp64_vs_oracle(medium):
+@pytest.mark.parametrize("sched", ["threshold", "link_threshold"])
+def test_solve_medium_fp64_vs_oracle(medium, sched):
     csr, p = medium
-    pi_or, C, H, info_or = oracle.run(csr, sched=oracle.THRESHOLD, tol=1e-12, max_steps=200000)
+    pi_or, C, H, info_or = oracle.run(csr, sched=SCHEDS[sched], tol=1e-12, max_steps=200000)
     ref, it, delta = oracle.power_iteration(csr, p, tol=1e-14, maxit=200000, nthreads=8)
     with Chain(csr) as ch:
-        info = ch.solve("threshold", tol=1e-12, max_steps=200000)
+        info = ch.solve(sched, tol=1e-12, max_steps=200000)
+        ch.reset()
+        ch.solve(sched, tol=0.0, max_steps=info_or["moves"], raise_on_noconv=False)
         pi = ch.estimate()
         inv = ch.invariant_residual()
     assert info["status"] == "RLGL_OK"
+    assert abs(info["moves"] - info_or["moves"]) <= 1
     assert np.abs(pi - pi_or).sum() <= FP64_PI_TOL
     # residual 1e-12 bounds the error by 1e-12 * ||Z|| (Eq. convergence)
     assert np.abs(pi - ref).sum() <= 1e-8
@@ -386,3 +396,27 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(RLGLError) as e:
         Chain(good, c=np.ones(50), h=np.ones(50))
     assert e.value.name == "RLGL_EINVAL"
+
+
+def test_profile_moves_and_move_log(medium):
+    """The gated profiling run makes the same moves as rlgl_step and the
+    device-side move log records them."""
+    csr, p = medium
+    with Chain(csr) as a, Chain(csr) as b:
+        for ch in (a, b):
+            ch.set_params(theta_scale=0.5)
+        a.profile(2)
+        kt = a.profile_moves("link_threshold", 0.0, 20)
+        for _ in range(20):
+            b.step("link_threshold", info=False)
+        ca, ha = a.get_state()
+        cb, hb = b.get_state()
+        # pushes add in a nondeterministic order: equal up to FP64 rounding
+        assert np.abs(ha - hb).max() <= 1e-12 * np.abs(hb).max()
+        assert np.abs(ca - cb).max() <= 1e-12 * np.abs(cb).max()
+        assert kt["select"][1] == 20 and kt["select"][0] > 0
+        log = a.move_log(50)
+        assert len(log) == 20 and [r["move"] for r in log] == list(range(20))
+        deg = np.diff(csr.row_ptr)
+        assert all(r["edges_pushed"] <= csr.nnz and r["green"] <= csr.n for r in log)
+        assert log[-1]["sum_hist"] > 0
