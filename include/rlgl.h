@@ -223,6 +223,36 @@ rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta,
  * is kept on the device by the select kernel and survives rlgl_reset. */
 rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, int64_t* written);
 
+/*
+ * ||C - C_0 - H (P - I)||_1 for a state held in the caller's own device
+ * buffers, computed without allocating any device memory. The paper has no
+ * counterpart: this entry point exists for callers that may not call
+ * cudaMalloc or cudaFree, for example while recording a CUDA stream capture,
+ * or inside a service whose device memory belongs to a framework's pool
+ * (cudaFree also synchronises the whole device).
+ *   n, nnz, row_ptr, col, w : the chain as for rlgl_create, all DEVICE
+ *              pointers (w may be NULL: unit weights).
+ *   c, h     : device double [n], the cash C_t and history H_t.
+ *   c0       : device double [n] or NULL (C_0 = 0).
+ *   l1_out   : device double [1]; receives the residual, or NaN when an
+ *              index of the CSR is out of range or a row is empty.
+ *   stream   : cudaStream_t the work is queued on (NULL: legacy stream).
+ * Asynchronous: returns after queueing three kernels; *l1_out is ready when
+ * the stream reaches that point. Its scratch is one fixed array in device
+ * memory (8 MiB of accumulators plus 8 KiB), held by every GPU that loads
+ * the library until the process exits, so n is limited to 2^20 nodes:
+ * RLGL_EINVAL beyond that, for NULL pointers, or for n or nnz < 1. RLGL_ECUDA
+ * when a launch fails. The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress), so make it before any stream
+ * capture. All calls on a device share the array and each one clears it
+ * first, so calls whose work overlaps on the GPU (two streams, or two
+ * threads) race and give wrong results; serialise them.
+ */
+rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                            const int32_t* col, const float* w, const double* c,
+                                            const double* h, const double* c0, double* l1_out,
+                                            void* stream);
+
 /* The CUDA stream the context works on (cudaStream_t). */
 void* rlgl_stream(const rlgl_ctx* ctx);
 

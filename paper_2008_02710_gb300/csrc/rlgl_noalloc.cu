@@ -1,0 +1,183 @@
+// rlgl_invariant_residual_noalloc: the cash-balance residual
+// ||C - C_0 - H (P - I)||_1 computed on buffers the caller owns, with no
+// device allocation at all.
+//
+// Who needs this: code that may not call cudaMalloc or cudaFree. Examples are
+// a caller recording a CUDA stream capture, a service whose device memory is
+// handed out by a framework's own pool (cudaFree also synchronises the whole
+// device, stalling every other stream), or a process that has already
+// reserved all of the GPU's memory for its pools. Such code can still run
+// this check on a state it holds in its own buffers.
+//
+// The scratch lives in one file-scope __device__ array of fixed size, so the
+// entry point works for chains of at most kNoAllocMaxNodes nodes. Every GPU
+// that loads this library keeps that array (about 8.1 MiB) until the process
+// exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/rlgl.h"
+
+namespace {
+
+constexpr long long kNoAllocMaxNodes = 1ll << 20;  // nodes: 8 MiB of FP64 accumulators
+constexpr int kNaThreads = 256;
+constexpr int kNaGrid = 1024;                       // blocks of the reduction (partials)
+constexpr size_t kAccBytes = (size_t)kNoAllocMaxNodes * sizeof(double);
+constexpr size_t kPartBytes = (size_t)kNaGrid * sizeof(double);
+constexpr size_t kScratchBytes = kAccBytes + kPartBytes + 256;
+
+// [0, kAccBytes): y_j accumulators; then kNaGrid partial sums; then a ticket
+// and an error flag.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+struct Scratch {
+    double* y;
+    double* part;
+    unsigned int* ticket;
+    unsigned int* bad;
+};
+
+__device__ __forceinline__ Scratch carve(unsigned char* base) {
+    Scratch s;
+    s.y = reinterpret_cast<double*>(base);
+    s.part = reinterpret_cast<double*>(base + kAccBytes);
+    s.ticket = reinterpret_cast<unsigned int*>(base + kAccBytes + kPartBytes);
+    s.bad = s.ticket + 1;
+    return s;
+}
+
+// Clears what must start at zero: the accumulators of this call's n nodes,
+// the ticket and the error flag (the array keeps the previous call's data).
+__global__ void na_clear(unsigned char* base, long long n) {
+    Scratch s = carve(base);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s.y[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *s.ticket = 0u;
+        *s.bad = 0u;
+    }
+}
+
+// y_j += H_i p_ij over every out-edge, one warp per row; p_ij = w_ij / sum_k
+// w_ik (or 1/deg_i without weights). Empty rows, row offsets outside
+// [0, nnz] and columns outside [0, n) are skipped and flagged instead of
+// being accessed.
+__global__ void na_scatter(unsigned char* base, long long n, long long nnz,
+                           const long long* __restrict__ row_ptr,
+                           const int* __restrict__ col, const float* __restrict__ w,
+                           const double* __restrict__ h) {
+    Scratch s = carve(base);
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < n; i += nwarps) {
+        const long long a = row_ptr[i], b = row_ptr[i + 1];
+        if (b <= a || a < 0 || b > nnz) {
+            if (lane == 0) atomicOr(s.bad, 1u);
+            continue;
+        }
+        double rs = 0.0;
+        if (w) {
+            for (long long k = a + lane; k < b; k += 32) rs += (double)w[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        } else {
+            rs = (double)(b - a);
+        }
+        const double hi = h[i] / rs;
+        for (long long k = a + lane; k < b; k += 32) {
+            const int j = col[k];
+            if (j < 0 || j >= n) {
+                atomicOr(s.bad, 1u);
+                continue;
+            }
+            atomicAdd(s.y + j, w ? hi * (double)w[k] : hi);
+        }
+    }
+}
+
+// l1 = sum_j |c_j - c0_j - (y_j - h_j)|, combined by the last block to
+// finish; NaN when an index was out of range.
+__global__ void na_reduce(unsigned char* base, long long n, const double* __restrict__ c,
+                          const double* __restrict__ h, const double* __restrict__ c0,
+                          double* l1_out) {
+    Scratch s = carve(base);
+    __shared__ double red[kNaThreads / 32];
+    __shared__ bool last;
+    double acc = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        double r = c[j] - (c0 ? c0[j] : 0.0) - (s.y[j] - h[j]);
+        acc += fabs(r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < kNaThreads / 32; ++k) b += red[k];
+        s.part[blockIdx.x] = b;
+        __threadfence();
+        last = (atomicAdd(s.ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned int k = 0; k < gridDim.x; ++k) t += __ldcg(s.part + k);
+        *l1_out = (*(volatile unsigned int*)s.bad) ? __longlong_as_double(0x7ff8000000000000ll) : t;
+        *s.ticket = 0u;
+    }
+}
+
+std::mutex g_setup_mu;
+unsigned char* g_scratch_ptr[128] = {nullptr};  // device address of the array, per device
+
+}  // namespace
+
+extern "C" rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz,
+                                                       const int64_t* row_ptr,
+                                                       const int32_t* col, const float* w,
+                                                       const double* c, const double* h,
+                                                       const double* c0, double* l1_out,
+                                                       void* stream) {
+    if (n < 1 || nnz < 1 || !row_ptr || !col || !c || !h || !l1_out) {
+        return RLGL_EINVAL;
+    }
+    if (n > kNoAllocMaxNodes) {
+        return RLGL_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+        return RLGL_ECUDA;
+    }
+    unsigned char* base = nullptr;
+    {
+        // First call on this device: look up the array's device address
+        // (the name itself is only a host-side stand-in).
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        if (!g_scratch_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                return RLGL_ECUDA;
+            }
+            g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_scratch_ptr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    na_clear<<<256, kNaThreads, 0, s>>>(base, n);
+    na_scatter<<<1024, kNaThreads, 0, s>>>(base, n, nnz, reinterpret_cast<const long long*>(row_ptr),
+                                           col, w, h);
+    na_reduce<<<kNaGrid, kNaThreads, 0, s>>>(base, n, c, h, c0, l1_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        return RLGL_ECUDA;
+    }
+    return RLGL_OK;
+}

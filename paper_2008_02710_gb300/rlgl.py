@@ -101,6 +101,8 @@ SIGNATURES = {
     "rlgl_kernel_times": (_ST, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "rlgl_profile_moves": (_ST, [_VP, _I32, _D, _I64]),
     "rlgl_move_log": (_ST, [_VP, ctypes.POINTER(MoveRecord), _I64, ctypes.POINTER(_I64)]),
+    "rlgl_invariant_residual_noalloc": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                              _VP]),
     "rlgl_stream": (_VP, [_VP]),
     "rlgl_last_error": (ctypes.c_char_p, [_VP]),
     "rlgl_status_string": (ctypes.c_char_p, [_ST]),
