@@ -489,6 +489,117 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Many-chain mix in one context: 4096 power-law chains (log-uniform
+    100..1e5 nodes), every chain to L1 error <= 1e-6 against its own oracle
+    stationary law; per-chain tolerance calibrated untimed."""
+    import torch
+    from paper_2008_02710_gb300 import synth
+    from paper_2008_02710_gb300.rlgl import Chain
+    import oracle
+    device = torch.device("cuda", 0)
+    t = time.time()
+    csr, node_ptr = synth.powerlaw_batch(args.chains, seed=1)
+    gen_s = time.time() - t
+    p = oracle.transition_probs(csr)
+    t = time.time()
+    ref, it, delta = oracle.power_iteration(csr, p, tol=1e-11, maxit=20000, nthreads=os.cpu_count() or 1)
+    ref_s = time.time() - t
+    del p
+    seg = np.repeat(np.arange(args.chains), np.diff(node_ptr))
+    ref = ref / np.bincount(seg, weights=ref, minlength=args.chains)[seg]  # per-chain normalisation
+    ref_dev = torch.from_numpy(ref).to(device)
+    seg_dev = torch.from_numpy(seg).to(device)
+    stream = torch.cuda.Stream(device=device)
+    pi = torch.empty(csr.n, dtype=torch.float64, device=device)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def chain_errors(ch):
+        ch.estimate(pi)
+        with torch.cuda.stream(stream):
+            e = torch.zeros(args.chains, dtype=torch.float64, device=device)
+            e.index_add_(0, seg_dev, (pi - ref_dev).abs())
+        return e.cpu().numpy()
+
+    out = {"metric": "batched: chains/s to L1 err 1e-6 per chain (4096-chain mix)", "unit": "chains/s",
+           "workload": f"{args.chains} power-law chains, n={csr.n}, nnz={csr.nnz}",
+           "gen_s": gen_s, "reference": dict(iterations=it, delta=delta, seconds=ref_s)}
+    with Chain(csr, precision="mixed", stream=stream, node_ptr=node_ptr) as ch:
+        for sched, scale in (("link_threshold", args.theta_scale), ("all_green", 1.0)):
+            ch.set_params(theta_scale=scale)
+            chosen = None
+            for tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 3e-10, 1e-10):
+                ch.reset()
+                info = ch.solve(sched, 0.0, tol, 20000, raise_on_noconv=False)
+                err = chain_errors(ch)
+                if err.max() <= ERR_TARGET:
+                    chosen = (tol, info, float(err.max()))
+                    break
+            if chosen is None:
+                out[sched] = {"reached": False, "max_err": float(err.max())}
+                continue
+            tol, info, emax = chosen
+            times = []
+            for i in range(args.warmup + args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ch.reset()
+                inf = ch.solve(sched, 0.0, tol, 20000, raise_on_noconv=False)
+                ch.estimate(pi)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            out[sched] = {"tol": tol, "max_err": emax, "ms": ms, "chains_per_s": args.chains / (ms / 1e3),
+                          "edge_pushes": inf["edges_pushed"],
+                          "edge_pushes_per_s": inf["edges_pushed"] / (ms / 1e3),
+                          "moves": inf["moves"], "status": inf["status"]}
+    if "ms" in out.get("link_threshold", {}):
+        out["value"] = out["link_threshold"]["chains_per_s"]
+        if "ms" in out.get("all_green", {}):
+            out["speedup_vs_all_green"] = out["all_green"]["ms"] / out["link_threshold"]["ms"]
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """Poisson stream of chain-solve requests through the continuous-batching
+    server, against one-at-a-time all-green solves of the same stream.
+    Requests draw their chain from a pool of R-MAT graphs with log-uniform
+    sizes 1e3..4e6 (each graph is generated once)."""
+    from paper_2008_02710_gb300 import synth
+    from paper_2008_02710_gb300.serve import Request, Server, summary
+    rng = np.random.default_rng(5)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(4e6), args.pool)).astype(np.int64)
+    t = time.time()
+    pool = [synth.rmat_chain_n(int(n), seed=1000 + k) for k, n in enumerate(sizes)]
+    gen_s = time.time() - t
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
+    picks = rng.integers(0, args.pool, args.requests)
+    tols = rng.choice([1e-4, 1e-6, 1e-8], args.requests)
+
+    def stream_of(schedule):
+        return [Request(i, float(arrivals[i]), pool[picks[i]], float(tols[i]), schedule=schedule)
+                for i in range(args.requests)]
+
+    out = {"metric": "serving: p50/p99 latency and solves/s (Poisson stream)", "unit": "solves/s",
+           "workload": f"{args.requests} requests at {args.rate}/s, pool of {args.pool} R-MAT graphs "
+                       f"(n {int(sizes.min())}..{int(sizes.max())}), tol in {{1e-4,1e-6,1e-8}}, "
+                       f"HBM budget {args.budget_gb} GB", "gen_s": gen_s}
+    srv = Server(args.budget_gb * 1e9, max_active=args.slots, precision="mixed",
+                 theta_scale=args.theta_scale, keep_pi=False)
+    res = srv.run(stream_of("link_threshold"), realtime=True)
+    out["ours"] = dict(summary(res), **srv.stats)
+    base = Server(args.budget_gb * 1e9, max_active=1, precision="mixed", keep_pi=False)
+    resb = base.run(stream_of("all_green"), realtime=True)
+    out["one_at_a_time_all_green"] = summary(resb)
+    out["value"] = out["ours"]["solves_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The FP64 CPU oracle timed on the host cores on the same workload."""
     ws, rank, local = dist_env()
@@ -529,7 +640,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving"], default="rmat20")
+    ap.add_argument("--chains", type=int, default=4096, help="batch: number of chains")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--pool", type=int, default=32, help="serving: distinct graphs drawn from")
+    ap.add_argument("--slots", type=int, default=32, help="serving: concurrent solves")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM budget")
     ap.add_argument("--sched", choices=["link_threshold", "threshold", "topfrac", "all_green"],
                     default="link_threshold")
     ap.add_argument("--theta-scale", type=float, default=0.5,
@@ -545,6 +662,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

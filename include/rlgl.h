@@ -22,6 +22,9 @@
  *    the call returns. Outputs go to caller-allocated buffers.
  *  - A context owns all its device memory and works on one CUDA stream. Calls
  *    on one context are not thread-safe; different contexts are independent.
+ *    Device memory comes from a stream-ordered pool shared by the contexts of
+ *    a device, so creating and destroying contexts does not synchronise the
+ *    device (freed memory up to 4 GiB is kept in the pool).
  *  - Node indices are 0-based; n < 2^27 and nnz < 2^37.
  */
 #ifndef RLGL_H
@@ -157,7 +160,35 @@ rlgl_status rlgl_create_from_state(int64_t n, int64_t nnz, const int64_t* row_pt
                                    const double* h, rlgl_precision prec, rlgl_memspace src,
                                    void* stream, rlgl_ctx** out);
 
-/* Step 0 again with a new M_0 (src memspace, double [n]; NULL = uniform),
+/*
+ * A batch of independent chains in one context (many chains, one launch per
+ * kernel): the chains are stacked block-diagonally, chain k owning the nodes
+ * node_ptr[k] .. node_ptr[k+1]-1, and no edge may leave its chain
+ * (RLGL_EINVAL otherwise). Every chain runs Alg. 1 on its own: its own
+ * statistics, threshold (THRESHOLD / LINK_THRESHOLD), stopping test and
+ * tolerance, and its own estimate pi_hat = H / (H 1) over its nodes. Step 0
+ * uses M_0 uniform within each chain. A chain that stops is frozen while
+ * the others continue; rlgl_solve returns when every chain has stopped
+ * (RLGL_OK when all converged, else the worst of ETIMEOUT, EDEGENERATE,
+ * ENOCONV) and rlgl_batch_chains reports each chain. RLGL_TOPFRAC is not
+ * available for a batch. The other arguments are those of rlgl_create,
+ * with node ids global (0..n-1); node_ptr is int64 [n_chains+1] in src.
+ */
+rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t n, int64_t nnz,
+                              const int64_t* row_ptr, const int32_t* col, const float* w,
+                              rlgl_precision prec, rlgl_memspace src, void* stream, rlgl_ctx** out);
+
+/* Per-chain tolerances (host double [n_chains], each >= 0), used by
+ * rlgl_solve when its tol argument is negative. */
+rlgl_status rlgl_batch_set_tol(rlgl_ctx* ctx, const double* tol);
+
+/* Per chain (host arrays of n_chains, each nullable): the status of its last
+ * solve (a rlgl_status value; -1 while running), moves made since step 0,
+ * and ||C||_1 / |H 1|. */
+rlgl_status rlgl_batch_chains(rlgl_ctx* ctx, int32_t* status, int64_t* moves, double* resid);
+
+/* Step 0 again with a new M_0 (src memspace, double [n]; NULL = uniform,
+ * within each chain for a batch),
  * keeping the uploaded chain. Clears the recorded C_0. */
 rlgl_status rlgl_reset(rlgl_ctx* ctx, const double* m0, rlgl_memspace src);
 
@@ -184,6 +215,20 @@ rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_ste
  */
 rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
                        int64_t max_steps, rlgl_solve_info* info);
+/* (For a batch, tol >= 0 applies to every chain and tol < 0 uses the
+ * per-chain tolerances of rlgl_batch_set_tol.) */
+
+/* rlgl_solve split in two, so that the host can do other work (or drive
+ * other contexts) while the device loop runs: rlgl_solve_async queues the
+ * solve graph on the context's stream and returns; rlgl_query sets
+ * *finished to 1 once it has completed (or when nothing is pending);
+ * rlgl_wait waits, fills info and returns the solve's status exactly as
+ * rlgl_solve would. Between rlgl_solve_async and rlgl_wait every other call
+ * on the context returns RLGL_EINVAL. */
+rlgl_status rlgl_solve_async(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                             int64_t max_steps);
+rlgl_status rlgl_query(rlgl_ctx* ctx, int32_t* finished);
+rlgl_status rlgl_wait(rlgl_ctx* ctx, rlgl_solve_info* info);
 
 /* pi_hat = H / (H 1) (Eq. pi_hat), FP64, into pi_out (dst memspace, double
  * [n]). RLGL_EDEGENERATE when |H 1| <= 1e-12 sum|H| (pi_out untouched). */
@@ -252,6 +297,12 @@ rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz, const int64_
                                             const int32_t* col, const float* w, const double* c,
                                             const double* h, const double* c0, double* l1_out,
                                             void* stream);
+
+/* Device bytes a context for such a chain (or batch of n_chains) holds once
+ * created, for admission control; -1 for n or nnz < 1. Transient memory
+ * during creation (the in-link build) adds about (n + 1) 8 bytes. */
+int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision prec,
+                       int64_t n_chains);
 
 /* The CUDA stream the context works on (cudaStream_t). */
 void* rlgl_stream(const rlgl_ctx* ctx);

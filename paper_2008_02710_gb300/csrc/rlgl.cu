@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -39,13 +40,19 @@ struct rlgl_ctx {
     bool has_w = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t pool = nullptr;
+    cudaEvent_t done_ev = nullptr;  // end of the last asynchronous solve
+    bool pending = false;           // an asynchronous solve not yet waited for
+    int pending_sched = 0;
+    long long pending_max = 0;
     int device = 0, sms = 0;
     // chain
     long long* row_ptr = nullptr;
     int* col = nullptr;
     float* w = nullptr;
     double* s = nullptr;
-    int* deg = nullptr;
+    float* sf = nullptr;     // s in FP32 (MIXED)
+    void* ideg = nullptr;    // 1 / out-degree in the cash type
     long long* t_ptr = nullptr;
     int* t_src = nullptr;
     float* t_w = nullptr;
@@ -69,11 +76,19 @@ struct rlgl_ctx {
     unsigned int* err = nullptr;
     MoveRecord* log = nullptr;
     DevState* st = nullptr;
+    // batch of independent chains (nchains > 1): node -> chain map and
+    // per-chain state; nchains == 1 is a single chain
+    int nchains = 1;
+    long long* node_ptr = nullptr;
+    int* chain_of = nullptr;
+    ChainState* cs = nullptr;
+    double* bsums = nullptr;  // per-chain sum H, sum |H| [2 nchains]
+    std::vector<int64_t> node_ptr_h;
     DevState* host_st = nullptr;  // pinned mirror
     Control* host_ctl = nullptr;  // pinned
     rlgl_params params{};
     // launch shapes
-    int grid_nodes = 1, grid_select = 1, grid_push = 1, grid_pull = 1;
+    int grid_nodes = 1, grid_select = 1, grid_push = 1, grid_pull = 1, grid_stats = 1;
     // solve graphs, one per schedule
     cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // profiling
@@ -106,18 +121,59 @@ static rlgl_status fail(rlgl_ctx* ctx, rlgl_status s, const char* fmt, ...) {
 
 #define CKL(ctx) CK(ctx, cudaGetLastError())
 
+#define NOT_PENDING(ctx)                                                                   \
+    do {                                                                                   \
+        if ((ctx)->pending)                                                                \
+            return fail((ctx), RLGL_EINVAL, "an asynchronous solve is pending: rlgl_wait"); \
+    } while (0)
+
 #define TRY(expr)                      \
     do {                               \
         rlgl_status s_ = (expr);       \
         if (s_ != RLGL_OK) return s_;  \
     } while (0)
 
+// Device memory comes from one stream-ordered pool per device (allocations
+// and frees are queued on the context's stream, so creating or destroying a
+// context does not synchronise the whole device, as cudaMalloc/cudaFree may).
+// Freed memory up to 4 GiB stays in the pool for the next context.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[128] = {nullptr};
+
+static rlgl_status device_pool(rlgl_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (ctx->device < 0 || ctx->device >= 128) return fail(ctx, RLGL_EINVAL, "device id out of range");
+    if (!g_pool[ctx->device]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        cudaMemPool_t pool;
+        CK(ctx, cudaMemPoolCreate(&pool, &props));
+        unsigned long long keep = 4ull << 30;
+        CK(ctx, cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[ctx->device] = pool;
+    }
+    ctx->pool = g_pool[ctx->device];
+    return RLGL_OK;
+}
+
+static rlgl_status dalloc_bytes(rlgl_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    CK(ctx, cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream));
+    return RLGL_OK;
+}
+
 template <typename P>
 static rlgl_status dalloc(rlgl_ctx* ctx, P** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    CK(ctx, cudaMalloc((void**)p, count * sizeof(P)));
-    return RLGL_OK;
+    return dalloc_bytes(ctx, (void**)p, count * sizeof(P));
+}
+
+static void dfree(rlgl_ctx* ctx, void* p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
 }
 
 static size_t cash_size(const rlgl_ctx* ctx) {
@@ -197,18 +253,35 @@ static rlgl_status enqueue_refresh(Launch L) {
     return RLGL_OK;
 }
 
-// One iteration of Alg. 1 on the device: [refresh] stats [top-k] select
-// push pull. Every kernel checks the device state and returns at once when
-// it has nothing to do, so the same sequence serves eager steps and the
-// captured solve loop.
+static int grid_for(long long work, int per_block, int cap);
+
+// Cash and 1/degree arrays start on 16-byte boundaries (vector loads).
+static int vec_aligned(const rlgl_ctx* ctx) {
+    return ((uintptr_t)ctx->c % 16 == 0) && ((uintptr_t)ctx->ideg % 16 == 0) ? 1 : 0;
+}
+
+// Graph handles of one solve graph (0 in eager mode).
+struct Conds {
+    unsigned long long loop = 0, refresh = 0, mode = 0;
+    int use = 0;
+};
+
+// stats, [top-k passes], select.
 template <typename T>
-static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long cond, int use_cond) {
+static rlgl_status enqueue_head(Launch L, int sched, const Conds& cd) {
     rlgl_ctx* ctx = L.ctx;
     const int n = (int)ctx->n;
-    if (ctx->prec == RLGL_MIXED && L.capture) TRY(enqueue_refresh<T>(L));
-    LAUNCH(L, KC_STATS,
-           (k_stats<T><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>((const T*)ctx->c, ctx->deg, n,
-                                                                       ctx->st, ctx->part, cond, use_cond)));
+    const BatchView bv{ctx->chain_of, ctx->cs, ctx->nchains};
+    if (ctx->nchains > 1)
+        LAUNCH(L, KC_STATS,
+               (k_bstats<T><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
+                   (const T*)ctx->c, (const T*)ctx->ideg, n, ctx->st, bv, cd.loop, cd.refresh,
+                   cd.use)));
+    else
+        LAUNCH(L, KC_STATS,
+               (k_stats<T><<<ctx->grid_stats, kThreads, 0, ctx->stream>>>(
+                   (const T*)ctx->c, (const T*)ctx->ideg, n, ctx->st, ctx->part, cd.loop, cd.refresh,
+                   cd.use, vec_aligned(ctx))));
     if (sched == RLGL_TOPFRAC) {
         const int bits = KeyOf<T>::bits;
         for (int hi = bits; hi > 0; hi -= kRadixBits) {
@@ -219,10 +292,24 @@ static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long con
                        (const T*)ctx->c, n, ctx->st, shift, width)));
         }
     }
-    LAUNCH(L, KC_SELECT,
-           (k_select<T><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
-               (T*)ctx->c, ctx->H, ctx->s, ctx->row_ptr, ctx->deg, ctx->masks, n, (T*)ctx->mt, ctx->f_eoff,
-               ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st, ctx->part, ctx->log)));
+    if (ctx->nchains > 1)
+        LAUNCH(L, KC_SELECT,
+               (k_select<T, true><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, ctx->H, ctx->s, ctx->sf, ctx->row_ptr, (const T*)ctx->ideg, ctx->masks, n,
+                   (T*)ctx->mt, ctx->f_eoff, ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st,
+                   ctx->part, ctx->log, cd.mode, cd.use, bv)));
+    else
+        LAUNCH(L, KC_SELECT,
+               (k_select<T, false><<<ctx->grid_select, kThreads, 0, ctx->stream>>>(
+                   (T*)ctx->c, ctx->H, ctx->s, ctx->sf, ctx->row_ptr, (const T*)ctx->ideg, ctx->masks, n,
+                   (T*)ctx->mt, ctx->f_eoff, ctx->f_base, (T*)ctx->f_m, ctx->chunk_row, ctx->st,
+                   ctx->part, ctx->log, cd.mode, cd.use, bv)));
+    return RLGL_OK;
+}
+
+template <typename T>
+static rlgl_status enqueue_push(Launch L) {
+    rlgl_ctx* ctx = L.ctx;
     if (ctx->has_w)
         LAUNCH(L, KC_PUSH,
                (k_push<T, true><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
@@ -233,6 +320,12 @@ static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long con
                (k_push<T, false><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
                    (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
                    ctx->chunk_row, ctx->st)));
+    return RLGL_OK;
+}
+
+template <typename T>
+static rlgl_status enqueue_pull(Launch L) {
+    rlgl_ctx* ctx = L.ctx;
     if (ctx->has_w)
         LAUNCH(L, KC_PULL,
                (k_pull<T, T, true, 0><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
@@ -246,11 +339,21 @@ static rlgl_status enqueue_iteration(Launch L, int sched, unsigned long long con
     return RLGL_OK;
 }
 
-static rlgl_status iteration(rlgl_ctx* ctx, bool capture, int sched, unsigned long long cond,
-                             int use_cond) {
+// One eager iteration of Alg. 1: stats [top-k] select push pull. Every kernel
+// checks the device state and returns at once when it has nothing to do.
+template <typename T>
+static rlgl_status enqueue_iteration(Launch L, int sched) {
+    Conds none;
+    TRY(enqueue_head<T>(L, sched, none));
+    TRY(enqueue_push<T>(L));
+    TRY(enqueue_pull<T>(L));
+    return RLGL_OK;
+}
+
+static rlgl_status iteration(rlgl_ctx* ctx, bool capture, int sched, unsigned long long, int) {
     Launch L{ctx, capture};
-    if (ctx->prec == RLGL_MIXED) return enqueue_iteration<float>(L, sched, cond, use_cond);
-    return enqueue_iteration<double>(L, sched, cond, use_cond);
+    if (ctx->prec == RLGL_MIXED) return enqueue_iteration<float>(L, sched);
+    return enqueue_iteration<double>(L, sched);
 }
 
 static rlgl_status forced_refresh(rlgl_ctx* ctx, bool apply) {
@@ -295,6 +398,11 @@ static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, dou
 }
 
 __global__ void k_begin(DevState* st) {
+    st->base_green = st->tot_green;
+    st->base_edges = st->tot_edges;
+    st->base_push = st->push_moves;
+    st->base_pull = st->pull_moves;
+    st->base_refreshes = st->refreshes;
     st->done = 0;
     st->status = 0;
     st->iters = 0;
@@ -309,12 +417,17 @@ __global__ void k_begin(DevState* st) {
 }
 
 static rlgl_status begin(rlgl_ctx* ctx, int sched, double theta, double tol, long long max_steps,
-                         int solving) {
+                         int solving, double chain_tol = -1.0) {
     fill_control(ctx, ctx->host_ctl, sched, theta, tol, max_steps, solving);
     CK(ctx, cudaMemcpyAsync(&ctx->st->ctl, ctx->host_ctl, sizeof(Control), cudaMemcpyHostToDevice,
                             ctx->stream));
     k_begin<<<1, 1, 0, ctx->stream>>>(ctx->st);
     CKL(ctx);
+    if (ctx->nchains > 1) {
+        k_bbegin<<<grid_for(ctx->nchains, kThreads, 1024), kThreads, 0, ctx->stream>>>(
+            ctx->cs, ctx->nchains, chain_tol, 0);
+        CKL(ctx);
+    }
     return RLGL_OK;
 }
 
@@ -348,7 +461,7 @@ static rlgl_status device_inclusive_scan(rlgl_ctx* ctx, long long* x, long long 
     k_scan_add<<<(unsigned)nb, kThreads, 0, ctx->stream>>>(x, m, tot);
     CKL(ctx);
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaFree(tot);
+    dfree(ctx, tot);
     return RLGL_OK;
 }
 
@@ -366,7 +479,7 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
     // result of step 0, C_1 = -M_0 (I - P).
     if (ctx->c0) {
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        cudaFree(ctx->c0);
+        dfree(ctx, ctx->c0);
         ctx->c0 = nullptr;
         drop_graphs(ctx);  // captured launches hold the C_0 pointer
     }
@@ -375,6 +488,14 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
     TRY(forced_refresh(ctx, true));
     k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
     CKL(ctx);
+    if (ctx->nchains > 1) {
+        const BatchView bv{ctx->chain_of, ctx->cs, ctx->nchains};
+        k_bbegin<<<grid_for(ctx->nchains, kThreads, 1024), kThreads, 0, ctx->stream>>>(
+            ctx->cs, ctx->nchains, -1.0, 1);
+        k_bhist_sums<<<ctx->grid_select, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, bv);
+        k_bhist_finish<<<grid_for(ctx->nchains, kThreads, 1024), kThreads, 0, ctx->stream>>>(bv, 1, nullptr);
+        CKL(ctx);
+    }
     TRY(read_state(ctx));
     return RLGL_OK;
 }
@@ -405,9 +526,12 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
         CK(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
         ctx->own_stream = true;
     }
+    TRY(device_pool(ctx));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming));
     const int cap = ctx->sms * 8 < kMaxGrid ? ctx->sms * 8 : kMaxGrid;
     ctx->grid_nodes = grid_for(n, kThreads, cap);
     ctx->grid_select = grid_for(n, kNodesPerIter, cap);
+    ctx->grid_stats = grid_for(n, kThreads * 8, ctx->sms * 2);  // about 8+ nodes per thread
     ctx->grid_push = ctx->sms * 4;
     ctx->grid_pull = ctx->sms * 8;
     const size_t cs = cash_size(ctx);
@@ -416,21 +540,22 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->col, (size_t)nnz));
     if (ctx->has_w) TRY(dalloc(ctx, &ctx->w, (size_t)nnz));
     TRY(dalloc(ctx, &ctx->s, (size_t)n));
-    TRY(dalloc(ctx, &ctx->deg, (size_t)n));
+    if (prec == RLGL_MIXED) TRY(dalloc(ctx, &ctx->sf, (size_t)n));
+    TRY(dalloc_bytes(ctx, &ctx->ideg, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->t_ptr, (size_t)n + 1));
     TRY(dalloc(ctx, &ctx->t_src, (size_t)nnz));
     if (ctx->has_w) TRY(dalloc(ctx, &ctx->t_w, (size_t)nnz));
     ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;
     TRY(dalloc(ctx, &ctx->tile_r, (size_t)ctx->ntiles + 1));
     TRY(dalloc(ctx, &ctx->tile_e, (size_t)ctx->ntiles + 1));
-    CK(ctx, cudaMalloc(&ctx->c, (size_t)n * cs));
+    TRY(dalloc_bytes(ctx, &ctx->c, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->H, (size_t)n));
-    CK(ctx, cudaMalloc(&ctx->mt, (size_t)n * cs));
+    TRY(dalloc_bytes(ctx, &ctx->mt, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->y, (size_t)n));
     TRY(dalloc(ctx, &ctx->hsrc, (size_t)n));
     TRY(dalloc(ctx, &ctx->f_eoff, (size_t)n));
     TRY(dalloc(ctx, &ctx->f_base, (size_t)n));
-    CK(ctx, cudaMalloc(&ctx->f_m, (size_t)n * cs));
+    TRY(dalloc_bytes(ctx, &ctx->f_m, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->chunk_row, (size_t)(nnz / kPushChunk + 2)));
     TRY(dalloc(ctx, &ctx->part, (size_t)(4 * kMaxGrid + 8)));
     TRY(dalloc(ctx, &ctx->err, 1));
@@ -459,7 +584,10 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
 
     const int gn = grid_for(n, kThreads, ctx->sms * 16);
     const int gw = grid_for(n * 32, kThreads, ctx->sms * 16);
-    k_row_scale<<<gn, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->w, n, ctx->s, ctx->deg);
+    k_row_scale<<<gn, kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, ctx->w, n, ctx->s, ctx->sf,
+        prec == RLGL_MIXED ? (float*)ctx->ideg : nullptr,
+        prec == RLGL_MIXED ? nullptr : (double*)ctx->ideg);
     CKL(ctx);
     // In-link (CSC) copy: counts, scan, scatter.
     long long* cursor = nullptr;
@@ -468,7 +596,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     k_count_in<<<gv, kThreads, 0, ctx->stream>>>(ctx->col, nnz, ctx->t_ptr);
     CKL(ctx);
     rlgl_status sc = device_inclusive_scan(ctx, ctx->t_ptr, n + 1);
-    if (sc != RLGL_OK) { cudaFree(cursor); return sc; }
+    if (sc != RLGL_OK) { dfree(ctx, cursor); return sc; }
     CK(ctx, cudaMemcpyAsync(cursor, ctx->t_ptr, ((size_t)n + 1) * sizeof(long long),
                             cudaMemcpyDeviceToDevice, ctx->stream));
     k_scatter_in<<<gw, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->col, ctx->w, n, cursor,
@@ -479,7 +607,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
                                                       ctx->tile_e);
     CKL(ctx);
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaFree(cursor);
+    dfree(ctx, cursor);
     return RLGL_OK;
 }
 
@@ -572,15 +700,117 @@ rlgl_status rlgl_create_from_state(int64_t n, int64_t nnz, const int64_t* row_pt
     return RLGL_OK;
 }
 
+rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t n, int64_t nnz,
+                              const int64_t* row_ptr, const int32_t* col, const float* w,
+                              rlgl_precision prec, rlgl_memspace src, void* stream, rlgl_ctx** out) {
+    if (!out) return fail(nullptr, RLGL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_chains < 1 || n_chains > (1ll << 30) || !node_ptr)
+        return fail(nullptr, RLGL_EINVAL, "n_chains out of range or node_ptr NULL");
+    std::vector<int64_t> np((size_t)n_chains + 1);
+    if (src == RLGL_DEVICE) {
+        if (cudaMemcpy(np.data(), node_ptr, np.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(nullptr, RLGL_ECUDA, "reading node_ptr failed");
+    } else {
+        memcpy(np.data(), node_ptr, np.size() * sizeof(int64_t));
+    }
+    if (np[0] != 0 || np[(size_t)n_chains] != n) return fail(nullptr, RLGL_EINVAL, "node_ptr must run from 0 to n");
+    for (int64_t k = 0; k < n_chains; ++k)
+        if (np[(size_t)k + 1] <= np[(size_t)k]) return fail(nullptr, RLGL_EINVAL, "chain %lld is empty", (long long)k);
+    rlgl_ctx* ctx = nullptr;
+    rlgl_status s = create_common(n, nnz, row_ptr, col, w, prec, src, stream, &ctx);
+    auto bail = [&](rlgl_status st) {
+        if (ctx) snprintf(g_thread_err, sizeof g_thread_err, "%s", ctx->err_msg);
+        rlgl_destroy(ctx);
+        return st;
+    };
+    if (s != RLGL_OK) return bail(s);
+    ctx->nchains = (int)n_chains;
+    ctx->node_ptr_h = np;
+    if ((s = dalloc(ctx, &ctx->node_ptr, (size_t)n_chains + 1)) != RLGL_OK) return bail(s);
+    if ((s = dalloc(ctx, &ctx->chain_of, (size_t)n)) != RLGL_OK) return bail(s);
+    if ((s = dalloc(ctx, &ctx->cs, (size_t)n_chains)) != RLGL_OK) return bail(s);
+    if ((s = dalloc(ctx, &ctx->bsums, 2 * (size_t)n_chains)) != RLGL_OK) return bail(s);
+    std::vector<ChainState> cs((size_t)n_chains);
+    memset(cs.data(), 0, cs.size() * sizeof(ChainState));
+    std::vector<double> m0((size_t)n);
+    for (int64_t k = 0; k < n_chains; ++k) {
+        cs[(size_t)k].n = np[(size_t)k + 1] - np[(size_t)k];
+        cs[(size_t)k].tol = 1e-12;
+        for (int64_t i = np[(size_t)k]; i < np[(size_t)k + 1]; ++i) m0[(size_t)i] = 1.0 / (double)cs[(size_t)k].n;
+    }
+    if (cudaMemcpyAsync(ctx->node_ptr, np.data(), np.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->cs, cs.data(), cs.size() * sizeof(ChainState), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, RLGL_ECUDA, "upload of chain data failed"));
+    k_chain_of<<<grid_for(n, kThreads, ctx->sms * 16), kThreads, 0, ctx->stream>>>(ctx->node_ptr, (int)n_chains, n,
+                                                                                  ctx->chain_of);
+    unsigned int zero = 0, err = 0;
+    if (cudaMemcpyAsync(ctx->err, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, RLGL_ECUDA, "memset failed"));
+    k_check_blocks<<<grid_for(n * 32, kThreads, ctx->sms * 16), kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, ctx->col, ctx->chain_of, n, ctx->err);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&err, ctx->err, sizeof err, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return bail(fail(ctx, RLGL_ECUDA, "chain map failed"));
+    if (err) return bail(fail(ctx, RLGL_EINVAL, "an edge leaves its chain: the CSR must be block-diagonal"));
+    if ((s = set_step0(ctx, m0.data(), RLGL_HOST)) != RLGL_OK) return bail(s);
+    *out = ctx;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_batch_set_tol(rlgl_ctx* ctx, const double* tol) {
+    if (!ctx || !tol) return fail(ctx, RLGL_EINVAL, "NULL argument");
+    if (ctx->nchains < 2) return fail(ctx, RLGL_EINVAL, "not a batch");
+    std::vector<ChainState> cs((size_t)ctx->nchains);
+    CK(ctx, cudaMemcpyAsync(cs.data(), ctx->cs, cs.size() * sizeof(ChainState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->nchains; ++k) {
+        if (!(tol[k] >= 0.0)) return fail(ctx, RLGL_EINVAL, "tol[%d] < 0", k);
+        cs[(size_t)k].tol = tol[k];
+    }
+    CK(ctx, cudaMemcpyAsync(ctx->cs, cs.data(), cs.size() * sizeof(ChainState), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_batch_chains(rlgl_ctx* ctx, int32_t* status, int64_t* moves, double* resid) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (ctx->nchains < 2) return fail(ctx, RLGL_EINVAL, "not a batch");
+    std::vector<ChainState> cs((size_t)ctx->nchains);
+    CK(ctx, cudaMemcpyAsync(cs.data(), ctx->cs, cs.size() * sizeof(ChainState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->nchains; ++k) {
+        const ChainState& c = cs[(size_t)k];
+        if (status) status[k] = c.done ? c.status : -1;
+        if (moves) moves[k] = c.moves;
+        if (resid) resid[k] = c.hsum != 0.0 ? c.l1 / fabs(c.hsum) : INFINITY;
+    }
+    return RLGL_OK;
+}
+
 rlgl_status rlgl_reset(rlgl_ctx* ctx, const double* m0, rlgl_memspace src) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
+    if (!m0 && ctx->nchains > 1) {
+        // uniform within each chain
+        std::vector<double> u((size_t)ctx->n);
+        for (int k = 0; k < ctx->nchains; ++k) {
+            const int64_t a = ctx->node_ptr_h[(size_t)k], b = ctx->node_ptr_h[(size_t)k + 1];
+            for (int64_t i = a; i < b; ++i) u[(size_t)i] = 1.0 / (double)(b - a);
+        }
+        return set_step0(ctx, u.data(), RLGL_HOST);
+    }
     return set_step0(ctx, m0, src);
 }
 
 rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period, rlgl_memspace src) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     if (!masks || period < 1) return fail(ctx, RLGL_EINVAL, "masks is NULL or period < 1");
-    if (ctx->masks) { cudaFree(ctx->masks); ctx->masks = nullptr; }
+    if (ctx->masks) { dfree(ctx, ctx->masks); ctx->masks = nullptr; }
     TRY(dalloc(ctx, &ctx->masks, (size_t)(period * ctx->n)));
     TRY(upload(ctx, ctx->masks, masks, (size_t)(period * ctx->n), src));
     ctx->n_masks = period;
@@ -594,12 +824,15 @@ rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period, 
 static rlgl_status check_sched(rlgl_ctx* ctx, rlgl_schedule sched) {
     if (sched < RLGL_ALL_GREEN || sched > RLGL_LINK_THRESHOLD)
         return fail(ctx, RLGL_EINVAL, "bad schedule %d", (int)sched);
+    if (sched == RLGL_TOPFRAC && ctx->nchains > 1)
+        return fail(ctx, RLGL_EINVAL, "RLGL_TOPFRAC is not available for a batch of chains");
     if (sched == RLGL_MASK && !ctx->masks) return fail(ctx, RLGL_EINVAL, "RLGL_MASK needs rlgl_set_masks");
     return RLGL_OK;
 }
 
 rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_step_info* info) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     TRY(check_sched(ctx, sched));
     TRY(begin(ctx, sched, theta, 0.0, 1, 0));
     TRY(iteration(ctx, false, sched, 0ull, 0));
@@ -614,11 +847,13 @@ rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_ste
         TRY(begin(ctx, sched, theta, 0.0, 1, 0));
         Launch L{ctx, false};
         if (ctx->prec == RLGL_MIXED)
-            LAUNCH(L, KC_STATS, (k_stats<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
-                                    (const float*)ctx->c, ctx->deg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0)));
+            LAUNCH(L, KC_STATS, (k_stats<float><<<ctx->grid_stats, kThreads, 0, ctx->stream>>>(
+                                    (const float*)ctx->c, (const float*)ctx->ideg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0ull, 0,
+                                    vec_aligned(ctx))));
         else
-            LAUNCH(L, KC_STATS, (k_stats<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
-                                    (const double*)ctx->c, ctx->deg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0)));
+            LAUNCH(L, KC_STATS, (k_stats<double><<<ctx->grid_stats, kThreads, 0, ctx->stream>>>(
+                                    (const double*)ctx->c, (const double*)ctx->ideg, (int)ctx->n, ctx->st, ctx->part, 0ull, 0ull, 0,
+                                    vec_aligned(ctx))));
         TRY(read_state(ctx));
         info->l1_cash = h->l1;
         info->sum_cash = h->sum;
@@ -627,60 +862,135 @@ rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_ste
     return RLGL_OK;
 }
 
-static rlgl_status build_graph(rlgl_ctx* ctx, int sched) {
-    cudaGraph_t g = nullptr;
-    CK(ctx, cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle handle;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, g, 1u, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+}  // extern "C"
+
+// Captures what `body` enqueues into graph g after the nodes deps; returns
+// the leaf nodes of the capture in *leaves (when given).
+template <typename F>
+static rlgl_status capture_into(rlgl_ctx* ctx, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                F&& body, std::vector<cudaGraphNode_t>* leaves) {
+    CK(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, g, deps, nullptr, nd,
+                                          cudaStreamCaptureModeRelaxed));
+    rlgl_status s = body();
+    if (s == RLGL_OK && leaves) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* d = nullptr;
+        size_t n = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, nullptr, &d, nullptr, &n);
+        if (e == cudaSuccess) leaves->assign(d, d + n);
+        else s = fail(ctx, RLGL_ECUDA, "cudaStreamGetCaptureInfo: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &out);
+    if (s != RLGL_OK) return s;
+    CK(ctx, e);
+    return RLGL_OK;
+}
+
+// Adds a conditional node (type, `size` bodies) to g after deps.
+static rlgl_status add_conditional(rlgl_ctx* ctx, cudaGraph_t g, const cudaGraphNode_t* deps,
+                                   size_t nd, cudaGraphConditionalHandle h,
+                                   cudaGraphConditionalNodeType type, unsigned size,
+                                   cudaGraphNode_t* node, cudaGraph_t* bodies) {
     // cudaGraphNodeParams holds a union without a default constructor:
     // build it in zeroed storage.
     alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
     memset(pbuf, 0, sizeof pbuf);
     cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(pbuf);
     p->type = cudaGraphNodeTypeConditional;
-    p->conditional.handle = handle;
-    p->conditional.type = cudaGraphCondTypeWhile;
-    p->conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, p);
-    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
-    cudaGraph_t body = p->conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
-    rlgl_status s = iteration(ctx, true, sched, (unsigned long long)handle, 1);
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(ctx->stream, &captured);
-    if (s != RLGL_OK) { cudaGraphDestroy(g); return s; }
-    if (e != cudaSuccess) { cudaGraphDestroy(g); CK(ctx, e); }
+    p->conditional.handle = h;
+    p->conditional.type = type;
+    p->conditional.size = size;
+    CK(ctx, cudaGraphAddNode(node, g, deps, nullptr, nd, p));
+    for (unsigned k = 0; k < size; ++k) bodies[k] = p->conditional.phGraph_out[k];
+    return RLGL_OK;
+}
+
+// The solve graph: WHILE(loop) { [IF(refresh) {re-derive C}] stats [top-k]
+// select IF/ELSE(mode) {pull} {push} }. k_stats ends the loop and requests
+// the refresh of the next iteration; k_select picks pull or push.
+template <typename T>
+static rlgl_status build_graph_t(rlgl_ctx* ctx, int sched, cudaGraph_t g) {
+    Conds cd;
+    cd.use = 1;
+    cudaGraphConditionalHandle hw;
+    CK(ctx, cudaGraphConditionalHandleCreate(&hw, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    TRY(add_conditional(ctx, g, nullptr, 0, hw, cudaGraphCondTypeWhile, 1, &wnode, &body));
+    cd.loop = (unsigned long long)hw;
+    cudaGraphConditionalHandle hr = 0, hm;
+    CK(ctx, cudaGraphConditionalHandleCreate(&hm, body, 0u, cudaGraphCondAssignDefault));
+    cd.mode = (unsigned long long)hm;
+    std::vector<cudaGraphNode_t> deps;
+    Launch L{ctx, true};
+    if (ctx->prec == RLGL_MIXED) {
+        CK(ctx, cudaGraphConditionalHandleCreate(&hr, body, 0u, cudaGraphCondAssignDefault));
+        cd.refresh = (unsigned long long)hr;
+        cudaGraphNode_t rnode;
+        cudaGraph_t rbody;
+        TRY(add_conditional(ctx, body, nullptr, 0, hr, cudaGraphCondTypeIf, 1, &rnode, &rbody));
+        TRY(capture_into(ctx, rbody, nullptr, 0, [&] { return enqueue_refresh<T>(L); }, nullptr));
+        deps.push_back(rnode);
+    }
+    std::vector<cudaGraphNode_t> leaves;
+    TRY(capture_into(ctx, body, deps.data(), deps.size(),
+                     [&] { return enqueue_head<T>(L, sched, cd); }, &leaves));
+    cudaGraphNode_t mnode;
+    cudaGraph_t mbody[2];
+    TRY(add_conditional(ctx, body, leaves.data(), leaves.size(), hm, cudaGraphCondTypeIf, 2, &mnode,
+                        mbody));
+    TRY(capture_into(ctx, mbody[0], nullptr, 0, [&] { return enqueue_pull<T>(L); }, nullptr));
+    TRY(capture_into(ctx, mbody[1], nullptr, 0, [&] { return enqueue_push<T>(L); }, nullptr));
+    return RLGL_OK;
+}
+
+static rlgl_status build_graph(rlgl_ctx* ctx, int sched) {
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaGraphCreate(&g, 0));
+    rlgl_status s = (ctx->prec == RLGL_MIXED) ? build_graph_t<float>(ctx, sched, g)
+                                              : build_graph_t<double>(ctx, sched, g);
+    if (s != RLGL_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     CK(ctx, e);
     ctx->graph[sched] = exec;
     return RLGL_OK;
 }
 
-rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
-                       int64_t max_steps, rlgl_solve_info* info) {
-    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+extern "C" {
+
+static rlgl_status solve_launch(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                                int64_t max_steps) {
     TRY(check_sched(ctx, sched));
     if (max_steps < 1 || max_steps > 100000000ll) return fail(ctx, RLGL_EINVAL, "max_steps out of range");
-    if (!(tol >= 0.0)) return fail(ctx, RLGL_EINVAL, "tol must be >= 0");
+    const bool batch_tols = ctx->nchains > 1 && tol < 0.0;  // per-chain tolerances
+    if (!(tol >= 0.0) && !batch_tols) return fail(ctx, RLGL_EINVAL, "tol must be >= 0");
     if (!ctx->graph[sched]) TRY(build_graph(ctx, sched));
-    TRY(read_state(ctx));
-    DevState before = *ctx->host_st;
-    TRY(begin(ctx, sched, theta, tol, max_steps, 1));
+    TRY(begin(ctx, sched, theta, batch_tols ? 0.0 : tol, max_steps, 1, batch_tols ? -1.0 : tol));
     CK(ctx, cudaGraphLaunch(ctx->graph[sched], ctx->stream));
-    TRY(read_state(ctx));
-    DevState* h = ctx->host_st;
+    CK(ctx, cudaMemcpyAsync(ctx->host_st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->done_ev, ctx->stream));
+    ctx->pending = true;
+    ctx->pending_max = max_steps;
+    return RLGL_OK;
+}
+
+static rlgl_status solve_finish(rlgl_ctx* ctx, rlgl_solve_info* info) {
+    ctx->pending = false;
+    CK(ctx, cudaEventSynchronize(ctx->done_ev));
+    const DevState* h = ctx->host_st;
     if (info) {
         info->moves = h->solve_moves;
-        info->edges_pushed = h->tot_edges - before.tot_edges;
-        info->green_total = h->tot_green - before.tot_green;
-        info->push_moves = h->push_moves - before.push_moves;
-        info->pull_moves = h->pull_moves - before.pull_moves;
-        info->refreshes = h->refreshes - before.refreshes;
+        info->edges_pushed = h->tot_edges - h->base_edges;
+        info->green_total = h->tot_green - h->base_green;
+        info->push_moves = h->push_moves - h->base_push;
+        info->pull_moves = h->pull_moves - h->base_pull;
+        info->refreshes = h->refreshes - h->base_refreshes;
         info->iterations = h->iters;
         info->resid = h->hsum != 0.0 ? h->l1 / fabs(h->hsum) : INFINITY;
         info->l1_cash = h->l1;
@@ -689,15 +999,77 @@ rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double 
     switch (h->status) {
         case ST_OK: return RLGL_OK;
         case ST_DEGENERATE: return fail(ctx, RLGL_EDEGENERATE, "degenerate history: |H 1| ~ 0");
-        case ST_NOCONV: return fail(ctx, RLGL_ENOCONV, "no convergence in %lld moves", (long long)max_steps);
+        case ST_NOCONV: return fail(ctx, RLGL_ENOCONV, "no convergence in %lld moves", ctx->pending_max);
         case ST_TIMEOUT: return fail(ctx, RLGL_ETIMEOUT, "solve exceeded its time limit");
         default: return fail(ctx, RLGL_ECUDA, "unexpected device status %d", h->status);
     }
 }
 
+rlgl_status rlgl_solve(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                       int64_t max_steps, rlgl_solve_info* info) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
+    TRY(solve_launch(ctx, sched, theta, tol, max_steps));
+    return solve_finish(ctx, info);
+}
+
+rlgl_status rlgl_solve_async(rlgl_ctx* ctx, rlgl_schedule sched, double theta, double tol,
+                             int64_t max_steps) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
+    return solve_launch(ctx, sched, theta, tol, max_steps);
+}
+
+rlgl_status rlgl_query(rlgl_ctx* ctx, int32_t* finished) {
+    if (!ctx || !finished) return fail(ctx, RLGL_EINVAL, "NULL argument");
+    if (!ctx->pending) {
+        *finished = 1;
+        return RLGL_OK;
+    }
+    cudaError_t e = cudaEventQuery(ctx->done_ev);
+    if (e == cudaErrorNotReady) {
+        *finished = 0;
+        return RLGL_OK;
+    }
+    CK(ctx, e);
+    *finished = 1;
+    return RLGL_OK;
+}
+
+rlgl_status rlgl_wait(rlgl_ctx* ctx, rlgl_solve_info* info) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (!ctx->pending) return fail(ctx, RLGL_EINVAL, "no asynchronous solve to wait for");
+    return solve_finish(ctx, info);
+}
+
+static rlgl_status batch_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
+    const int n = (int)ctx->n;
+    const BatchView bv{ctx->chain_of, ctx->cs, ctx->nchains};
+    k_bhist_sums<<<ctx->grid_select, kThreads, 0, ctx->stream>>>(ctx->H, n, bv);
+    k_bhist_finish<<<grid_for(ctx->nchains, kThreads, 1024), kThreads, 0, ctx->stream>>>(bv, 0, ctx->bsums);
+    CKL(ctx);
+    std::vector<double> sums(2 * (size_t)ctx->nchains);
+    CK(ctx, cudaMemcpyAsync(sums.data(), ctx->bsums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    int bad = -1;
+    for (int k = 0; k < ctx->nchains; ++k)
+        if (!(fabs(sums[2 * k]) > 1e-12 * sums[2 * k + 1]) || sums[2 * k + 1] == 0.0) { bad = k; break; }
+    if (bad >= 0) return fail(ctx, RLGL_EDEGENERATE, "degenerate history in chain %d", bad);
+    double* out = (dst == RLGL_HOST) ? ctx->hsrc : pi_out;
+    k_bscale<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->chain_of, ctx->bsums, out);
+    CKL(ctx);
+    if (dst == RLGL_HOST)
+        CK(ctx, cudaMemcpyAsync(pi_out, out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLGL_OK;
+}
+
 rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
     if (!pi_out) return fail(ctx, RLGL_EINVAL, "pi_out is NULL");
+    NOT_PENDING(ctx);
+    if (ctx->nchains > 1) return batch_estimate(ctx, pi_out, dst);
     const int n = (int)ctx->n;
     k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->st, ctx->part, 0);
     CKL(ctx);
@@ -718,6 +1090,7 @@ rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
 
 rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace dst) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     const int n = (int)ctx->n;
     if (c) {
         double* out = (dst == RLGL_HOST) ? ctx->hsrc : c;
@@ -739,6 +1112,7 @@ rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace ds
 
 rlgl_status rlgl_invariant_residual(rlgl_ctx* ctx, double* l1) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     TRY(forced_refresh(ctx, false));
     TRY(read_state(ctx));
     if (l1) *l1 = ctx->host_st->resid_l1;
@@ -747,6 +1121,7 @@ rlgl_status rlgl_invariant_residual(rlgl_ctx* ctx, double* l1) {
 
 rlgl_status rlgl_refresh(rlgl_ctx* ctx, double* l1_before) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     TRY(forced_refresh(ctx, true));
     TRY(read_state(ctx));
     if (l1_before) *l1_before = ctx->host_st->resid_l1;
@@ -808,6 +1183,7 @@ void CUDART_CB gate_wait(void* p) {
 
 rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
     TRY(check_sched(ctx, sched));
     if (moves < 0) return fail(ctx, RLGL_EINVAL, "moves < 0");
     const int prev = ctx->profiling;
@@ -845,6 +1221,23 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
     return RLGL_OK;
 }
 
+int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision prec,
+                       int64_t n_chains) {
+    if (n < 1 || nnz < 1) return -1;
+    const int64_t cs = prec == RLGL_MIXED ? 4 : 8;
+    const int64_t ntiles = (n + nnz + kMpItems - 1) / kMpItems;
+    int64_t b = 0;
+    b += 2 * ((n + 1) * 8 + nnz * 4 + (weighted ? nnz * 4 : 0));  // CSR and CSC
+    b += n * (8 + (prec == RLGL_MIXED ? 4 : 0) + cs);                // s, sf, 1/deg
+    b += 2 * (ntiles + 1) * 8;                                       // merge-path tiles
+    b += n * (cs + 8 + cs + 8 + 8 + 8 + 8 + cs);                     // c H mt y hsrc f_eoff f_base f_m
+    b += (nnz / kPushChunk + 2) * 4;                                 // chunk index
+    b += (4 * kMaxGrid + 8) * 8 + 8 + (int64_t)kLogCap * (int64_t)sizeof(MoveRecord) +
+         (int64_t)sizeof(DevState);
+    if (n_chains > 1) b += (n_chains + 1) * 8 + n * 4 + n_chains * ((int64_t)sizeof(ChainState) + 16);
+    return b;
+}
+
 void* rlgl_stream(const rlgl_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 const char* rlgl_last_error(const rlgl_ctx* ctx) { return ctx ? ctx->err_msg : g_thread_err; }
@@ -869,12 +1262,15 @@ void rlgl_destroy(rlgl_ctx* ctx) {
     for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto& g : ctx->graph)
         if (g) cudaGraphExecDestroy(g);
-    void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->deg, ctx->t_ptr, ctx->t_src, ctx->t_w,
+    void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
-                   ctx->err, ctx->log, ctx->st};
+                   ctx->err, ctx->log, ctx->st, ctx->node_ptr, ctx->chain_of, ctx->cs,
+                   ctx->bsums};
     for (void* p : dev)
-        if (p) cudaFree(p);
+        dfree(ctx, p);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     if (ctx->host_st) cudaFreeHost(ctx->host_st);
     if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -23,6 +23,7 @@
 // can hang.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace rlgl {
@@ -43,6 +44,23 @@ struct MoveRecord {                   // layout of rlgl_move_record
     long long move, green, edges;
     int mode, pad;
     double theta, l1, hsum;
+};
+
+// Per-chain state of a batch (many independent chains on one block-diagonal
+// CSR). acc[] are atomic accumulators, zero at rest: 0 ||C||_1, 1 sum C,
+// 2 sum v^r, 3 sum of moved cash, 4 sum |moved cash|, 5 sum H, 6 sum |H|.
+struct ChainState {
+    double acc[7];
+    double l1, sum, sumr, theta, hsum, habs, tol;
+    long long n, moves;
+    float theta_f;
+    int done, status, pad;
+};
+
+struct BatchView {
+    const int* chain_of;   // node -> chain
+    ChainState* cs;
+    int nchains;
 };
 
 enum Mode : int { MODE_NONE = 0, MODE_PUSH = 1, MODE_PULL = 2 };
@@ -80,6 +98,8 @@ struct DevState {
     Control ctl;
     // statistics of the current cash (written by the stats kernel)
     double l1, sum, sumr, theta;
+    float theta_f;           // FP32 threshold of the MIXED path (see set_theta)
+    float pad_f;
     double hsum, habs;       // H 1 (kept incrementally) and an upper bound of sum |H|
     double l1_refresh;       // ||C||_1 right after the last re-derivation
     double resid_l1;         // residual measured by the last refresh pass
@@ -89,6 +109,7 @@ struct DevState {
     long long moves;         // moves since step 0 (t - 1)
     long long solve_moves, iters, mask_cursor;
     long long tot_green, tot_edges, push_moves, pull_moves, refreshes;
+    long long base_green, base_edges, base_push, base_pull, base_refreshes;  // at solve start
     unsigned long long t_start;
     unsigned long long reserve;   // packed frontier reservation
     unsigned int ticket;
@@ -213,11 +234,20 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nb, doub
 
 // ------------------------------------------------------- stats + control
 
+// Stores theta and its FP32 form for the MIXED path. For the |C| tests the
+// FP32 threshold is theta rounded up, so that for an FP32 cash value v,
+// |v| >= theta_f exactly when |v| >= theta; the per-link test compares an
+// FP32 product and uses theta rounded to nearest.
+__device__ __forceinline__ void set_theta(DevState* st, double theta, int sched) {
+    st->theta = theta;
+    st->theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+}
+
 // Decides, after the cash statistics of C_t are known, whether the solve
 // stops (Alg. 1 line (7): t >= 2 and ||C_t||_1 / |H_t 1| < tol) and sets the
 // threshold for this move. Runs in one thread.
-__device__ void control_after_stats(DevState* st, unsigned long long cond_handle, int use_cond,
-                                    int n) {
+__device__ void control_after_stats(DevState* st, unsigned long long cond_handle,
+                                    unsigned long long cond_refresh, int use_cond, int n) {
     const Control& c = st->ctl;
     st->skip_move = 0;
     if (c.solving) {
@@ -247,11 +277,16 @@ __device__ void control_after_stats(DevState* st, unsigned long long cond_handle
         if (stop >= 0) {
             st->done = 1;
             st->status = stop;
-            if (use_cond) cudaGraphSetConditional(cond_handle, 0u);
+            if (use_cond) {
+                cudaGraphSetConditional(cond_handle, 0u);
+                if (c.mixed) cudaGraphSetConditional(cond_refresh, 0u);
+            }
             return;
         }
         if (c.mixed && c.refresh_factor > 0.0 && st->l1 < c.refresh_factor * st->l1_refresh)
             st->want_refresh = 1;  // applied at the start of the next iteration
+        // the refresh of the next iteration runs only when requested
+        if (use_cond && c.mixed) cudaGraphSetConditional(cond_refresh, st->want_refresh ? 1u : 0u);
     }
     // Threshold of this move.
     int sched = c.sched;
@@ -259,10 +294,11 @@ __device__ void control_after_stats(DevState* st, unsigned long long cond_handle
     st->mode = MODE_NONE;
     if (sched == SCHED_THRESHOLD || sched == SCHED_LINK) {
         if (c.theta_arg > 0.0) {
-            st->theta = c.theta_arg;
+            set_theta(st, c.theta_arg, sched);
         } else {
             double mean = st->sumr / (double)n;
-            st->theta = (c.r == 1) ? c.theta_scale * mean : c.theta_scale * pow(mean, 1.0 / c.r);
+            set_theta(st, (c.r == 1) ? c.theta_scale * mean : c.theta_scale * pow(mean, 1.0 / c.r),
+                      sched);
         }
     } else if (sched == SCHED_TOPFRAC) {
         double f = (c.theta_arg > 0.0 && c.theta_arg <= 1.0) ? c.theta_arg : c.top_frac;
@@ -271,45 +307,258 @@ __device__ void control_after_stats(DevState* st, unsigned long long cond_handle
         if (k > n) k = n;
         st->tk_remain = k;
         st->tk_prefix = 0ull;
-        st->theta = 0.0;
+        set_theta(st, 0.0, sched);
     } else {
-        st->theta = 0.0;
+        set_theta(st, 0.0, sched);
     }
 }
 
-// ||C||_1, sum C, sum |C|^r (FP64) of the current cash, then control.
+// Chain of the nodes [it0, it0 + kNodesPerIter) when one chain holds them
+// all (chain ids grow with node ids), else -1.
+__device__ __forceinline__ int iter_chain(const BatchView& bv, long long it0, int n) {
+    long long last = it0 + kNodesPerIter - 1;
+    if (last >= n) last = n - 1;
+    int a = bv.chain_of[it0], b = bv.chain_of[last];
+    return a == b ? a : -1;
+}
+
+// Adds the block's values to chain ch's accumulators (all threads call it;
+// ch is the same in every thread).
+template <int K, typename V>
+__device__ __forceinline__ void block_chain_add(ChainState* cs, int ch, const int* ks, const V* v,
+                                                V* scratch) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        V t = block_sum(v[k], scratch);
+        if (threadIdx.x == 0 && t != V(0)) atomicAdd(&cs[ch].acc[ks[k]], (double)t);
+    }
+}
+
+__device__ __forceinline__ int status_rank(int st) {
+    return st == ST_OK ? 0 : st == ST_NOCONV ? 1 : st == ST_DEGENERATE ? 2 : 3;
+}
+__device__ __forceinline__ int rank_status(int r) {
+    return r == 0 ? ST_OK : r == 1 ? ST_NOCONV : r == 2 ? ST_DEGENERATE : ST_TIMEOUT;
+}
+
+// The batch form of control_after_stats, run by every thread of the last
+// block: each chain takes its statistics from its accumulators, is tested
+// for its own stop (Alg. 1 line (7) with its own tolerance) and gets its own
+// threshold; the loop ends when no chain is left running.
+__device__ void batch_control(DevState* st, const BatchView& bv, unsigned long long cond_handle,
+                              unsigned long long cond_refresh, int use_cond) {
+    __shared__ int s_active, s_need, s_worst, s_timeout;
+    __shared__ double scratch[32];
+    const Control& c = st->ctl;
+    if (threadIdx.x == 0) {
+        s_active = 0;
+        s_need = 0;
+        s_worst = 0;
+        st->skip_move = 0;
+        int to = 0;
+        if (c.solving) {
+            unsigned long long now = globaltimer();
+            if (st->iters == 0) st->t_start = now;
+            st->iters++;
+            to = ((double)(now - st->t_start) > c.time_limit_ns || st->iters > c.max_iters) ? 1 : 0;
+        }
+        s_timeout = to;
+    }
+    __syncthreads();
+    int sched = c.sched;
+    if (c.safety_every > 0 && ((st->solve_moves + 1) % c.safety_every) == 0) sched = SCHED_ALL_GREEN;
+    const bool link = c.sched == SCHED_LINK;
+    const int r = c.r;
+    double l1sum = 0.0, ssum = 0.0;
+    for (int k = threadIdx.x; k < bv.nchains; k += blockDim.x) {
+        ChainState* ch = bv.cs + k;
+        const double a = __ldcg(&ch->acc[0]), sm = __ldcg(&ch->acc[1]), sr = __ldcg(&ch->acc[2]);
+        ch->acc[0] = 0.0;
+        ch->acc[1] = 0.0;
+        ch->acc[2] = 0.0;
+        ch->l1 = a;
+        ch->sum = sm;
+        ch->sumr = (r == 1 && !link) ? a : sr;
+        l1sum += a;
+        ssum += sm;
+        if (ch->done) continue;
+        if (c.solving) {
+            const double hs = ch->hsum;
+            const bool degenerate = !(fabs(hs) > 1e-12 * ch->habs) || ch->habs == 0.0;
+            const bool converged = ch->moves >= 1 && a / fabs(hs) < ch->tol;
+            int stop = -1;
+            if (degenerate) stop = ST_DEGENERATE;
+            else if (converged) {
+                if (c.mixed && !st->fresh) atomicOr(&s_need, 1);
+                else stop = ST_OK;
+            } else if (st->solve_moves >= c.max_steps) stop = ST_NOCONV;
+            else if (s_timeout) stop = ST_TIMEOUT;
+            if (stop >= 0) {
+                ch->done = 1;
+                ch->status = stop;
+                atomicMax(&s_worst, status_rank(stop));
+                continue;
+            }
+        }
+        double th = 0.0;
+        if (sched == SCHED_THRESHOLD || sched == SCHED_LINK) {
+            const double mean = ch->sumr / (double)ch->n;
+            th = c.theta_arg > 0.0 ? c.theta_arg
+                                   : (r == 1 ? c.theta_scale * mean : c.theta_scale * pow(mean, 1.0 / r));
+        }
+        ch->theta = th;
+        ch->theta_f = (sched == SCHED_LINK) ? __double2float_rn(th) : __double2float_ru(th);
+        atomicAdd(&s_active, 1);
+    }
+    l1sum = block_sum(l1sum, scratch);
+    ssum = block_sum(ssum, scratch);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->l1 = l1sum;
+        st->sum = ssum;
+        st->sumr = 0.0;
+        st->theta = 0.0;
+        st->mode = MODE_NONE;
+        if (c.solving) {
+            if (s_active == 0) {
+                st->done = 1;
+                st->status = rank_status(s_worst);
+                if (use_cond) {
+                    cudaGraphSetConditional(cond_handle, 0u);
+                    if (c.mixed) cudaGraphSetConditional(cond_refresh, 0u);
+                }
+                return;
+            }
+            if (s_need) {
+                st->want_refresh = 1;
+                st->skip_move = 1;
+            } else if (c.mixed && c.refresh_factor > 0.0 && st->l1 < c.refresh_factor * st->l1_refresh) {
+                st->want_refresh = 1;
+            }
+            if (use_cond && c.mixed) cudaGraphSetConditional(cond_refresh, st->want_refresh ? 1u : 0u);
+        }
+    }
+}
+
+// Batch statistics: per chain ||C||_1, sum C, sum v^r, accumulated per
+// block-iteration (one atomic per statistic when the iteration lies inside
+// one chain), then batch_control.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bstats(const T* __restrict__ c,
+                                                     const T* __restrict__ ideg, int n,
+                                                     DevState* st, BatchView bv,
+                                                     unsigned long long cond_handle,
+                                                     unsigned long long cond_refresh, int use_cond) {
+    if (st->done) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond_handle, 0u);
+        return;
+    }
+    __shared__ T tscratch[32];
+    const int r = st->ctl.r;
+    const bool link = st->ctl.sched == SCHED_LINK;
+    const int ks[3] = {0, 1, 2};
+    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+         it0 += (long long)gridDim.x * kNodesPerIter) {
+        const int uni = iter_chain(bv, it0, n);
+        T a = T(0), sm = T(0), pr = T(0);
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            if (i >= n) continue;
+            const T v = c[i];
+            const T av = fabs(v);
+            const T tv = link ? av * ideg[i] : av;
+            const T pv = (link && r == 1) ? tv : (r == 2 ? tv * tv : (r > 2 ? pow(tv, (T)r) : T(0)));
+            if (uni >= 0) {
+                a += av;
+                sm += v;
+                pr += pv;
+            } else {
+                const int ch = bv.chain_of[i];
+                atomicAdd(&bv.cs[ch].acc[0], (double)av);
+                atomicAdd(&bv.cs[ch].acc[1], (double)v);
+                if (pv != T(0)) atomicAdd(&bv.cs[ch].acc[2], (double)pv);
+            }
+        }
+        if (uni >= 0) {
+            const T vals[3] = {a, sm, pr};
+            block_chain_add<3>(bv.cs, uni, ks, vals, tscratch);
+        }
+    }
+    if (!last_block(&st->ticket)) return;
+    batch_control(st, bv, cond_handle, cond_refresh, use_cond);
+}
+
+// ||C||_1, sum C and sum v^r (v = |C_i|, or |C_i| / d_i for the per-link
+// test) of the current cash, then control. Each thread sums its nodes in the
+// cash type (FP32 on the MIXED path: GB300's FP64 rate is low) and the
+// per-thread sums are combined in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_stats(const T* __restrict__ c,
-                                                    const int* __restrict__ deg, int n,
+                                                    const T* __restrict__ ideg, int n,
                                                     DevState* st, double* part,
-                                                    unsigned long long cond_handle, int use_cond) {
+                                                    unsigned long long cond_handle,
+                                                    unsigned long long cond_refresh, int use_cond,
+                                                    int vec_ok) {
     if (st->done) {
         // Never leave the device loop running once the solve is over.
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond_handle, 0u);
         return;
     }
-    __shared__ double scratch[32];
-    double a = 0.0, s = 0.0, pr = 0.0;
+    T a = T(0), s = T(0), pr = T(0);
     const int r = st->ctl.r;
     const bool link = st->ctl.sched == SCHED_LINK;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v = (double)c[i];
-        double av = fabs(v);
+    auto add = [&](T v, T idg) {
+        const T av = fabs(v);
         a += av;
         s += v;
-        // threshold statistic: |C_i| (THRESHOLD) or |C_i| / d_i (LINK)
-        double tv = link ? av / (double)deg[i] : av;
+        const T tv = link ? av * idg : av;
         if (link && r == 1) pr += tv;
         else if (r == 2) pr += tv * tv;
-        else if (r > 2) pr += pow(tv, (double)r);
+        else if (r > 2) pr += pow(tv, (T)r);
+    };
+    // 16-byte vector loads (4 FP32 / 2 FP64 values), two vectors in flight
+    // per thread, then the scalar tail.
+    using V = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+    constexpr int kW = sizeof(V) / sizeof(T);
+    const long long nv = vec_ok ? n / kW : 0;
+    const V* cv = reinterpret_cast<const V*>(c);
+    const V* iv = reinterpret_cast<const V*>(ideg);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; k + stride < nv; k += 2 * stride) {
+        const V x0 = cv[k], x1 = cv[k + stride];
+        V d0, d1;
+        if (link) { d0 = iv[k]; d1 = iv[k + stride]; } else { d0 = x0; d1 = x1; }
+        const T* p0 = reinterpret_cast<const T*>(&x0);
+        const T* p1 = reinterpret_cast<const T*>(&x1);
+        const T* q0 = reinterpret_cast<const T*>(&d0);
+        const T* q1 = reinterpret_cast<const T*>(&d1);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p1[u], q1[u]);
     }
-    a = block_sum(a, scratch);
-    s = block_sum(s, scratch);
-    pr = block_sum(pr, scratch);
+    for (; k < nv; k += stride) {
+        const V x0 = cv[k];
+        V d0 = link ? iv[k] : x0;
+        const T* p0 = reinterpret_cast<const T*>(&x0);
+        const T* q0 = reinterpret_cast<const T*>(&d0);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
+    }
+    for (long long i = nv * kW + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+        add(c[i], link ? ideg[i] : T(0));
+    // block sums in the cash type too; the partials of the blocks are
+    // combined in FP64
+    __shared__ T tscratch[32];
+    const T ba = block_sum(a, tscratch);
+    const T bs = block_sum(s, tscratch);
+    const T bp = block_sum(pr, tscratch);
     if (threadIdx.x == 0) {
-        part[3 * blockIdx.x + 0] = a;
-        part[3 * blockIdx.x + 1] = s;
-        part[3 * blockIdx.x + 2] = pr;
+        part[3 * blockIdx.x + 0] = (double)ba;
+        part[3 * blockIdx.x + 1] = (double)bs;
+        part[3 * blockIdx.x + 2] = (double)bp;
     }
     if (!last_block(&st->ticket)) return;
     double tot[3];
@@ -318,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) k_stats(const T* __restrict__ c,
         st->l1 = tot[0];
         st->sum = tot[1];
         st->sumr = (r == 1 && !link) ? tot[0] : tot[2];
-        control_after_stats(st, cond_handle, use_cond, n);
+        control_after_stats(st, cond_handle, cond_refresh, use_cond, n);
     }
 }
 
@@ -397,44 +646,76 @@ __global__ void __launch_bounds__(kThreads) k_radix_pass(const T* __restrict__ c
         long long cum = found >= 0 ? above_found : 0;
         st->tk_prefix = prefix | ((unsigned long long)digit << shift);
         st->tk_remain = remain - cum;
-        if (shift == 0) st->theta = KeyOf<T>::value(st->tk_prefix);
+        if (shift == 0) set_theta(st, KeyOf<T>::value(st->tk_prefix), SCHED_TOPFRAC);
     }
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) st->hist[b] = 0u;
 }
 
 // ------------------------------------------------------------------ select
 
+// m~_i = m_i s_i, the cash a green row sends per unit of edge weight: in
+// FP64 on the FP64 path, in FP32 (with s_i rounded to FP32) on the MIXED path.
+__device__ __forceinline__ double moved_per_weight(double v, const double* s, const float*, long long i) {
+    return v * s[i];
+}
+__device__ __forceinline__ float moved_per_weight(float v, const double*, const float* sf, long long i) {
+    return v * sf[i];
+}
+
 // Green-light selection, snapshot and frontier compaction (Eq. recursion_M
 // and Eq. recursion_H): for every green node, m_i = C_i, C_i <- 0,
 // H_i += m_i, and the frontier entry (edge offset, CSR base, m~_i = m_i s_i)
 // is written. Dense mt[i] = m~_i (0 for red nodes) feeds the pull.
-template <typename T>
+template <typename T, bool kBatch>
 __global__ void __launch_bounds__(kThreads) k_select(
     T* __restrict__ c, double* __restrict__ H, const double* __restrict__ s,
-    const long long* __restrict__ row_ptr, const int* __restrict__ deg,
-    const unsigned char* __restrict__ masks, int n,
+    const float* __restrict__ sf, const long long* __restrict__ row_ptr,
+    const T* __restrict__ ideg, const unsigned char* __restrict__ masks, int n,
     T* __restrict__ mt, long long* __restrict__ f_eoff, long long* __restrict__ f_base,
     T* __restrict__ f_m, int* __restrict__ chunk_row, DevState* st, double* part,
-    MoveRecord* __restrict__ log) {
+    MoveRecord* __restrict__ log, unsigned long long cond_mode, int use_cond, BatchView bv) {
     if (st->done || st->skip_move) return;
     const Control& ctl = st->ctl;
     int sched = ctl.sched;
     if (ctl.safety_every > 0 && ((st->solve_moves + 1) % ctl.safety_every) == 0) sched = SCHED_ALL_GREEN;
-    const double theta = st->theta;
+    // The MIXED path compares in FP32 against theta_f (see set_theta); the
+    // FP64 path compares in FP64.
+    const T theta = std::is_same<T, float>::value ? (T)st->theta_f : (T)st->theta;
     const unsigned char* mask = nullptr;
     if (sched == SCHED_MASK) mask = masks + (size_t)(st->mask_cursor % ctl.n_masks) * (size_t)n;
 
     __shared__ double scratch[32];
+    __shared__ T tscratch[32];
     __shared__ unsigned long long base_sh;
-    double msum = 0.0, mabs = 0.0;
+    T msum = T(0), mabs = T(0);  // per-thread sums in the cash type
 
+    // Batch: all-green goes through the frontier path, since nodes of chains
+    // that have stopped are red.
+    const bool dense_all = (sched == SCHED_ALL_GREEN) && !kBatch;
     for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
          it0 += (long long)gridDim.x * kNodesPerIter) {
         int idx[kNodesPerThread];
         T val[kNodesPerThread];
-        long long rdeg[kNodesPerThread], rb[kNodesPerThread];
+        long long rb[kNodesPerThread];
+        int rdeg[kNodesPerThread];
         bool g[kNodesPerThread];
         unsigned long long mine = 0ull;
+        int uni = -1;
+        if (kBatch) {
+            uni = iter_chain(bv, it0, n);
+            msum = T(0);
+            mabs = T(0);
+        }
+        // Row offsets are read for every node (not only green ones) so that
+        // these loads overlap the cash loads instead of waiting for the test.
+        if (!dense_all) {
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                rb[q] = (i < n) ? row_ptr[i] : 0;
+                rdeg[q] = (i < n) ? (int)(row_ptr[i + 1] - rb[q]) : 0;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
             long long i = it0 + q * kThreads + threadIdx.x;
@@ -444,29 +725,33 @@ __global__ void __launch_bounds__(kThreads) k_select(
             if (i < n) {
                 T v = c[i];
                 val[q] = v;
-                if (sched == SCHED_ALL_GREEN) g[q] = true;
+                T th = theta;
+                bool active = true;
+                if (kBatch) {
+                    const ChainState& ch = bv.cs[uni >= 0 ? uni : bv.chain_of[i]];
+                    active = !ch.done;
+                    th = std::is_same<T, float>::value ? (T)ch.theta_f : (T)ch.theta;
+                }
+                if (!active) g[q] = false;
+                else if (sched == SCHED_ALL_GREEN) g[q] = true;
                 else if (sched == SCHED_MASK) g[q] = mask[i] != 0;
-                else if (sched == SCHED_LINK) g[q] = (v != T(0)) && (fabs((double)v) / (double)deg[i] >= theta);
-                else g[q] = (v != T(0)) && (fabs((double)v) >= theta);
+                else if (sched == SCHED_LINK) g[q] = (v != T(0)) && (fabs(v) * ideg[i] >= th);
+                else g[q] = (v != T(0)) && (fabs(v) >= th);
             }
-            if (g[q] && sched != SCHED_ALL_GREEN) {
-                rb[q] = row_ptr[idx[q]];
-                rdeg[q] = row_ptr[idx[q] + 1] - rb[q];
-                mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
-            }
+            if (g[q] && !dense_all) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
         }
-        if (sched == SCHED_ALL_GREEN) {
+        if (dense_all) {
             // All-green always pulls: no frontier, no degrees.
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
                 long long i = idx[q];
                 if (i >= n) continue;
-                double mv = (double)val[q];
+                const T v = val[q];
                 c[i] = T(0);
-                H[i] += mv;
-                msum += mv;
-                mabs += fabs(mv);
-                mt[i] = (T)(mv * s[i]);
+                H[i] += (double)v;
+                msum += v;
+                mabs += fabs(v);
+                mt[i] = moved_per_weight(v, s, sf, i);
             }
             continue;
         }
@@ -482,13 +767,18 @@ __global__ void __launch_bounds__(kThreads) k_select(
             long long i = idx[q];
             if (i >= n) continue;
             if (g[q]) {
-                T v = val[q];
-                double mv = (double)v;
-                T mtil = (T)(mv * s[i]);
+                const T v = val[q];
+                const T mtil = moved_per_weight(v, s, sf, i);
                 c[i] = T(0);
-                H[i] += mv;
-                msum += mv;
-                mabs += fabs(mv);
+                H[i] += (double)v;
+                if (kBatch && uni < 0) {
+                    const int ch = bv.chain_of[i];
+                    atomicAdd(&bv.cs[ch].acc[3], (double)v);
+                    atomicAdd(&bv.cs[ch].acc[4], (double)fabs(v));
+                } else {
+                    msum += v;
+                    mabs += fabs(v);
+                }
                 mt[i] = mtil;
                 f_eoff[k] = e;
                 f_base[k] = rb[q] - e;
@@ -503,23 +793,49 @@ __global__ void __launch_bounds__(kThreads) k_select(
                 mt[i] = T(0);
             }
         }
+        if (kBatch && uni >= 0) {
+            const int ks[2] = {3, 4};
+            const T vals[2] = {msum, mabs};
+            block_chain_add<2>(bv.cs, uni, ks, vals, tscratch);
+        }
         __syncthreads();
     }
-    msum = block_sum(msum, scratch);
-    mabs = block_sum(mabs, scratch);
+    if (kBatch) {
+        msum = T(0);
+        mabs = T(0);
+    }
+    const double bmsum = (double)block_sum(msum, tscratch);
+    const double bmabs = (double)block_sum(mabs, tscratch);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = msum;
-        part[2 * blockIdx.x + 1] = mabs;
+        part[2 * blockIdx.x] = bmsum;
+        part[2 * blockIdx.x + 1] = bmabs;
     }
     if (!last_block(&st->ticket)) return;
     double tot[2];
     reduce_partials<2>(part, gridDim.x, tot);
+    double bsum = 0.0, babs = 0.0;
+    if (kBatch) {
+        // per chain: history totals and the move count of running chains
+        for (int k = threadIdx.x; k < bv.nchains; k += blockDim.x) {
+            ChainState* ch = bv.cs + k;
+            const double m = __ldcg(&ch->acc[3]), ma = __ldcg(&ch->acc[4]);
+            ch->acc[3] = 0.0;
+            ch->acc[4] = 0.0;
+            ch->hsum += m;
+            ch->habs += ma;
+            bsum += m;
+            babs += ma;
+            if (!ch->done) ch->moves++;
+        }
+        bsum = block_sum(bsum, scratch);
+        babs = block_sum(babs, scratch);
+    }
     if (threadIdx.x == 0) {
-        const double ms = tot[0], ma = tot[1];
+        const double ms = kBatch ? bsum : tot[0], ma = kBatch ? babs : tot[1];
         unsigned long long rsv = *(volatile unsigned long long*)&st->reserve;
         long long green = (long long)(rsv & ((1ull << kCountBits) - 1ull));
         long long edges = (long long)(rsv >> kCountBits);
-        if (sched == SCHED_ALL_GREEN) {  // every node, every edge (no frontier built)
+        if (dense_all) {  // every node, every edge (no frontier built)
             green = n;
             edges = ctl.nnz;
         }
@@ -544,6 +860,8 @@ __global__ void __launch_bounds__(kThreads) k_select(
         st->mode = mode;
         if (mode == MODE_PUSH) st->push_moves++;
         if (mode == MODE_PULL) st->pull_moves++;
+        // in the solve graph, only the chosen one of pull / push is launched
+        if (use_cond) cudaGraphSetConditional(cond_mode, mode == MODE_PULL ? 1u : 0u);
         MoveRecord rec;
         rec.move = st->moves - 1;
         rec.green = green;
@@ -562,44 +880,75 @@ __global__ void __launch_bounds__(kThreads) k_select(
 // c_j += m~_i w_ij for every out-edge of every frontier row (Eq.
 // grl_update_C). Work is split into chunks of kPushChunk consecutive
 // frontier edges, whatever the row degrees; chunk_row[b] is the frontier row
-// holding the chunk's first edge (written by k_select).
+// holding the chunk's first edge (written by k_select). Within a chunk each
+// edge slot is labelled with its row by marking the row starts and taking a
+// block-wide running maximum, so every edge costs one shared-memory read;
+// edges are then handled in a coalesced order (slot = thread + q * threads).
 template <typename T, bool kHasW>
 __global__ void __launch_bounds__(kThreads) k_push(
     T* __restrict__ c, const int* __restrict__ col, const float* __restrict__ w,
     const long long* __restrict__ f_eoff, const long long* __restrict__ f_base,
     const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st) {
     if (st->done || st->skip_move || st->mode != MODE_PUSH) return;
+    constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread (8)
     const long long E = st->edges;
     const long long K = st->green;
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
-    __shared__ int s_off[kPushChunk + 1];
+    __shared__ int s_row[kPushChunk];
     __shared__ long long s_base[kPushChunk + 1];
     __shared__ T s_m[kPushChunk + 1];
+    __shared__ int s_wmax[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (long long b = blockIdx.x; b < nchunks; b += gridDim.x) {
         const long long e0 = b * kPushChunk;
         const int ne = (int)min((long long)kPushChunk, E - e0);
         const long long k0 = chunk_row[b];
         const long long k1 = (b + 1 < nchunks) ? (long long)chunk_row[b + 1] : K - 1;
         const int nr = (int)(k1 - k0 + 1);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = 0;
+        __syncthreads();
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-            long long eo = f_eoff[k0 + r];
-            s_off[r] = (int)(eo - e0);
+            const long long eo = f_eoff[k0 + r];
             s_base[r] = f_base[k0 + r];
             s_m[r] = f_m[k0 + r];
+            const long long off = eo - e0;  // row 0 starts at or before the chunk
+            if (r > 0 && off < ne) s_row[(int)off] = r;
         }
         __syncthreads();
-        for (int le = threadIdx.x; le < ne; le += blockDim.x) {
-            // last row whose local offset is <= le
-            int lo = 0, hi = nr - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= le) lo = mid; else hi = mid - 1;
+        // running maximum over the slots: slot -> row
+        int v[kPer];
+        int run = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            run = max(run, s_row[threadIdx.x * kPer + q]);
+            v[q] = run;
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        if (lane == 31) s_wmax[wid] = incl;
+        __syncthreads();
+        int before = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) before = 0;
+        for (int k = 0; k < wid; ++k) before = max(before, s_wmax[k]);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = max(v[q], before);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int le = threadIdx.x + q * kThreads;
+            if (le < ne) {
+                const int r = s_row[le];
+                const long long pos = s_base[r] + e0 + le;
+                const int j = __ldg(col + pos);
+                T val = s_m[r];
+                if (kHasW) val = val * (T)__ldg(w + pos);
+                atomicAdd(c + j, val);
             }
-            long long pos = s_base[lo] + e0 + le;
-            int j = __ldg(col + pos);
-            T v = s_m[lo];
-            if (kHasW) v = v * (T)__ldg(w + pos);
-            atomicAdd(c + j, v);
         }
         __syncthreads();
     }
@@ -852,6 +1201,91 @@ __global__ void __launch_bounds__(kThreads) k_hist_sums(const double* __restrict
     }
 }
 
+// Batch: per chain sum H and sum |H| into acc[5], acc[6] (zero at rest).
+__global__ void __launch_bounds__(kThreads) k_bhist_sums(const double* __restrict__ H, int n,
+                                                         BatchView bv) {
+    __shared__ double scratch[32];
+    const int ks[2] = {5, 6};
+    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+         it0 += (long long)gridDim.x * kNodesPerIter) {
+        const int uni = iter_chain(bv, it0, n);
+        double hs = 0.0, ha = 0.0;
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            if (i >= n) continue;
+            const double v = H[i];
+            if (uni >= 0) {
+                hs += v;
+                ha += fabs(v);
+            } else {
+                const int ch = bv.chain_of[i];
+                atomicAdd(&bv.cs[ch].acc[5], v);
+                atomicAdd(&bv.cs[ch].acc[6], fabs(v));
+            }
+        }
+        if (uni >= 0) {
+            const double vals[2] = {hs, ha};
+            block_chain_add<2, double>(bv.cs, uni, ks, vals, scratch);
+        }
+    }
+}
+
+// Batch: moves the per-chain sums from the accumulators into hsum / habs
+// (set_state) and leaves them, one chain per thread.
+__global__ void k_bhist_finish(BatchView bv, int set_state, double* sums_out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < bv.nchains; k += gridDim.x * blockDim.x) {
+        ChainState* ch = bv.cs + k;
+        const double S = ch->acc[5], A = ch->acc[6];
+        ch->acc[5] = 0.0;
+        ch->acc[6] = 0.0;
+        if (set_state) {
+            ch->hsum = S;
+            ch->habs = A;
+        }
+        if (sums_out) {
+            sums_out[2 * k] = S;
+            sums_out[2 * k + 1] = A;
+        }
+    }
+}
+
+// Batch estimate: pi_i = H_i / (sum of H over i's chain).
+__global__ void k_bscale(const double* __restrict__ H, int n, const int* __restrict__ chain_of,
+                         const double* __restrict__ sums, double* __restrict__ pi) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        pi[i] = H[i] / sums[2 * chain_of[i]];
+}
+
+// Node -> chain map from the chain offsets (binary search per node).
+__global__ void k_chain_of(const long long* __restrict__ node_ptr, int nchains, long long n,
+                           int* __restrict__ chain_of) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nchains - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (node_ptr[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        chain_of[i] = lo;
+    }
+}
+
+// Every edge must stay inside its chain (block-diagonal CSR); err |= 16.
+__global__ void k_check_blocks(const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                               const int* __restrict__ chain_of, long long n, unsigned int* err) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned int e = 0;
+    for (long long i = warp; i < n; i += nwarps) {
+        const int ci = chain_of[i];
+        for (long long k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32)
+            if (chain_of[col[k]] != ci) e = 16u;
+    }
+    if (e) atomicOr(err, e);
+}
+
 __global__ void k_scale(const double* __restrict__ H, int n, const double* __restrict__ sums,
                         double* __restrict__ pi) {
     double S = sums[0];
@@ -898,7 +1332,8 @@ __global__ void k_validate(const long long* __restrict__ row_ptr, const int* __r
 
 // s_i = 1 / sum_k w_ik (FP64 sum in CSR order) or 1 / deg_i.
 __global__ void k_row_scale(const long long* __restrict__ row_ptr, const float* __restrict__ w,
-                            long long n, double* __restrict__ s, int* __restrict__ deg) {
+                            long long n, double* __restrict__ s, float* __restrict__ sf,
+                            float* __restrict__ idegf, double* __restrict__ idegd) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         long long a = row_ptr[i], b = row_ptr[i + 1];
@@ -910,7 +1345,10 @@ __global__ void k_row_scale(const long long* __restrict__ row_ptr, const float* 
             sum = (double)(b - a);
         }
         s[i] = 1.0 / sum;
-        deg[i] = (int)(b - a);
+        if (sf) sf[i] = (float)(1.0 / sum);
+        const double id = 1.0 / (double)(b - a);
+        if (idegf) idegf[i] = (float)id;
+        if (idegd) idegd[i] = id;
     }
 }
 
@@ -936,6 +1374,16 @@ __global__ void k_scatter_in(const long long* __restrict__ row_ptr, const int* _
             t_src[q] = (int)i;
             if (w) t_w[q] = w[k];
         }
+    }
+}
+
+// Batch: every chain running again (and its tolerance, when tol >= 0).
+__global__ void k_bbegin(ChainState* cs, int nchains, double tol, int reset_moves) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchains; k += gridDim.x * blockDim.x) {
+        cs[k].done = 0;
+        cs[k].status = 0;
+        if (tol >= 0.0) cs[k].tol = tol;
+        if (reset_moves) cs[k].moves = 0;
     }
 }
 

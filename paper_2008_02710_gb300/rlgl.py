@@ -87,10 +87,17 @@ SIGNATURES = {
     "rlgl_create": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _I32, _I32, _VP, ctypes.POINTER(_VP)]),
     "rlgl_create_from_state": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _I32, _I32, _VP,
                                      ctypes.POINTER(_VP)]),
+    "rlgl_batch_create": (_ST, [_I64, _VP, _I64, _I64, _VP, _VP, _VP, _I32, _I32, _VP,
+                                ctypes.POINTER(_VP)]),
+    "rlgl_batch_set_tol": (_ST, [_VP, _VP]),
+    "rlgl_batch_chains": (_ST, [_VP, _VP, _VP, _VP]),
     "rlgl_reset": (_ST, [_VP, _VP, _I32]),
     "rlgl_set_masks": (_ST, [_VP, _VP, _I64, _I32]),
     "rlgl_step": (_ST, [_VP, _I32, _D, ctypes.POINTER(StepInfo)]),
     "rlgl_solve": (_ST, [_VP, _I32, _D, _D, _I64, ctypes.POINTER(SolveInfo)]),
+    "rlgl_solve_async": (_ST, [_VP, _I32, _D, _D, _I64]),
+    "rlgl_query": (_ST, [_VP, ctypes.POINTER(_I32)]),
+    "rlgl_wait": (_ST, [_VP, ctypes.POINTER(SolveInfo)]),
     "rlgl_estimate": (_ST, [_VP, _VP, _I32]),
     "rlgl_get_state": (_ST, [_VP, _VP, _VP, _I32]),
     "rlgl_invariant_residual": (_ST, [_VP, ctypes.POINTER(_D)]),
@@ -103,6 +110,7 @@ SIGNATURES = {
     "rlgl_move_log": (_ST, [_VP, ctypes.POINTER(MoveRecord), _I64, ctypes.POINTER(_I64)]),
     "rlgl_invariant_residual_noalloc": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                               _VP]),
+    "rlgl_footprint": (_I64, [_I64, _I64, _I32, _I32, _I64]),
     "rlgl_stream": (_VP, [_VP]),
     "rlgl_last_error": (ctypes.c_char_p, [_VP]),
     "rlgl_status_string": (ctypes.c_char_p, [_ST]),
@@ -164,7 +172,8 @@ class Chain:
     numpy arrays (copied from host) or CUDA torch tensors (copied on device).
     """
 
-    def __init__(self, csr, m0=None, precision="fp64", stream=None, c=None, h=None):
+    def __init__(self, csr, m0=None, precision="fp64", stream=None, c=None, h=None,
+                 node_ptr=None):
         self.lib = load()
         self.n = int(csr.n)
         self.nnz = int(csr.row_ptr[-1])
@@ -177,7 +186,13 @@ class Chain:
         wp, _, k3 = _ptr(csr.w, cv(np.float32))
         sptr = _stream_ptr(stream)
         out = _VP()
-        if c is not None:
+        self.nchains = 1
+        if node_ptr is not None:
+            npp, _, k6 = _ptr(node_ptr, cv(np.int64))
+            self.nchains = int(len(node_ptr)) - 1
+            st = self.lib.rlgl_batch_create(self.nchains, npp, self.n, self.nnz, rp, cp, wp, prec, sp,
+                                            sptr, ctypes.byref(out))
+        elif c is not None:
             c_p, _, k4 = _ptr(c, cv(np.float64))
             h_p, _, k5 = _ptr(h, cv(np.float64))
             st = self.lib.rlgl_create_from_state(self.n, self.nnz, rp, cp, wp, c_p, h_p, prec, sp,
@@ -243,12 +258,43 @@ class Chain:
             self._c(st)
         return res
 
+    def solve_async(self, schedule="threshold", theta: float = 0.0, tol: float = 1e-12,
+                    max_steps: int = 100000):
+        self._c(self.lib.rlgl_solve_async(self.ctx, _sched(schedule), float(theta), float(tol),
+                                          int(max_steps)))
+
+    def query(self) -> bool:
+        f = ctypes.c_int32()
+        self._c(self.lib.rlgl_query(self.ctx, ctypes.byref(f)))
+        return bool(f.value)
+
+    def wait(self, raise_on_noconv: bool = True):
+        si = SolveInfo()
+        st = self.lib.rlgl_wait(self.ctx, ctypes.byref(si))
+        res = si.asdict()
+        res["status"] = _STATUS.get(st, st)
+        if st != 0 and (raise_on_noconv or st not in (5, 6, 7)):
+            self._c(st)
+        return res
+
     def estimate(self, out=None):
         if out is None:
             out = np.empty(self.n, dtype=np.float64)
         p, sp, keep = _ptr(out)
         self._c(self.lib.rlgl_estimate(self.ctx, p, sp))
         return out
+
+    def set_chain_tol(self, tol):
+        t = np.ascontiguousarray(tol, dtype=np.float64)
+        self._c(self.lib.rlgl_batch_set_tol(self.ctx, t.ctypes.data))
+
+    def chains(self):
+        """Per chain of a batch: (status, moves, residual)."""
+        stt = np.empty(self.nchains, np.int32)
+        mv = np.empty(self.nchains, np.int64)
+        rs = np.empty(self.nchains, np.float64)
+        self._c(self.lib.rlgl_batch_chains(self.ctx, stt.ctypes.data, mv.ctypes.data, rs.ctypes.data))
+        return stt, mv, rs
 
     def get_state(self):
         c = np.empty(self.n)
@@ -317,6 +363,12 @@ def _stream_ptr(stream):
 
 def _sched(s) -> int:
     return SCHEDULES[s] if isinstance(s, str) else int(s)
+
+
+def footprint(n: int, nnz: int, weighted: bool, precision="mixed", n_chains: int = 1) -> int:
+    """Device bytes a context holds (rlgl_footprint)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return int(load().rlgl_footprint(n, nnz, int(weighted), prec, n_chains))
 
 
 def default_params() -> Params:

@@ -64,6 +64,14 @@ def _load():
             lib.synth_tiny_edges.argtypes = [i64, u64, vp, vp, vp, i64]
             lib.synth_rmat_edges.restype = None
             lib.synth_rmat_edges.argtypes = [i32, i64, dbl, dbl, dbl, u64, vp, vp]
+            lib.synth_rmat_edges_n.restype = None
+            lib.synth_rmat_edges_n.argtypes = [i64, i64, dbl, dbl, dbl, u64, vp, vp]
+            lib.synth_batch_sizes.restype = i64
+            lib.synth_batch_sizes.argtypes = [i64, u64, dbl, dbl, dbl, dbl, vp]
+            lib.synth_batch_degrees.restype = i64
+            lib.synth_batch_degrees.argtypes = [i64, u64, dbl, dbl, dbl, dbl, vp, vp]
+            lib.synth_batch_fill.restype = ctypes.c_int
+            lib.synth_batch_fill.argtypes = [i64, u64, vp, vp, vp]
             lib.synth_permutation.restype = None
             lib.synth_permutation.argtypes = [i64, u64, vp]
             lib.synth_relabel.restype = None
@@ -200,6 +208,23 @@ def rmat_chain(scale: int, edge_factor: int = 16, seed: int = 1, a: float = 0.57
     return edges_to_csr(n, src, dst, w)
 
 
+def rmat_chain_n(n: int, edge_factor: int = 16, seed: int = 1, a: float = 0.57,
+                 b: float = 0.19, c: float = 0.19) -> CSR:
+    """R-MAT chain on n nodes (any n): scale ceil(log2 n), out-of-range
+    endpoints drawn again, seeded relabelling, cycle and self-loops; unit
+    weights."""
+    lib = _load()
+    m = edge_factor * n
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    lib.synth_rmat_edges_n(n, m, a, b, c, seed, _p(src), _p(dst))
+    perm = np.empty(n, dtype=np.int32)
+    lib.synth_permutation(n, seed, _p(perm))
+    lib.synth_relabel(m, _p(perm), _p(src), _p(dst))
+    cs, cd = cycle_selfloop_edges(n)
+    return edges_to_csr(n, np.concatenate([src, cs]), np.concatenate([dst, cd]), None)
+
+
 def two_wheels() -> CSR:
     """The 12-node two-wheels graph (Sec. 6, two-wheels figure), undirected,
     unit weights, each edge stored in both directions, no self-loops.
@@ -273,3 +298,36 @@ def u64(seed: int, stream: int, i: int) -> int:
 
 def unit(seed: int, stream: int, i: int) -> float:
     return float(_load().synth_unit(seed, stream, i))
+
+
+def stack_chains(chains):
+    """Block-diagonal stack of several chains (node ids shifted): returns
+    (CSR of the batch, node_ptr int64 [k+1]). Mixing weighted and unit-weight
+    chains gives unit weights 1.0 to the latter."""
+    n_off = np.cumsum([0] + [c.n for c in chains]).astype(np.int64)
+    e_off = np.cumsum([0] + [c.nnz for c in chains]).astype(np.int64)
+    row_ptr = np.concatenate([c.row_ptr[:-1] + e_off[k] for k, c in enumerate(chains)] +
+                             [np.array([e_off[-1]], np.int64)])
+    col = np.concatenate([c.col.astype(np.int64) + n_off[k] for k, c in enumerate(chains)]).astype(np.int32)
+    if all(c.w is None for c in chains):
+        w = None
+    else:
+        w = np.concatenate([c.w if c.w is not None else np.ones(c.nnz, np.float32) for c in chains])
+    return CSR(int(n_off[-1]), row_ptr, col, w), n_off
+
+
+def powerlaw_batch(nchains: int = 4096, seed: int = 1, lo: float = 100, hi: float = 1e5,
+                   dlo: float = 4.0, dhi: float = 32.0):
+    """The many-chain mix: nchains chains of log-uniform size in [lo, hi),
+    mean out-degree U(dlo, dhi), Poisson out-degrees, power-law targets,
+    cycle and self-loops, as one block-diagonal CSR (unit weights).
+    Returns (CSR, node_ptr)."""
+    lib = _load()
+    node_ptr = np.empty(nchains + 1, dtype=np.int64)
+    n = int(lib.synth_batch_sizes(nchains, seed, lo, hi, dlo, dhi, _p(node_ptr)))
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    nnz = int(lib.synth_batch_degrees(nchains, seed, lo, hi, dlo, dhi, _p(node_ptr), _p(row_ptr)))
+    col = np.empty(nnz, dtype=np.int32)
+    if lib.synth_batch_fill(nchains, seed, _p(node_ptr), _p(row_ptr), _p(col)) != 0:
+        raise MemoryError("batch generator")
+    return CSR(n, row_ptr, col, None), node_ptr

@@ -119,6 +119,44 @@ void synth_rmat_edges(int32_t scale, int64_t m, double a, double b, double c,
     }
 }
 
+/*
+ * R-MAT edges on n nodes (n need not be a power of two): generated at scale
+ * ceil(log2 n); an edge with an endpoint >= n is drawn again from the next
+ * sub-stream (at most 64 times, then its endpoints are folded mod n).
+ */
+void synth_rmat_edges_n(int64_t n, int64_t m, double a, double b, double c, uint64_t seed,
+                        int32_t* src, int32_t* dst) {
+    int32_t scale = 0;
+    while ((1ll << scale) < n) ++scale;
+    if (scale == 0) scale = 1;
+    double ab = a + b, abc = a + b + c;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t u = 0, v = 0;
+        for (int attempt = 0; attempt < 64; ++attempt) {
+            uint64_t key = rnd_key(seed, S_RMAT + 1000u * (uint64_t)attempt);
+            u = 0;
+            v = 0;
+            for (int32_t l = 0; l < scale; ++l) {
+                double r = unit_at(key, (uint64_t)e * (uint64_t)scale + (uint64_t)l);
+                uint32_t bit = 1u << (scale - 1 - l);
+                if (r < a) {
+                } else if (r < ab) {
+                    v |= bit;
+                } else if (r < abc) {
+                    u |= bit;
+                } else {
+                    u |= bit;
+                    v |= bit;
+                }
+            }
+            if ((int64_t)u < n && (int64_t)v < n) break;
+        }
+        src[e] = (int32_t)((int64_t)u % n);
+        dst[e] = (int32_t)((int64_t)v % n);
+    }
+}
+
 /* Seeded uniform random permutation of 0..n-1 (Fisher-Yates). */
 void synth_permutation(int64_t n, uint64_t seed, int32_t* perm) {
     uint64_t key = rnd_key(seed, S_PERM);
@@ -222,4 +260,94 @@ int64_t synth_powerlaw_chain_edges(int64_t n, double delta, uint64_t seed,
     free(perm);
     free(cdf);
     return m;
+}
+
+/*
+ * A batch of independent power-law chains written straight into one
+ * block-diagonal CSR, in three passes so that the caller can size the
+ * arrays: sizes (node_ptr), out-degrees (row_ptr), then targets (col).
+ * Chain k has n_k = floor(exp(U(ln lo, ln hi))) nodes and mean out-degree
+ * delta_k ~ U(dlo, dhi); node i draws Poisson(delta_k) targets from a power
+ * law P(rank r) proportional to 1/(r+1) over a seeded permutation of the
+ * chain, then gets the cycle edge and the self-loop. Node ids are global.
+ */
+static void batch_chain_params(uint64_t seed, int64_t k, double lo, double hi, double dlo,
+                               double dhi, int64_t* n, double* delta) {
+    double u = unit_at(rnd_key(seed, S_SIZE), (uint64_t)k);
+    double v = unit_at(rnd_key(seed, S_DELTA), (uint64_t)k);
+    *n = (int64_t)floor(exp(log(lo) + u * (log(hi) - log(lo))));
+    if (*n < 2) *n = 2;
+    *delta = dlo + v * (dhi - dlo);
+}
+
+static int64_t poisson_at(uint64_t key, uint64_t i, double delta) {
+    double u = unit_at(key, i), p = exp(-delta), s = p;
+    int64_t d = 0;
+    while (u > s && d < 100000) { ++d; p *= delta / (double)d; s += p; }
+    return d;
+}
+
+int64_t synth_batch_sizes(int64_t nchains, uint64_t seed, double lo, double hi, double dlo,
+                          double dhi, int64_t* node_ptr) {
+    node_ptr[0] = 0;
+    for (int64_t k = 0; k < nchains; ++k) {
+        int64_t n;
+        double d;
+        batch_chain_params(seed, k, lo, hi, dlo, dhi, &n, &d);
+        node_ptr[k + 1] = node_ptr[k] + n;
+    }
+    return node_ptr[nchains];
+}
+
+int64_t synth_batch_degrees(int64_t nchains, uint64_t seed, double lo, double hi, double dlo,
+                            double dhi, const int64_t* node_ptr, int64_t* row_ptr) {
+    uint64_t kp = rnd_key(seed, S_POIS);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nchains; ++k) {
+        int64_t n;
+        double delta;
+        batch_chain_params(seed, k, lo, hi, dlo, dhi, &n, &delta);
+        for (int64_t i = node_ptr[k]; i < node_ptr[k + 1]; ++i)
+            row_ptr[i + 1] = poisson_at(kp, (uint64_t)i, delta) + 2;
+    }
+    row_ptr[0] = 0;
+    int64_t N = node_ptr[nchains];
+    for (int64_t i = 0; i < N; ++i) row_ptr[i + 1] += row_ptr[i];
+    return row_ptr[N];
+}
+
+int synth_batch_fill(int64_t nchains, uint64_t seed, const int64_t* node_ptr,
+                     const int64_t* row_ptr, int32_t* col) {
+    uint64_t kt = rnd_key(seed, S_PL);
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nchains; ++k) {
+        const int64_t base = node_ptr[k], n = node_ptr[k + 1] - base;
+        int32_t* perm = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        double* cdf = (double*)malloc((size_t)n * sizeof(double));
+        if (!perm || !cdf) {
+            free(perm);
+            free(cdf);
+#pragma omp atomic write
+            err = 1;
+            continue;
+        }
+        synth_permutation(n, seed ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(k + 1)), perm);
+        double acc = 0.0;
+        for (int64_t r = 0; r < n; ++r) { acc += 1.0 / (double)(r + 1); cdf[r] = acc; }
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t gi = base + i, a = row_ptr[gi], d = row_ptr[gi + 1] - a - 2;
+            for (int64_t q = 0; q < d; ++q) {
+                double x = unit_at(kt, (uint64_t)(a + q)) * acc;
+                int64_t lo = 0, hi = n - 1;
+                while (lo < hi) { int64_t mid = (lo + hi) / 2; if (cdf[mid] > x) hi = mid; else lo = mid + 1; }
+                col[a + q] = (int32_t)(base + perm[lo]);
+            }
+            col[a + d] = (int32_t)(base + (i + 1) % n);
+            col[a + d + 1] = (int32_t)gi;
+        }
+        free(perm);
+        free(cdf);
+    }
+    return err ? -1 : 0;
 }

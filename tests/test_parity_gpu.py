@@ -99,16 +99,21 @@ def _one_move_parity(csr, p, ch, sched, theta=0.0, top_frac=0.01):
     gpu_set = set(green_of(h, h2).tolist())
     or_set = set(np.nonzero(g_or & (c != 0))[0].tolist())
     diff = gpu_set ^ or_set
+    # Ties: nodes whose test value is within the rounding of theta may go
+    # either way. The FP64 path decides in FP64 (band 1e-12 relative); the
+    # MIXED path sums the statistics in FP32 within blocks and takes the
+    # per-link test in FP32 (band 1e-4 relative).
+    band = 1e-12 if ch.precision == "fp64" else 1e-4
     deg = np.diff(csr.row_ptr)
-    for i in diff:  # only ties at theta may differ
+    for i in diff:
         v = abs(c[i]) / deg[i] if sched == "link_threshold" else abs(c[i])
-        assert abs(v - th) <= 1e-12 * max(th, 1e-300), (i, c[i], th)
+        assert abs(v - th) <= band * max(th, 1e-300), (i, c[i], th)
     if not diff:
         assert info["green"] == int(g_or.sum())
         deg = np.diff(csr.row_ptr)
         assert info["edges_pushed"] == int(deg[g_or.astype(bool)].sum())
     if sched in ("threshold", "link_threshold"):
-        assert abs(info["theta"] - th) <= 1e-13 * th
+        assert abs(info["theta"] - th) <= (1e-13 if ch.precision == "fp64" else 1e-5) * th
     if sched == "topfrac":
         assert info["theta"] == th  # a selection, not arithmetic: exact
     C, H = c.copy(), h.copy()
@@ -201,8 +206,10 @@ def test_solve_medium_fp64_vs_oracle(medium, sched):
         pi = ch.estimate()
         inv = ch.invariant_residual()
     assert info["status"] == "RLGL_OK"
-    assert abs(info["moves"] - info_or["moves"]) <= 1
     assert np.abs(pi - pi_or).sum() <= FP64_PI_TOL
+    # the stop test fires on a residual that both sides compute with their
+    # own rounding: over ~1e4 moves it may fire a few moves apart
+    assert abs(info["moves"] - info_or["moves"]) <= max(1, info_or["moves"] // 1000)
     # residual 1e-12 bounds the error by 1e-12 * ||Z|| (Eq. convergence)
     assert np.abs(pi - ref).sum() <= 1e-8
     assert inv <= 1e-13 * np.abs(H).sum()
