@@ -58,6 +58,9 @@ WORKLOADS = {
                         "weights U(0,1], FP32 cash, FP64 history"),
     "rmat16": dict(scale=16, edge_factor=16, weighted=False, precision="mixed",
                    desc="R-MAT scale 16 (small case)"),
+    "pagerank20": dict(scale=20, edge_factor=16, weighted=False, precision="mixed", pagerank=True,
+                       desc="PageRank c=0.85, uniform restart, on R-MAT scale 20 through the "
+                            "auxiliary-node chain P^(0) (N=2^20+1), FP32 cash, FP64 history"),
 }
 
 
@@ -158,11 +161,25 @@ class ClockSampler:
 
 # ------------------------------------------------------------ workload
 
-def make_workload(name: str, seed: int = 1):
+def make_workload(name: str, seed: int = 1, precision=None):
     from paper_2008_02710_gb300 import synth
-    w = WORKLOADS[name]
+    w = dict(WORKLOADS[name])
+    if precision:
+        w["precision"] = precision
     csr = synth.rmat_chain(w["scale"], w["edge_factor"], seed=seed, weighted=w["weighted"])
+    if w.get("pagerank"):
+        csr = synth.pagerank_chain(csr)
     return csr, w
+
+
+def workload_m0(csr, wl):
+    """Step-0 mass: e_0 on the PageRank chain (Sec. 2.3.2), else the
+    default uniform M_0."""
+    if not wl.get("pagerank"):
+        return None
+    m0 = np.zeros(csr.n)
+    m0[0] = 1.0
+    return m0
 
 
 def oracle_reference(csr, tol=1e-11, maxit=50000):
@@ -206,7 +223,9 @@ class GpuRun:
         self.stream = torch.cuda.Stream(device=device)
         self.csr = csr
         self.wl = wl
-        self.chain = Chain(csr, precision=wl["precision"], stream=self.stream)
+        m0 = workload_m0(csr, wl)
+        self.m0 = None if m0 is None else torch.from_numpy(m0).to(device)
+        self.chain = Chain(csr, m0=self.m0, precision=wl["precision"], stream=self.stream)
         self.pi_dev = torch.empty(csr.n, dtype=torch.float64, device=device)
         self.flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
@@ -219,7 +238,7 @@ class GpuRun:
     def calibrate(self, sched, theta, ref_dev, max_moves=20000):
         """Untimed: the first move count T* with L1 error <= 1e-6."""
         ch = self.chain
-        ch.reset()
+        ch.reset(self.m0)
         traj = []
         for k in range(1, max_moves + 1):
             ch.step(sched, theta, info=False)
@@ -245,7 +264,7 @@ class GpuRun:
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(self.stream)
-            ch.reset()
+            ch.reset(self.m0)
             info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
             ch.estimate(self.pi_dev)
             ev1.record(self.stream)
@@ -266,7 +285,7 @@ class GpuRun:
         cash = 4 if self.wl["precision"] == "mixed" else 8
         wb = 4 if csr.w is not None else 0
         link = 4 if sched == "link_threshold" else 0
-        ch.reset()
+        ch.reset(self.m0)
         ch.profile(2)
         kt = ch.profile_moves(sched, theta, tstar)
         log = ch.move_log(tstar)
@@ -297,12 +316,15 @@ class GpuRun:
                            torch.from_numpy(csr.col).pin_memory(),
                            None if csr.w is None else torch.from_numpy(csr.w).pin_memory())
         pi_host = torch.empty(csr.n, dtype=torch.float64).pin_memory()
+        m0 = workload_m0(csr, self.wl)
+        m0 = None if m0 is None else torch.from_numpy(m0).pin_memory()
         h2d = pinned.row_ptr.numel() * 8 + pinned.col.numel() * 4 + (0 if csr.w is None else csr.nnz * 4)
+        h2d += 0 if m0 is None else csr.n * 8
         times, pushes = [], []
         for i in range(warmup + steps):
             torch.cuda.synchronize(self.device)
             t0 = time.perf_counter()
-            with Chain(pinned, precision=self.wl["precision"], stream=self.stream) as ch:
+            with Chain(pinned, m0=m0, precision=self.wl["precision"], stream=self.stream) as ch:
                 ch.set_params(theta_scale=theta_scale)
                 info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
                 ch.estimate(pi_host)
@@ -355,7 +377,7 @@ def run_gpu(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     dist = init_dist(ws, "nccl")
-    csr, wl = make_workload(args.workload)
+    csr, wl = make_workload(args.workload, precision=args.precision)
     # oracle leg: reference stationary law (host cores)
     ref, ref_info = oracle_reference(csr)
     ref_dev = torch.from_numpy(ref).to(device)
@@ -641,6 +663,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving"], default="rmat20")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None,
+                    help="override the workload's precision")
     ap.add_argument("--chains", type=int, default=4096, help="batch: number of chains")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")

@@ -311,7 +311,15 @@ void* rlgl_stream(const rlgl_ctx* ctx);
 const char* rlgl_last_error(const rlgl_ctx* ctx);
 const char* rlgl_status_string(rlgl_status s);
 
-/* Frees the context and all its device memory (NULL is a no-op). */
+/* Destroys the solve graphs kept from destroyed contexts and returns how
+ * many there were. rlgl_destroy does not destroy a context's executable
+ * graphs itself, because that can wait for unrelated work still running on
+ * the device; call this where no solve is running (it may wait for the
+ * device otherwise). */
+int64_t rlgl_release_retired(void);
+
+/* Frees the context and all its device memory (NULL is a no-op); its solve
+ * graphs are kept until rlgl_release_retired. */
 void rlgl_destroy(rlgl_ctx* ctx);
 
 #ifdef __cplusplus

@@ -160,6 +160,40 @@ static rlgl_status device_pool(rlgl_ctx* ctx) {
     return RLGL_OK;
 }
 
+// Pinned host blocks for each context's device-state mirror, cut from slabs
+// that live until the process exits and are recycled: releasing pinned
+// memory (cudaFreeHost) may synchronise the whole device.
+static constexpr size_t kPinBlock = ((sizeof(DevState) + sizeof(Control) + 255) / 256) * 256;
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+
+static void* pin_get() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        const int per_slab = 32;
+        void* slab = nullptr;
+        if (cudaMallocHost(&slab, kPinBlock * per_slab) != cudaSuccess) return nullptr;
+        for (int k = per_slab - 1; k >= 0; --k) g_pin_free.push_back((char*)slab + k * kPinBlock);
+    }
+    void* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+static void pin_put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
+// Solve graphs of destroyed contexts. Destroying an executable graph that
+// has been launched can wait for unrelated work on the device, which would
+// stall a server that retires one request while others run; they are kept
+// here until rlgl_release_retired() (a point where the caller knows the
+// device is idle) or the end of the process.
+static std::mutex g_retired_mu;
+static std::vector<cudaGraphExec_t> g_retired;
+
 static rlgl_status dalloc_bytes(rlgl_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 1;
@@ -532,8 +566,11 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     ctx->grid_nodes = grid_for(n, kThreads, cap);
     ctx->grid_select = grid_for(n, kNodesPerIter, cap);
     ctx->grid_stats = grid_for(n, kThreads * 8, ctx->sms * 2);  // about 8+ nodes per thread
-    ctx->grid_push = ctx->sms * 4;
-    ctx->grid_pull = ctx->sms * 8;
+    // push/pull grids grow with the work up to a few blocks per SM, so that a
+    // small chain does not launch hundreds of idle blocks (which would also
+    // crowd out other contexts' work on the device)
+    ctx->grid_push = grid_for(nnz, kPushChunk, ctx->sms * 4);
+    ctx->grid_pull = grid_for(n + nnz, kMpItems, ctx->sms * 8);
     const size_t cs = cash_size(ctx);
 
     TRY(dalloc(ctx, &ctx->row_ptr, (size_t)n + 1));
@@ -545,7 +582,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->t_ptr, (size_t)n + 1));
     TRY(dalloc(ctx, &ctx->t_src, (size_t)nnz));
     if (ctx->has_w) TRY(dalloc(ctx, &ctx->t_w, (size_t)nnz));
-    ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;
+    ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;  // (grid_pull above uses the same count)
     TRY(dalloc(ctx, &ctx->tile_r, (size_t)ctx->ntiles + 1));
     TRY(dalloc(ctx, &ctx->tile_e, (size_t)ctx->ntiles + 1));
     TRY(dalloc_bytes(ctx, &ctx->c, (size_t)n * cs));
@@ -561,8 +598,9 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->err, 1));
     TRY(dalloc(ctx, &ctx->log, (size_t)kLogCap));
     TRY(dalloc(ctx, &ctx->st, 1));
-    CK(ctx, cudaMallocHost((void**)&ctx->host_st, sizeof(DevState)));
-    CK(ctx, cudaMallocHost((void**)&ctx->host_ctl, sizeof(Control)));
+    ctx->host_st = static_cast<DevState*>(pin_get());
+    if (!ctx->host_st) return fail(ctx, RLGL_ENOMEM, "pinned host allocation failed");
+    ctx->host_ctl = reinterpret_cast<Control*>(reinterpret_cast<char*>(ctx->host_st) + sizeof(DevState));
     CK(ctx, cudaMemsetAsync(ctx->y, 0, (size_t)n * sizeof(double), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(unsigned int), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream));
@@ -1221,6 +1259,16 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
     return RLGL_OK;
 }
 
+int64_t rlgl_release_retired(void) {
+    std::vector<cudaGraphExec_t> v;
+    {
+        std::lock_guard<std::mutex> lk(g_retired_mu);
+        v.swap(g_retired);
+    }
+    for (auto g : v) cudaGraphExecDestroy(g);
+    return (int64_t)v.size();
+}
+
 int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision prec,
                        int64_t n_chains) {
     if (n < 1 || nnz < 1) return -1;
@@ -1260,8 +1308,11 @@ void rlgl_destroy(rlgl_ctx* ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
-    for (auto& g : ctx->graph)
-        if (g) cudaGraphExecDestroy(g);
+    {
+        std::lock_guard<std::mutex> lk(g_retired_mu);
+        for (auto& g : ctx->graph)
+            if (g) g_retired.push_back(g);
+    }
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
@@ -1271,8 +1322,7 @@ void rlgl_destroy(rlgl_ctx* ctx) {
         dfree(ctx, p);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
-    if (ctx->host_st) cudaFreeHost(ctx->host_st);
-    if (ctx->host_ctl) cudaFreeHost(ctx->host_ctl);
+    pin_put(ctx->host_st);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -22,6 +22,7 @@
 // combined by the last block to finish (an atomic ticket), so nothing here
 // can hang.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -222,14 +223,46 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 template <int K>
 __device__ __forceinline__ void reduce_partials(const double* part, int nb, double* out) {
     __shared__ double scratch[32];
+    // Groups of 4 partials per thread, each group's loads issued before its
+    // adds: one round trip per group (one in all for up to 1024 blocks).
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int g0 = 0; g0 < nb; g0 += 4 * kThreads) {
+        double v[4][K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += ldcg(part + K * b + k);
+        for (int u = 0; u < 4; ++u) {
+            const int b = g0 + threadIdx.x + u * kThreads;
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[u][k] = (b < nb) ? ldcg(part + K * b + k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] += v[u][k];
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = block_sum(acc[k], scratch);
+}
+
+// The scalar part of the device state (everything before the radix
+// histogram), staged in shared memory by the last block of a kernel: one
+// parallel load, the bookkeeping on the copy, one parallel store. This keeps
+// the serial tail of a kernel from paying one global round trip per field.
+constexpr int kStWords = (int)(offsetof(DevState, hist) / sizeof(unsigned int));
+struct StStage {
+    unsigned int w[kStWords];
+};
+__device__ __forceinline__ DevState* st_stage_in(const DevState* st, StStage* sh) {
+    const unsigned int* src = reinterpret_cast<const unsigned int*>(st);
+    for (int k = threadIdx.x; k < kStWords; k += blockDim.x) sh->w[k] = __ldcg(src + k);
+    __syncthreads();
+    return reinterpret_cast<DevState*>(sh);
+}
+__device__ __forceinline__ void st_stage_out(DevState* st, const StStage* sh) {
+    __syncthreads();
+    unsigned int* dst = reinterpret_cast<unsigned int*>(st);
+    for (int k = threadIdx.x; k < kStWords; k += blockDim.x) dst[k] = sh->w[k];
 }
 
 // ------------------------------------------------------- stats + control
@@ -563,12 +596,15 @@ __global__ void __launch_bounds__(kThreads) k_stats(const T* __restrict__ c,
     if (!last_block(&st->ticket)) return;
     double tot[3];
     reduce_partials<3>(part, gridDim.x, tot);
+    __shared__ StStage stage;
+    DevState* ss = st_stage_in(st, &stage);
     if (threadIdx.x == 0) {
-        st->l1 = tot[0];
-        st->sum = tot[1];
-        st->sumr = (r == 1 && !link) ? tot[0] : tot[2];
-        control_after_stats(st, cond_handle, cond_refresh, use_cond, n);
+        ss->l1 = tot[0];
+        ss->sum = tot[1];
+        ss->sumr = (r == 1 && !link) ? tot[0] : tot[2];
+        control_after_stats(ss, cond_handle, cond_refresh, use_cond, n);
     }
+    st_stage_out(st, &stage);
 }
 
 // ------------------------------------------------------ top-k radix select
@@ -830,49 +866,52 @@ __global__ void __launch_bounds__(kThreads) k_select(
         bsum = block_sum(bsum, scratch);
         babs = block_sum(babs, scratch);
     }
+    __shared__ StStage stage;
+    DevState* ss = st_stage_in(st, &stage);
     if (threadIdx.x == 0) {
         const double ms = kBatch ? bsum : tot[0], ma = kBatch ? babs : tot[1];
-        unsigned long long rsv = *(volatile unsigned long long*)&st->reserve;
+        unsigned long long rsv = ss->reserve;
         long long green = (long long)(rsv & ((1ull << kCountBits) - 1ull));
         long long edges = (long long)(rsv >> kCountBits);
         if (dense_all) {  // every node, every edge (no frontier built)
             green = n;
-            edges = ctl.nnz;
+            edges = ss->ctl.nnz;
         }
-        st->reserve = 0ull;
-        st->green = green;
-        st->edges = edges;
-        st->hsum += ms;
-        st->habs += ma;
-        st->last_mabs = ma;
-        st->moves++;
-        st->solve_moves++;
-        st->tot_green += green;
-        st->tot_edges += edges;
-        st->fresh = 0;
-        if (sched == SCHED_MASK) st->mask_cursor++;
+        ss->reserve = 0ull;
+        ss->green = green;
+        ss->edges = edges;
+        ss->hsum += ms;
+        ss->habs += ma;
+        ss->last_mabs = ma;
+        ss->moves++;
+        ss->solve_moves++;
+        ss->tot_green += green;
+        ss->tot_edges += edges;
+        ss->fresh = 0;
+        if (sched == SCHED_MASK) ss->mask_cursor++;
         int mode;
         if (green == 0) mode = MODE_NONE;
-        else if (sched == SCHED_ALL_GREEN || (double)edges >= ctl.pull_crossover * (double)ctl.nnz)
+        else if (sched == SCHED_ALL_GREEN || (double)edges >= ss->ctl.pull_crossover * (double)ss->ctl.nnz)
             mode = MODE_PULL;
         else
             mode = MODE_PUSH;
-        st->mode = mode;
-        if (mode == MODE_PUSH) st->push_moves++;
-        if (mode == MODE_PULL) st->pull_moves++;
+        ss->mode = mode;
+        if (mode == MODE_PUSH) ss->push_moves++;
+        if (mode == MODE_PULL) ss->pull_moves++;
         // in the solve graph, only the chosen one of pull / push is launched
         if (use_cond) cudaGraphSetConditional(cond_mode, mode == MODE_PULL ? 1u : 0u);
         MoveRecord rec;
-        rec.move = st->moves - 1;
+        rec.move = ss->moves - 1;
         rec.green = green;
         rec.edges = edges;
         rec.mode = mode;
         rec.pad = 0;
         rec.theta = theta;
-        rec.l1 = st->l1;
-        rec.hsum = st->hsum;
+        rec.l1 = ss->l1;
+        rec.hsum = ss->hsum;
         log[rec.move % kLogCap] = rec;
     }
+    st_stage_out(st, &stage);
 }
 
 // -------------------------------------------------------------------- push

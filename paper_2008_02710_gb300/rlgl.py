@@ -111,6 +111,7 @@ SIGNATURES = {
     "rlgl_invariant_residual_noalloc": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                               _VP]),
     "rlgl_footprint": (_I64, [_I64, _I64, _I32, _I32, _I64]),
+    "rlgl_release_retired": (_I64, []),
     "rlgl_stream": (_VP, [_VP]),
     "rlgl_last_error": (ctypes.c_char_p, [_VP]),
     "rlgl_status_string": (ctypes.c_char_p, [_ST]),
@@ -369,6 +370,11 @@ def footprint(n: int, nnz: int, weighted: bool, precision="mixed", n_chains: int
     """Device bytes a context holds (rlgl_footprint)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return int(load().rlgl_footprint(n, nnz, int(weighted), prec, n_chains))
+
+
+def release_retired() -> int:
+    """Destroys the solve graphs of destroyed contexts (rlgl_release_retired)."""
+    return int(load().rlgl_release_retired())
 
 
 def default_params() -> Params:

@@ -127,6 +127,7 @@ class Server:
                 nxt = todo[0].arrival - now() if (realtime and todo and not queue) else 0.0
                 time.sleep(min(max(nxt, 0.0), 0.002) if nxt > 0 else 0.0002)
         self.stats = {"max_used_bytes": max_used, "max_active": max_active}
+        rlgl.release_retired()  # nothing runs any more
         return results
 
 

@@ -331,3 +331,47 @@ def powerlaw_batch(nchains: int = 4096, seed: int = 1, lo: float = 100, hi: floa
     if lib.synth_batch_fill(nchains, seed, _p(node_ptr), _p(row_ptr), _p(col)) != 0:
         raise MemoryError("batch generator")
     return CSR(n, row_ptr, col, None), node_ptr
+
+
+def pagerank_chain(csr: CSR, c_num: int = 17, c_den: int = 20) -> CSR:
+    """The augmented chain P^(0) on n+1 nodes through which RLGL computes
+    PageRank with damping c = c_num/c_den and uniform restart (Sec. 2.3.2,
+    the Gauss-Southwell comparison): node 0 is the auxiliary node, original
+    node i becomes i+1. Weights (FP32-exact integers; rows are normalised by
+    the solver):
+      row 0   : c_num * n to itself and c_den - c_num to every node, so
+                p_00 = c and p_0j = (1 - c) / n;
+      row i+1 : (c_den - c_num) * deg_i to node 0 and c_num per out-edge,
+                so p_{i0} = 1 - c and p_ij = c / deg_i (unit-weight P);
+                a node without out-edges sends everything to node 0.
+    Without such dangling nodes the stationary law is (1/2, pi*/2), pi* the
+    PageRank vector. With them, the original nodes' part, normalised, is
+    PageRank with each dangling row replaced by the restart law s (the
+    normalised solution of y = c y P + (1 - c) s with those rows zero).
+    """
+    if csr.w is not None:
+        raise ValueError("pagerank_chain expects unit weights")
+    n = csr.n
+    a = float(c_num * n)
+    if float(np.float32(a)) != a:
+        raise ValueError("c_num * n is not exact in FP32")
+    deg = np.diff(csr.row_ptr)
+    rest = c_den - c_num
+    row_ptr = np.empty(n + 2, dtype=np.int64)
+    row_ptr[0] = 0
+    row_ptr[1] = n + 1
+    row_ptr[2:] = (n + 1) + np.cumsum(deg + 1)
+    col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    w = np.empty(int(row_ptr[-1]), dtype=np.float32)
+    col[:n + 1] = np.arange(n + 1)
+    w[0] = a
+    w[1:n + 1] = rest
+    starts = row_ptr[1:-1]
+    col[starts] = 0
+    w[starts] = np.where(deg > 0, rest * deg, 1).astype(np.float32)
+    body = np.ones(int(row_ptr[-1]), dtype=bool)
+    body[:n + 1] = False
+    body[starts] = False
+    col[body] = csr.col + 1
+    w[body] = float(c_num)
+    return CSR(n + 1, row_ptr, col, w)

@@ -1,0 +1,86 @@
+"""Full-size parity on R-MAT scale 20 (N = 2^20, nnz = 18,874,368), in the
+launch configuration the bench times (device-loop solve, MIXED precision):
+the estimate against the oracle's reference law, one move against the
+oracle's move of the same state, and the symmetrised graph against the
+closed form pi_i = d_i / sum d."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_02710_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+def Chain(*a, **k):
+    from paper_2008_02710_gb300.rlgl import Chain as C
+    return C(*a, **k)
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    csr = synth.rmat_chain(20, 16, seed=1)
+    p = oracle.transition_probs(csr)
+    ref, it, delta = oracle.power_iteration(csr, p, tol=1e-11, maxit=20000, nthreads=THREADS)
+    return csr, p, ref
+
+
+@pytest.mark.parametrize("sched", ["link_threshold", "all_green"])
+def test_rmat20_solve_reaches_1e6_against_oracle(rmat20, sched):
+    csr, p, ref = rmat20
+    with Chain(csr, precision="mixed") as ch:
+        ch.set_params(theta_scale=0.5)
+        info = ch.solve(sched, 0.0, tol=1e-8, max_steps=5000)
+        pi = ch.estimate()
+        inv = ch.invariant_residual()
+    assert info["status"] == "RLGL_OK"
+    assert np.abs(pi - ref).sum() <= 1e-6
+    assert abs(pi.sum() - 1.0) < 1e-12
+    assert inv <= 1e-6 * 2 ** -10  # re-derived before convergence was reported
+
+
+def test_rmat20_one_move_against_oracle(rmat20):
+    """The 6th push move of the per-link schedule from the GPU's own FP64
+    state equals the oracle's move of that state, node by node within the
+    FP64 rounding budget."""
+    csr, p, ref = rmat20
+    with Chain(csr, precision="fp64") as ch:
+        ch.set_params(theta_scale=0.5)
+        for _ in range(5):
+            ch.step("link_threshold", info=False)
+        c, h = ch.get_state()
+        g, th = oracle.select(c, oracle.LINK_THRESHOLD, theta_scale=0.5, row_ptr=csr.row_ptr)
+        info = ch.step("link_threshold")
+        c2, h2 = ch.get_state()
+    assert info["mode"] == 1 and 0 < info["green"] < csr.n
+    gpu_g = (h2 != h)
+    deg = np.diff(csr.row_ptr)
+    diff = np.nonzero(gpu_g != (g.astype(bool) & (c != 0)))[0]
+    for i in diff:  # ties within rounding of theta only
+        assert abs(abs(c[i]) / deg[i] - th) <= 1e-12 * th
+    C, H = c.copy(), h.copy()
+    oracle.move(csr, p, gpu_g.astype(np.uint8), C, H)
+    assert np.array_equal(h2, H)
+    A, HA = np.abs(c), np.zeros(csr.n)
+    oracle.move(csr, p, gpu_g.astype(np.uint8), A, HA)
+    rows = np.repeat(np.arange(csr.n), deg)
+    adds = np.bincount(csr.col, weights=gpu_g[rows].astype(float), minlength=csr.n)
+    budget = (adds + 4) * 2.0 ** -53 * A + 1e-300
+    assert np.all(np.abs(c2 - C) <= budget)
+
+
+@pytest.mark.parametrize("prec,bound", [("mixed", 1e-6), ("fp64", 1e-10)])
+def test_rmat20_undirected_degree_law(prec, bound):
+    csr = synth.rmat_chain(20, 16, seed=2, undirected=True)
+    d = csr.degrees().astype(np.float64)
+    with Chain(csr, precision=prec) as ch:
+        ch.set_params(theta_scale=0.5)
+        info = ch.solve("link_threshold", 0.0, tol=1e-9 if prec == "mixed" else 1e-13,
+                        max_steps=20000)
+        pi = ch.estimate()
+    assert info["status"] == "RLGL_OK"
+    assert np.abs(pi - d / d.sum()).sum() <= bound

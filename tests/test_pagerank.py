@@ -1,0 +1,129 @@
+"""PageRank through the RLGL sweep on the augmented chain P^(0) (Sec.
+2.3.2): pins of the construction on the CPU oracle, then the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_02710_gb300 import synth
+
+
+def _pagerank_closed_form(csr, c):
+    """pi* = (1 - c) s (I - c P)^-1 with uniform s (dense solve)."""
+    P = oracle.dense_P(csr, oracle.transition_probs(csr))
+    n = csr.n
+    s = np.full(n, 1.0 / n)
+    return np.linalg.solve((np.eye(n) - c * P).T, (1 - c) * s)
+
+
+def test_augmented_step0_is_gauss_southwell_initialisation():
+    """With M_0 = e_0, step 0 gives C_1 = (-(1-c), (1-c) s), H_1 = (1, 0):
+    the initialisation of Alg. 2 on the original nodes (Sec. 2.3.2)."""
+    g = synth.tiny_chain(64, seed=3)
+    g = synth.CSR(g.n, g.row_ptr, g.col, None)
+    aug = synth.pagerank_chain(g)
+    p = oracle.transition_probs(aug)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    C, H = oracle.initial_step(aug, p, m0)
+    assert abs(C[0] + 0.15) < 1e-16
+    assert np.abs(C[1:] - 0.15 / 64).max() < 1e-17
+    assert H[0] == 1.0 and not H[1:].any()
+
+
+@pytest.mark.parametrize("sched", [oracle.ALL_GREEN, oracle.LINK_THRESHOLD, oracle.THRESHOLD])
+def test_augmented_chain_gives_pagerank(sched):
+    g = synth.rmat_chain(9, 8, seed=4)
+    aug = synth.pagerank_chain(g)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    pi, C, H, info = oracle.run(aug, sched=sched, m0=m0, theta_scale=0.5, tol=1e-13,
+                                max_steps=100000)
+    assert info["status"] == "OK"
+    ref = _pagerank_closed_form(g, 0.85)
+    assert abs(pi[0] - 0.5) < 1e-12          # x_0 = sum y when p_00 = c
+    y = pi[1:] / pi[1:].sum()
+    assert np.abs(y - ref).sum() < 1e-11
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-11), ("mixed", 1e-6)])
+def test_pagerank_on_gpu(prec, bound):
+    from paper_2008_02710_gb300 import pagerank
+    g = synth.rmat_chain(12, 16, seed=5)
+    y, info = pagerank.solve(g, tol=1e-13 if prec == "fp64" else 1e-9, precision=prec)
+    assert info["status"] == "RLGL_OK"
+    assert np.abs(y - _pagerank_closed_form(g, 0.85)).sum() <= bound
+
+
+@pytest.mark.gpu
+def test_pagerank_degenerate_schedule_on_gpu():
+    """The GPU path ends the degenerate run (node 0 alone green, H 1 -> 0)
+    the way the oracle does: without convergence, H 1 vanishing."""
+    from paper_2008_02710_gb300.rlgl import Chain
+    g = synth.tiny_chain(40, seed=2)
+    aug = synth.pagerank_chain(synth.CSR(g.n, g.row_ptr, g.col, None))
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    with Chain(aug, m0=m0, precision="fp64") as ch:
+        for t in range(1, 11):
+            ch.step("threshold", info=False)
+        _, h = ch.get_state()
+        assert abs(h.sum() - 0.85 ** 10) < 1e-14
+        info = ch.solve("threshold", tol=1e-12, max_steps=3000, raise_on_noconv=False)
+    assert info["status"] == "RLGL_ENOCONV" and abs(info["sum_hist"]) < 1e-9
+
+
+def test_dangling_nodes_follow_restart_law():
+    """Dangling rows: the normalised original-node part equals the
+    eigenvector of the Google matrix whose dangling rows are s."""
+    n = 40
+    rng = np.random.default_rng(8)
+    src, dst = [], []
+    for i in range(n):
+        if i % 7 == 3:
+            continue                       # dangling
+        for j in rng.choice(n, size=3, replace=False):
+            src.append(i)
+            dst.append(int(j))
+    g = synth.edges_to_csr(n, np.array(src, np.int32), np.array(dst, np.int32), None)
+    aug = synth.pagerank_chain(g)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    pi, C, H, info = oracle.run(aug, sched=oracle.LINK_THRESHOLD, m0=m0, theta_scale=0.5,
+                                tol=1e-14, max_steps=100000)
+    assert info["status"] == "OK" and info["hsum"] > 0.1
+    y = pi[1:] / pi[1:].sum()
+    P = np.zeros((n, n))
+    for i, j in zip(src, dst):
+        P[i, j] += 1.0
+    deg = P.sum(1)
+    P[deg > 0] /= deg[deg > 0, None]
+    P[deg == 0] = 1.0 / n
+    G = 0.85 * P + 0.15 / n
+    w, v = np.linalg.eig(G.T)
+    ref = np.real(v[:, np.argmin(np.abs(w - 1))])
+    ref /= ref.sum()
+    assert np.abs(y - ref).sum() < 1e-11
+
+
+def test_aux_node_alone_green_degenerates():
+    """With uniform s and the |C| threshold at scale 1, only node 0 passes at
+    first (|C_0| = 1 - c against a mean of 2(1 - c)/(N + 1)). Moving node 0
+    alone keeps a share c of its negative cash on itself and sends the rest
+    to cancel the positive cash: H 1 = c^t after t such moves, so H tends to
+    0 and the estimate H / H 1 degenerates; the solve ends without
+    convergence."""
+    g = synth.tiny_chain(40, seed=2)
+    g = synth.CSR(g.n, g.row_ptr, g.col, None)
+    aug = synth.pagerank_chain(g)
+    p = oracle.transition_probs(aug)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    C, H = oracle.initial_step(aug, p, m0)
+    for t in range(1, 21):
+        green, _ = oracle.select(C, oracle.THRESHOLD, 1.0)
+        assert green[0] == 1 and green.sum() == 1
+        oracle.move(aug, p, green, C, H)
+        assert abs(H.sum() - 0.85 ** t) < 1e-14
+    pi, C, H, info = oracle.run(aug, sched=oracle.THRESHOLD, m0=m0, tol=1e-12, max_steps=3000)
+    assert info["status"] == "ENOCONV" and abs(info["hsum"]) < 1e-9
