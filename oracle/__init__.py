@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD = 0, 1, 2, 3, 4
+ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD, BLOCK_RR, PC = 0, 1, 2, 3, 4, 5, 6
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOTSTOCHASTIC", 5: "EDEGENERATE", 6: "ENOCONV"}
 
 
@@ -52,7 +52,12 @@ def _load():
             L.oracle_initial_step.restype = None
             L.oracle_initial_step.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.oracle_select.restype = dbl
-            L.oracle_select.argtypes = [i64, vp, vp, i32, dbl, i32, dbl, dbl, vp, vp]
+            L.oracle_select.argtypes = [i64, vp, vp, i32, dbl, i32, dbl, dbl, vp, i64, i64, dbl,
+                                        ctypes.c_uint64, vp]
+            L.oracle_pc_uniform.restype = dbl
+            L.oracle_pc_uniform.argtypes = [ctypes.c_uint64, i64, i64]
+            L.oracle_sm64_next.restype = ctypes.c_uint64
+            L.oracle_sm64_next.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
             L.oracle_l1.restype = dbl
             L.oracle_l1.argtypes = [i64, vp]
             L.oracle_sum.restype = dbl
@@ -61,7 +66,8 @@ def _load():
             L.oracle_invariant_residual.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.oracle_solve.restype = ctypes.c_int
             L.oracle_solve.argtypes = [i64, vp, vp, vp, i32, dbl, i32, dbl, dbl, vp, i64,
-                                       i64, dbl, i64, vp, vp, i64, vp, vp]
+                                       i64, dbl, i64, vp, vp, i64, vp, vp, i64, i64, dbl,
+                                       ctypes.c_uint64]
             L.oracle_estimate.restype = ctypes.c_int
             L.oracle_estimate.argtypes = [i64, vp, vp]
             L.oracle_power_iteration.restype = i64
@@ -101,9 +107,11 @@ def initial_step(csr, p, m0: Optional[np.ndarray] = None):
 
 
 def select(C, sched: int, theta_scale: float = 1.0, r: int = 1, abs_theta: float = 0.0,
-           top_frac: float = 0.01, mask=None, row_ptr=None):
+           top_frac: float = 0.01, mask=None, row_ptr=None, move: int = 0, rr_blocks: int = 8,
+           pc_frac: float = 0.05, seed: int = 0):
     """Green set of the schedule for cash C: returns (green uint8[n], theta).
-    row_ptr (the CSR offsets) is needed by LINK_THRESHOLD only."""
+    row_ptr (the CSR offsets) is needed by LINK_THRESHOLD only; move (t,
+    counted from step 0), rr_blocks, pc_frac and seed by BLOCK_RR and PC."""
     L = _load()
     C = _f64(C)
     green = np.empty(C.shape[0], dtype=np.uint8)
@@ -112,7 +120,7 @@ def select(C, sched: int, theta_scale: float = 1.0, r: int = 1, abs_theta: float
     if sched == LINK_THRESHOLD and rp is None:
         raise ValueError("LINK_THRESHOLD needs row_ptr")
     th = L.oracle_select(C.shape[0], _p(rp), _p(C), sched, theta_scale, r, abs_theta, top_frac,
-                         _p(mk), _p(green))
+                         _p(mk), move, rr_blocks, pc_frac, seed, _p(green))
     return green, th
 
 
@@ -147,7 +155,8 @@ def invariant_residual(csr, p, C, H, c0=None) -> float:
 
 def solve(csr, p, C, H, sched: int = THRESHOLD, theta_scale: float = 1.0, r: int = 1,
           abs_theta: float = 0.0, top_frac: float = 0.01, masks=None, safety_every: int = 0,
-          tol: float = 1e-12, max_steps: int = 100000, check_every: int = 0):
+          tol: float = 1e-12, max_steps: int = 100000, check_every: int = 0, move0: int = 0,
+          rr_blocks: int = 8, pc_frac: float = 0.05, seed: int = 0):
     """Algorithm 1 from state (C, H) (modified in place). Returns a dict with
     status, moves, resid (||C||_1/|H 1|), pushes, hsum and the worst
     per-step invariant values when check_every >= 0."""
@@ -161,12 +170,25 @@ def solve(csr, p, C, H, sched: int = THRESHOLD, theta_scale: float = 1.0, r: int
     out = np.zeros(4)
     st = L.oracle_solve(csr.n, _p(csr.row_ptr), _p(csr.col), _p(p), sched, theta_scale, r,
                         abs_theta, top_frac, _p(mk), period, safety_every, tol, max_steps,
-                        _p(C), _p(H), check_every, _p(chk), _p(out))
+                        _p(C), _p(H), check_every, _p(chk), _p(out), move0, rr_blocks,
+                        pc_frac, seed)
     res = dict(status=STATUS.get(st, st), moves=int(out[0]), resid=float(out[1]),
                pushes=float(out[2]), hsum=float(out[3]))
     if chk is not None:
         res.update(sum_cash=float(chk[0]), l1_growth=float(chk[1]), invariant=float(chk[2]))
     return res
+
+
+def sm64_outputs(state: int, count: int):
+    """The first `count` outputs of SplitMix64 from `state` (sequential form)."""
+    L = _load()
+    st = ctypes.c_uint64(state)
+    return [L.oracle_sm64_next(ctypes.byref(st)) for _ in range(count)]
+
+
+def pc_uniform(seed: int, t: int, i: int) -> float:
+    """u_{t,i} of the PC schedule (SplitMix64, counter-based)."""
+    return _load().oracle_pc_uniform(seed, t, i)
 
 
 def estimate(H) -> np.ndarray:

@@ -23,7 +23,7 @@
 #include <string.h>
 
 enum { SCHED_ALL_GREEN = 0, SCHED_THRESHOLD = 1, SCHED_TOPFRAC = 2, SCHED_MASK = 3,
-       SCHED_LINK_THRESHOLD = 4 };
+       SCHED_LINK_THRESHOLD = 4, SCHED_BLOCK_RR = 5, SCHED_PC = 6 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOTSTOCHASTIC = 2, OR_EDEGENERATE = 5, OR_ENOCONV = 6 };
 
 /*
@@ -116,6 +116,34 @@ static int cmp_desc(const void* a, const void* b) {
 }
 
 /*
+ * Uniform numbers of the PC schedule: the counter-based form of SplitMix64
+ * (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014). Its k-th output for seed s is mix(s + k g), with
+ * g = 0x9E3779B97F4A7C15 and mix the generator's output function below.
+ * Move t draws for node i the value
+ *   u_{t,i} = 2^-53 floor(mix(key_t + (i + 1) g) / 2^11),
+ *   key_t = mix(seed + (t + 1) g),
+ * a double in [0, 1).
+ */
+static uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* The generator in its sequential form: state += g, return mix(state). */
+uint64_t oracle_sm64_next(uint64_t* state) {
+    *state += 0x9E3779B97F4A7C15ull;
+    return sm64_mix(*state);
+}
+
+double oracle_pc_uniform(uint64_t seed, int64_t t, int64_t i) {
+    const uint64_t g = 0x9E3779B97F4A7C15ull;
+    const uint64_t key = sm64_mix(seed + (uint64_t)(t + 1) * g);
+    return (double)(sm64_mix(key + (uint64_t)(i + 1) * g) >> 11) * 0x1.0p-53;
+}
+
+/*
  * Green-light schedules (Sec. 6, cash-dependent heuristics), in the
  * synchronous data-parallel form:
  *   ALL_GREEN : G = [N]                           (power iteration, Sec. 2.3.1)
@@ -131,10 +159,22 @@ static int cmp_desc(const void* a, const void* b) {
  *   TOPFRAC   : k = ceil(f N); theta = the k-th largest |C_i|;
  *               G = {i : |C_i| >= theta, C_i != 0} (ties all included;
  *               RLGL_MaxC widened to "large, not necessarily largest");
- *   MASK      : G = {i : mask_i != 0}.
+ *   MASK      : G = {i : mask_i != 0};
+ *   BLOCK_RR  : the nodes cut into contiguous blocks of b = ceil(N / K) nodes
+ *               (K = rr_blocks, at most N), K' = ceil(N / b) of them; move t
+ *               (t = 0, 1, ... counted from step 0) greens block t mod K':
+ *               G = {i : floor(i / b) = t mod K'}: RLGL_RR of Sec. 6 taken a
+ *               block at a time, a generalized cyclic G (Sec. 3.2, Eq.
+ *               cycle) with m = K';
+ *   PC        : each node with C_i != 0 is green with probability
+ *               p_i = min(1, k |C_i| / ||C||_1), k = pc_frac N, decided by
+ *               u_{t,i} < p_i (oracle_pc_uniform): RLGL_PC of Sec. 6 (one
+ *               node drawn with probability proportional to |C_i|) with
+ *               about k nodes drawn at once, independently.
  * Zero-cash nodes are left out of the cash-dependent sets; moving zero cash
- * changes nothing. row_ptr is read only by LINK_THRESHOLD. Writes green[] and
- * returns theta (0 for ALL_GREEN/MASK).
+ * changes nothing. row_ptr is read only by LINK_THRESHOLD. `move` is t for
+ * BLOCK_RR and PC. Writes green[] and returns theta (0 for the schedules
+ * without a threshold).
  */
 static double select_value(int32_t sched, const int64_t* row_ptr, const double* C, int64_t i) {
     if (sched == SCHED_LINK_THRESHOLD) return fabs(C[i]) / (double)(row_ptr[i + 1] - row_ptr[i]);
@@ -143,8 +183,30 @@ static double select_value(int32_t sched, const int64_t* row_ptr, const double* 
 
 double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t sched,
                      double theta_scale, int32_t r, double abs_theta, double top_frac,
-                     const uint8_t* mask, uint8_t* green) {
+                     const uint8_t* mask, int64_t move, int64_t rr_blocks, double pc_frac,
+                     uint64_t seed, uint8_t* green) {
     double theta = 0.0;
+    if (sched == SCHED_BLOCK_RR) {
+        int64_t K = rr_blocks < 1 ? 1 : (rr_blocks > n ? n : rr_blocks);
+        int64_t b = (n + K - 1) / K;
+        int64_t nblocks = (n + b - 1) / b;
+        int64_t cur = move % nblocks;
+        for (int64_t i = 0; i < n; ++i) green[i] = (i / b == cur) ? 1 : 0;
+        return 0.0;
+    }
+    if (sched == SCHED_PC) {
+        double l1 = 0.0;
+        for (int64_t j = 0; j < n; ++j) l1 += fabs(C[j]);
+        const double k = pc_frac * (double)n;
+        for (int64_t i = 0; i < n; ++i) {
+            green[i] = 0;
+            if (C[i] == 0.0 || l1 == 0.0) continue;
+            double pi_ = k * fabs(C[i]) / l1;
+            if (pi_ > 1.0) pi_ = 1.0;
+            green[i] = (oracle_pc_uniform(seed, move, i) < pi_) ? 1 : 0;
+        }
+        return 0.0;
+    }
     if (sched == SCHED_ALL_GREEN) {
         for (int64_t i = 0; i < n; ++i) green[i] = 1;
         return 0.0;
@@ -228,13 +290,16 @@ double oracle_invariant_residual(int64_t n, const int64_t* row_ptr, const int32_
  * Theorem 6's proof), check[2] = max invariant residual / sum|H| (every
  * check_every steps when check_every > 0).
  * out[0] = moves made, out[1] = ||C||_1/|H 1| at exit, out[2] = edge pushes
- * (sum over moves of sum_{i in G} deg_i), out[3] = H 1.
+ * (sum over moves of sum_{i in G} deg_i), out[3] = H 1. move0 = moves made
+ * since step 0 before this call (the t of BLOCK_RR and PC); rr_blocks,
+ * pc_frac and seed: see oracle_select.
  */
 int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* p,
                  int32_t sched, double theta_scale, int32_t r, double abs_theta,
                  double top_frac, const uint8_t* mask, int64_t mask_period,
                  int64_t safety_every, double tol, int64_t max_steps, double* C, double* H,
-                 int64_t check_every, double* check, double* out) {
+                 int64_t check_every, double* check, double* out, int64_t move0,
+                 int64_t rr_blocks, double pc_frac, uint64_t seed) {
     uint8_t* green = (uint8_t*)malloc((size_t)n);
     int64_t moves = 0;
     double pushes = 0.0;
@@ -249,7 +314,8 @@ int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const do
         int32_t s = sched;
         if (safety_every > 0 && (moves + 1) % safety_every == 0) s = SCHED_ALL_GREEN;
         const uint8_t* mk = (s == SCHED_MASK) ? mask + (size_t)((moves % mask_period) * n) : NULL;
-        oracle_select(n, row_ptr, C, s, theta_scale, r, abs_theta, top_frac, mk, green);
+        oracle_select(n, row_ptr, C, s, theta_scale, r, abs_theta, top_frac, mk, move0 + moves,
+                      rr_blocks, pc_frac, seed, green);
         double st[3];
         oracle_move(n, row_ptr, col, p, green, C, H, st);
         ++moves;

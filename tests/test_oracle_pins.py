@@ -410,3 +410,137 @@ def test_not_stochastic_rejected():
     csr = synth.edges_to_csr(3, np.array([0, 1]), np.array([1, 0]), None)
     with pytest.raises(ValueError):
         oracle.transition_probs(csr)
+
+
+# ------------------------------------------- block round robin and PC
+
+def test_splitmix64_published_outputs():
+    """The PC schedule's generator against the reference outputs of
+    SplitMix64 from state 0 (Steele, Lea and Flood 2014; the published
+    reference implementation's first three values)."""
+    assert oracle.sm64_outputs(0, 3) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                         0x06C45D188009454F]
+
+
+def test_pc_uniforms_are_uniform_and_counter_based():
+    u = np.array([[oracle.pc_uniform(7, t, i) for i in range(2000)] for t in range(5)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    # same counter, same value; different moves differ
+    assert oracle.pc_uniform(7, 3, 11) == u[3, 11]
+    assert not np.array_equal(u[0], u[1])
+    # Kolmogorov-Smirnov against U(0,1) at the 1e-4 level
+    from scipy import stats
+    assert stats.kstest(u.ravel(), "uniform").pvalue > 1e-4
+    # u is a multiple of 2^-53 (53 high bits of the 64-bit output)
+    assert np.all(u * 2.0 ** 53 == np.floor(u * 2.0 ** 53))
+
+
+@pytest.mark.parametrize("n,K", [(10, 4), (10, 6), (1000, 7), (1000, 1), (5, 9)])
+def test_block_rr_partitions_the_nodes(n, K):
+    """K' consecutive moves green every node exactly once, in contiguous
+    blocks of ceil(N / K) nodes taken in order."""
+    b = -(-n // min(K, n))
+    kp = -(-n // b)
+    C = np.ones(n)
+    seen = np.zeros(n, int)
+    for t in range(kp):
+        g, _ = oracle.select(C, oracle.BLOCK_RR, move=t, rr_blocks=K)
+        idx = np.nonzero(g)[0]
+        assert idx.min() == t * b and idx.max() == min(n, (t + 1) * b) - 1
+        assert len(idx) == idx.max() - idx.min() + 1
+        seen += g
+    assert np.all(seen == 1)
+    g, _ = oracle.select(C, oracle.BLOCK_RR, move=kp, rr_blocks=K)  # the cycle restarts
+    assert np.nonzero(g)[0].min() == 0
+
+
+def test_block_rr_one_block_is_power_iteration():
+    csr = synth.tiny_chain(300, seed=4)
+    p = oracle.transition_probs(csr)
+    C1, H1 = oracle.initial_step(csr, p)
+    C2, H2 = C1.copy(), H1.copy()
+    oracle.solve(csr, p, C1, H1, sched=oracle.BLOCK_RR, rr_blocks=1, tol=0.0, max_steps=40)
+    oracle.solve(csr, p, C2, H2, sched=oracle.ALL_GREEN, tol=0.0, max_steps=40)
+    assert np.array_equal(C1, C2) and np.array_equal(H1, H2)
+
+
+def test_block_rr_equals_the_same_masks_and_converges():
+    """BLOCK_RR is the MASK schedule with the block masks (a generalized
+    cyclic G, Sec. 3.2); it converges to the stationary law."""
+    csr = synth.tiny_chain(500, seed=6)
+    p = oracle.transition_probs(csr)
+    K = 7
+    b = -(-csr.n // K)
+    masks = np.zeros((K, csr.n), np.uint8)
+    for k in range(K):
+        masks[k, k * b:(k + 1) * b] = 1
+    C1, H1 = oracle.initial_step(csr, p)
+    C2, H2 = C1.copy(), H1.copy()
+    i1 = oracle.solve(csr, p, C1, H1, sched=oracle.BLOCK_RR, rr_blocks=K, tol=1e-12,
+                      max_steps=100000)
+    i2 = oracle.solve(csr, p, C2, H2, sched=oracle.MASK, masks=masks, tol=1e-12, max_steps=100000)
+    assert i1["status"] == i2["status"] == "OK" and i1["moves"] == i2["moves"]
+    assert np.array_equal(H1, H2)
+    ref = oracle.gth(oracle.dense_P(csr, p))
+    assert np.abs(oracle.estimate(H1) - ref).sum() < 1e-10
+
+
+def test_pc_large_k_is_all_nonzero_nodes():
+    """With k |C_i| / ||C||_1 >= 1 for every nonzero C_i, every node with cash
+    is green: the trajectory is power iteration's."""
+    csr = synth.tiny_chain(300, seed=4)
+    p = oracle.transition_probs(csr)
+    C1, H1 = oracle.initial_step(csr, p)
+    C2, H2 = C1.copy(), H1.copy()
+    oracle.solve(csr, p, C1, H1, sched=oracle.PC, pc_frac=1e30, tol=0.0, max_steps=30)
+    oracle.solve(csr, p, C2, H2, sched=oracle.ALL_GREEN, tol=0.0, max_steps=30)
+    assert np.array_equal(C1, C2) and np.array_equal(H1, H2)
+
+
+def test_pc_inclusion_frequencies():
+    """Node i is green with probability min(1, k |C_i| / ||C||_1): over many
+    moves (fresh draws each t) the counts match within 5 standard deviations."""
+    rng = np.random.default_rng(3)
+    n = 200
+    C = rng.normal(size=n) * np.where(rng.random(n) < 0.1, 20.0, 1.0)
+    C[::17] = 0.0
+    k = 0.05 * n
+    pi_ = np.minimum(1.0, k * np.abs(C) / np.abs(C).sum())
+    T = 4000
+    cnt = np.zeros(n)
+    for t in range(T):
+        g, _ = oracle.select(C, oracle.PC, move=t, pc_frac=0.05, seed=11)
+        cnt += g
+    sd = np.sqrt(T * pi_ * (1 - pi_)) + 1e-9
+    assert np.all(np.abs(cnt - T * pi_) <= 5 * sd + 1e-9)
+    assert np.all(cnt[C == 0] == 0)
+    assert np.all(cnt[pi_ == 1.0] == T)
+
+
+def test_pc_converges():
+    csr = synth.tiny_chain(500, seed=6)
+    pi, C, H, info = oracle.run(csr, sched=oracle.PC, pc_frac=0.2, seed=5, tol=1e-12,
+                                max_steps=200000)
+    p = oracle.transition_probs(csr)
+    assert info["status"] == "OK"
+    assert np.abs(pi - oracle.gth(oracle.dense_P(csr, p))).sum() < 1e-10
+
+
+def test_block_rr_dobrushin_bound():
+    """Sec. 3.2: for delta(P) < 1 (Eq. dobrushin) and a deterministic G that
+    greens every node within m moves (Eq. cycle), ||C_t||_1 <=
+    2 delta^-1 delta^(t/m). BLOCK_RR with K blocks has m = K."""
+    rng = np.random.default_rng(12)
+    n, K = 40, 5
+    W = rng.random((n, n)) ** 3 + 0.01
+    W = np.round(W * 2 ** 20) / 2 ** 20
+    csr = synth.from_dense(W)
+    p = oracle.transition_probs(csr)
+    P = oracle.dense_P(csr, p)
+    delta = 1.0 - min(np.minimum(P[i], P[k]).sum() for i in range(n) for k in range(n))
+    assert 0 < delta < 1
+    C, H = oracle.initial_step(csr, p)
+    for t in range(1, 121):
+        g, _ = oracle.select(C, oracle.BLOCK_RR, move=t - 1, rr_blocks=K)
+        oracle.move(csr, p, g, C, H)
+        assert np.abs(C).sum() <= 2.0 / delta * delta ** (t / K) + 1e-15
