@@ -46,7 +46,7 @@ if ROOT not in sys.path:
 METRIC = "time to L1 err 1e-6 & edge-pushes/s, RLGL sched vs all-green, % HBM peak"
 UNIT = "edge-pushes/s"
 ERR_TARGET = 1e-6
-KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh")
+KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh", "sweep")
 
 WORKLOADS = {
     # name: (scale, edge_factor, weighted, precision)
@@ -305,6 +305,18 @@ class GpuRun:
                 alg["topk"] += (3 if cash == 4 else 6) * n * cash
         return kt, alg
 
+    def sweep_profile(self, sched, theta, tstar, alg):
+        """T* moves of the persistent sweep launched eagerly, each launch
+        timed with CUDA events on the context's stream; the algorithmic
+        bytes of those moves are the sum over the phases (the same moves as
+        the per-phase profile, so the same bytes)."""
+        ch = self.chain
+        ch.reset(self.m0)
+        ch.profile(2)
+        kt = ch.profile_sweep(sched, theta, tstar)
+        ch.profile(2)
+        return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull"))
+
     def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0):
         """Through the public API with host buffers: every step uploads the
         chain from pinned host memory (create), solves, and reads pi back."""
@@ -409,11 +421,27 @@ def run_gpu(args):
         raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves")
     tstar = cal[head]["tstar"]
 
-    # kernel profile of the headline schedule (CUDA events on the context stream)
+    # kernel profile of the headline schedule (CUDA events on the context
+    # stream): per phase on the one-kernel-per-phase path, then the
+    # persistent sweep that the timed solves run
     sched_h, theta_h, _ = use(head)
+    g.chain.set_params(persistent=0)
     nvtx.range_push("profile")
     kt, alg = g.kernel_profile(sched_h, theta_h, tstar)
     nvtx.range_pop()
+    g.chain.set_params(persistent=args.persistent)
+    sweep_on = args.persistent == 1 and head != "topfrac"
+    if sweep_on:
+        nvtx.range_push("profile_sweep")
+        (ms_sw, n_sw), bytes_sw = g.sweep_profile(sched_h, theta_h, tstar, alg)
+        nvtx.range_pop()
+    # the headline schedule on the one-kernel-per-phase path, for comparison
+    phase_ms = None
+    if sweep_on and not args.skip_compare:
+        g.chain.set_params(persistent=0)
+        ts, _ = g.timed_solves(sched_h, theta_h, tstar, max(3, args.steps // 2), 3)
+        phase_ms = float(np.median(ts))
+        g.chain.set_params(persistent=1)
 
     # comparison schedules, timed the same way
     compare = {}
@@ -459,17 +487,26 @@ def run_gpu(args):
     e2e_t = max_over_ranks(dist, float(np.sum(et)), device)
     e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
 
-    # roofline of the dominant kernel class (most device time in the profile;
-    # classes whose launches returned at once carry no algorithmic bytes)
-    dom = max((k for k in KERNEL_CLASSES if alg[k] > 0), key=lambda k: kt[k][0])
-    ms_dom, n_dom = kt[dom]
-    bytes_dom = alg[dom]
+    # roofline of the dominant kernel: the persistent sweep when the timed
+    # solves run it (every move's work is in it), else the phase class with
+    # the most device time (classes whose launches returned at once carry no
+    # algorithmic bytes)
+    if sweep_on:
+        dom, ms_dom, n_dom, bytes_dom = "sweep", ms_sw, n_sw, bytes_sw
+    else:
+        dom = max((k for k in KERNEL_CLASSES if alg[k] > 0), key=lambda k: kt[k][0])
+        ms_dom, n_dom = kt[dom]
+        bytes_dom = alg[dom]
     peak, peak_src = measured_peaks()
-    # time of the launches that did the work: for push/pull the launches of
-    # the other mode return at once and are a few microseconds each
     achieved = bytes_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
-    kernels_per_iter = (7 if head == "topfrac" else 4) + (3 if wl["precision"] == "mixed" else 0)
-    launches = args.steps * (kernels_per_iter * iters + 1 + 5 + 2)
+    refreshes = infos[0]["refreshes"]
+    if sweep_on:
+        # reset (5), begin (1), sweep launches (1 + one per re-derivation),
+        # re-derivation kernels (3 each), estimate (2)
+        launches = args.steps * (5 + 1 + (1 + refreshes) + 3 * refreshes + 2)
+    else:
+        kernels_per_iter = (7 if head == "topfrac" else 4) + (3 if wl["precision"] == "mixed" else 0)
+        launches = args.steps * (kernels_per_iter * iters + 1 + 5 + 2)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -487,6 +524,8 @@ def run_gpu(args):
                                **{k: v.get("edges") for k, v in compare.items()}},
         "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step)
         if compare.get("all_green", {}).get("ms") else None,
+        "persistent_sweep": sweep_on,
+        "time_to_err_ms_phase_kernels": phase_ms,
         "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
         "final_l1_err": final_err,
         "reference": {"kind": "oracle power iteration (FP64, host)", **ref_info},
@@ -496,8 +535,8 @@ def run_gpu(args):
                      "traffic": traffic_from_profiles(dom, args.workload),
                      "launches": n_dom, "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
                      "alg_bytes_per_launch": bytes_dom / max(n_dom, 1)},
-        "kernel_ms": {k: v[0] for k, v in kt.items()},
-        "kernel_launches": {k: v[1] for k, v in kt.items()},
+        "phase_kernel_ms": {k: v[0] for k, v in kt.items() if k != "sweep"},
+        "phase_kernel_launches": {k: v[1] for k, v in kt.items() if k != "sweep"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * e2e_t / len(et)},
         "gpu_launches": launches,
@@ -676,6 +715,8 @@ def main(argv=None):
     ap.add_argument("--theta-scale", type=float, default=0.5,
                     help="theta_scale of the per-link threshold schedule")
     ap.add_argument("--max-moves", type=int, default=20000)
+    ap.add_argument("--persistent", type=int, choices=[0, 1], default=1,
+                    help="1: solves run as the persistent sweep; 0: one kernel per phase")
     ap.add_argument("--skip-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")

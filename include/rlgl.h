@@ -64,13 +64,27 @@ typedef enum {
  *              G = {i : v_i >= theta, C_i != 0}, theta = the call's theta when
  *              > 0, else params.theta_scale * (sum_j v_j^r / N)^(1/r). Moving
  *              node i costs d_i links, the paper's unit of work (Sec. 6), so v_i
- *              is the cash moved per link used. */
+ *              is the cash moved per link used.
+ *  BLOCK_RR  : RLGL_RR (Sec. 6) a block at a time: nodes in contiguous blocks
+ *              of b = ceil(N / K) nodes, K = params.rr_blocks clipped to
+ *              [1, N]; move t (t - 1 = moves made since step 0) greens block
+ *              (t - 1) mod ceil(N / b). A generalized cyclic G (Sec. 3.2).
+ *  PC        : RLGL_PC (Sec. 6) drawing about k = params.pc_frac N nodes at
+ *              once: node i is green when C_i != 0 and
+ *              u ||C||_1 < k |C_i| (in FP64), u the SplitMix64 draw of node i
+ *              for this move: key = mix(seed + t g), u = 2^-53 *
+ *              floor(mix(key + (i + 1) g) / 2^11), g = 0x9E3779B97F4A7C15,
+ *              mix the generator's output function (Steele, Lea and Flood,
+ *              OOPSLA 2014).
+ *  BLOCK_RR and PC serve single chains only (EINVAL in batch mode). */
 typedef enum {
     RLGL_ALL_GREEN = 0,
     RLGL_THRESHOLD = 1,
     RLGL_TOPFRAC = 2,
     RLGL_MASK = 3,
-    RLGL_LINK_THRESHOLD = 4
+    RLGL_LINK_THRESHOLD = 4,
+    RLGL_BLOCK_RR = 5,
+    RLGL_PC = 6
 } rlgl_schedule;
 
 /* FP64: cash, moved cash and history in FP64.
@@ -92,6 +106,13 @@ typedef struct {
     int32_t safety_every;   /* every K-th move of a solve is all-green (0 = never, default) */
     double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-3; 0 = only at the end) */
     double time_limit_s;    /* wall-clock limit of one rlgl_solve, checked on the device (default 600) */
+    int64_t rr_blocks;      /* BLOCK_RR: number of blocks K (default 8) */
+    double pc_frac;         /* PC: expected green fraction k / N before capping (default 0.05) */
+    uint64_t seed;          /* PC: seed of the counter-based draws (default 0) */
+    int32_t persistent;     /* 1 (default): a single-chain solve with any schedule but TOPFRAC runs
+                               as one persistent cooperative kernel per stretch between FP64
+                               re-derivations of the cash, with grid barriers between the phases
+                               of a move; 0: one kernel per phase. Same moves either way. */
 } rlgl_params;
 
 typedef struct {
@@ -251,8 +272,8 @@ rlgl_status rlgl_get_params(const rlgl_ctx* ctx, rlgl_params* p);
 /* Per-kernel-class device time (ms) and launch counts accumulated while
  * profiling is on (rlgl_profile(ctx, 1)): eager moves then record a CUDA
  * event pair around every kernel on the context's stream. Classes, in order:
- * 0 stats, 1 select, 2 push, 3 pull, 4 top-k select, 5 refresh.
- * ms[6], launches[6]. rlgl_profile(ctx, 0) stops and clears nothing;
+ * 0 stats, 1 select, 2 push, 3 pull, 4 top-k select, 5 refresh,
+ * 6 persistent sweep. ms[7], launches[7]. rlgl_profile(ctx, 0) stops and clears nothing;
  * rlgl_profile(ctx, 2) clears. */
 rlgl_status rlgl_profile(rlgl_ctx* ctx, int32_t mode);
 rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches);
@@ -262,6 +283,15 @@ rlgl_status rlgl_kernel_times(rlgl_ctx* ctx, double* ms, int64_t* launches);
  * kernel, so each pair measures the kernel's own device time. Adds to the
  * totals read by rlgl_kernel_times. Synchronises. */
 rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves);
+
+/* Profiling run of the persistent sweep (params.persistent): `moves` moves
+ * made as a solve with tol 0 and max_steps = moves, the sweep launched
+ * eagerly with a CUDA event pair around each launch (class 6) and around
+ * each FP64 re-derivation kernel (class 5). EINVAL when the sweep does not
+ * serve the context (batch) or the schedule (TOPFRAC). Synchronises; the
+ * solve ends with status ENOCONV on the device, which this call does not
+ * report. */
+rlgl_status rlgl_profile_sweep(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves);
 
 /* Copies the log of the last min(count, 65536) moves, oldest first, into
  * out (host, count entries); *written receives the number copied. The log

@@ -18,6 +18,7 @@
 
 #include "../../include/rlgl.h"
 #include "rlgl_kernels.cuh"
+#include "rlgl_sweep.cuh"
 
 using namespace rlgl;
 
@@ -25,7 +26,7 @@ namespace {
 
 thread_local char g_thread_err[512] = "";
 
-enum KClass { KC_STATS = 0, KC_SELECT, KC_PUSH, KC_PULL, KC_TOPK, KC_REFRESH, KC_N };
+enum KClass { KC_STATS = 0, KC_SELECT, KC_PUSH, KC_PULL, KC_TOPK, KC_REFRESH, KC_SWEEP, KC_N };
 
 struct ProfEv {
     int cls;
@@ -76,6 +77,7 @@ struct rlgl_ctx {
     unsigned int* err = nullptr;
     MoveRecord* log = nullptr;
     DevState* st = nullptr;
+    SweepState* sw = nullptr;  // grid barrier and per-move slots of the persistent sweep
     // batch of independent chains (nchains > 1): node -> chain map and
     // per-chain state; nchains == 1 is a single chain
     int nchains = 1;
@@ -90,7 +92,10 @@ struct rlgl_ctx {
     // launch shapes
     int grid_nodes = 1, grid_select = 1, grid_push = 1, grid_pull = 1, grid_stats = 1;
     // solve graphs, one per schedule
-    cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // solve graph of the persistent sweep (any schedule it serves) and its grid
+    cudaGraphExec_t sweep_graph = nullptr;
+    int grid_sweep = 0;
     // profiling
     int profiling = 0;
     std::vector<ProfEv> prof;
@@ -373,6 +378,96 @@ static rlgl_status enqueue_pull(Launch L) {
     return RLGL_OK;
 }
 
+// The persistent sweep (rlgl_sweep.cuh): one cooperative launch of
+// ctx->grid_sweep blocks, never more than fit on the device at once.
+template <typename T, bool kHasW>
+static rlgl_status launch_sweep(rlgl_ctx* ctx, const SweepArgs<T>& a) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)ctx->grid_sweep);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    memset(attr, 0, sizeof attr);
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(ctx, cudaLaunchKernelEx(&cfg, k_sweep<T, kHasW>, a));
+    return RLGL_OK;
+}
+
+template <typename T>
+static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
+    rlgl_ctx* ctx = L.ctx;
+    SweepArgs<T> a;
+    a.c = (T*)ctx->c;
+    a.H = ctx->H;
+    a.s = ctx->s;
+    a.sf = ctx->sf;
+    a.row_ptr = ctx->row_ptr;
+    a.ideg = (const T*)ctx->ideg;
+    a.masks = ctx->masks;
+    a.mt = (T*)ctx->mt;
+    a.f_eoff = ctx->f_eoff;
+    a.f_base = ctx->f_base;
+    a.f_m = (T*)ctx->f_m;
+    a.chunk_row = ctx->chunk_row;
+    a.col = ctx->col;
+    a.w = ctx->w;
+    a.t_ptr = ctx->t_ptr;
+    a.t_src = ctx->t_src;
+    a.t_w = ctx->t_w;
+    a.tile_r = ctx->tile_r;
+    a.tile_e = ctx->tile_e;
+    a.ntiles = ctx->ntiles;
+    a.st = ctx->st;
+    a.sw = ctx->sw;
+    a.log = ctx->log;
+    a.cond_loop = cd.loop;
+    a.cond_refresh = cd.refresh;
+    a.use_cond = cd.use;
+    a.n = (int)ctx->n;
+    a.vec_ok = vec_aligned(ctx);
+    if (ctx->has_w)
+        LAUNCH(L, KC_SWEEP, TRY((launch_sweep<T, true>(ctx, a))));
+    else
+        LAUNCH(L, KC_SWEEP, TRY((launch_sweep<T, false>(ctx, a))));
+    return RLGL_OK;
+}
+
+// Blocks of the sweep: all that fit on the device at once (the occupancy of
+// the instantiation this context uses), fewer for a small chain, where each
+// block still gets at least one block-iteration of nodes.
+template <typename T>
+static int sweep_fit(rlgl_ctx* ctx) {
+    int nb = 0;
+    cudaError_t e = ctx->has_w
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<T, true>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<T, false>, kThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+static int sweep_grid(rlgl_ctx* ctx) {
+    const int nb = ctx->prec == RLGL_MIXED ? sweep_fit<float>(ctx) : sweep_fit<double>(ctx);
+    if (nb < 1) return 0;
+    const long long fit = (long long)nb * ctx->sms;
+    long long work = ctx->n > ctx->nnz / 8 ? ctx->n : ctx->nnz / 8;
+    long long want = (work + kNodesPerIter - 1) / kNodesPerIter;
+    if (want < 1) want = 1;
+    return (int)(want < fit ? want : fit);
+}
+
+// Whether a solve with this schedule runs as the persistent sweep.
+static bool use_sweep(const rlgl_ctx* ctx, int sched) {
+    return ctx->params.persistent && ctx->nchains <= 1 && sched != RLGL_TOPFRAC && ctx->grid_sweep > 0;
+}
+
 // One eager iteration of Alg. 1: stats [top-k] select push pull. Every kernel
 // checks the device state and returns at once when it has nothing to do.
 template <typename T>
@@ -401,6 +496,10 @@ static rlgl_status forced_refresh(rlgl_ctx* ctx, bool apply) {
 static void drop_graphs(rlgl_ctx* ctx) {
     for (auto& g : ctx->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (ctx->sweep_graph) {
+        cudaGraphExecDestroy(ctx->sweep_graph);
+        ctx->sweep_graph = nullptr;
+    }
 }
 
 static rlgl_status read_state(rlgl_ctx* ctx) {
@@ -423,6 +522,9 @@ static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, dou
     c->max_steps = max_steps;
     c->max_iters = 2 * max_steps + 16;
     c->nnz = ctx->nnz;
+    c->rr_blocks = ctx->params.rr_blocks;
+    c->pc_frac = ctx->params.pc_frac;
+    c->seed = ctx->params.seed;
     c->sched = sched;
     c->r = ctx->params.r;
     c->safety_every = solving ? ctx->params.safety_every : 0;
@@ -571,6 +673,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     // crowd out other contexts' work on the device)
     ctx->grid_push = grid_for(nnz, kPushChunk, ctx->sms * 4);
     ctx->grid_pull = grid_for(n + nnz, kMpItems, ctx->sms * 8);
+    ctx->grid_sweep = sweep_grid(ctx);
     const size_t cs = cash_size(ctx);
 
     TRY(dalloc(ctx, &ctx->row_ptr, (size_t)n + 1));
@@ -598,12 +701,14 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->err, 1));
     TRY(dalloc(ctx, &ctx->log, (size_t)kLogCap));
     TRY(dalloc(ctx, &ctx->st, 1));
+    TRY(dalloc(ctx, &ctx->sw, 1));
     ctx->host_st = static_cast<DevState*>(pin_get());
     if (!ctx->host_st) return fail(ctx, RLGL_ENOMEM, "pinned host allocation failed");
     ctx->host_ctl = reinterpret_cast<Control*>(reinterpret_cast<char*>(ctx->host_st) + sizeof(DevState));
     CK(ctx, cudaMemsetAsync(ctx->y, 0, (size_t)n * sizeof(double), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(unsigned int), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
 
     TRY(upload(ctx, ctx->row_ptr, row_ptr, ((size_t)n + 1) * sizeof(long long), src));
     TRY(upload(ctx, ctx->col, col, (size_t)nnz * sizeof(int), src));
@@ -660,6 +765,10 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->safety_every = 0;
     p->refresh_factor = 1e-3;
     p->time_limit_s = 600.0;
+    p->rr_blocks = 8;
+    p->pc_frac = 0.05;
+    p->seed = 0;
+    p->persistent = 1;
     return RLGL_OK;
 }
 
@@ -860,10 +969,10 @@ rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period, 
 }
 
 static rlgl_status check_sched(rlgl_ctx* ctx, rlgl_schedule sched) {
-    if (sched < RLGL_ALL_GREEN || sched > RLGL_LINK_THRESHOLD)
+    if (sched < RLGL_ALL_GREEN || sched > RLGL_PC)
         return fail(ctx, RLGL_EINVAL, "bad schedule %d", (int)sched);
-    if (sched == RLGL_TOPFRAC && ctx->nchains > 1)
-        return fail(ctx, RLGL_EINVAL, "RLGL_TOPFRAC is not available for a batch of chains");
+    if ((sched == RLGL_TOPFRAC || sched == RLGL_BLOCK_RR || sched == RLGL_PC) && ctx->nchains > 1)
+        return fail(ctx, RLGL_EINVAL, "schedule %d is not available for a batch of chains", (int)sched);
     if (sched == RLGL_MASK && !ctx->masks) return fail(ctx, RLGL_EINVAL, "RLGL_MASK needs rlgl_set_masks");
     return RLGL_OK;
 }
@@ -983,6 +1092,53 @@ static rlgl_status build_graph_t(rlgl_ctx* ctx, int sched, cudaGraph_t g) {
     return RLGL_OK;
 }
 
+// The sweep's solve graph: WHILE(loop) { [IF(refresh) {re-derive C}] sweep }.
+// The sweep ends the loop when the solve stops and requests the
+// re-derivation when it returns for one.
+template <typename T>
+static rlgl_status build_sweep_graph_t(rlgl_ctx* ctx, cudaGraph_t g) {
+    Conds cd;
+    cd.use = 1;
+    cudaGraphConditionalHandle hw;
+    CK(ctx, cudaGraphConditionalHandleCreate(&hw, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNode_t wnode;
+    cudaGraph_t body;
+    TRY(add_conditional(ctx, g, nullptr, 0, hw, cudaGraphCondTypeWhile, 1, &wnode, &body));
+    cd.loop = (unsigned long long)hw;
+    std::vector<cudaGraphNode_t> deps;
+    Launch L{ctx, true};
+    if (ctx->prec == RLGL_MIXED) {
+        cudaGraphConditionalHandle hr;
+        CK(ctx, cudaGraphConditionalHandleCreate(&hr, body, 0u, cudaGraphCondAssignDefault));
+        cd.refresh = (unsigned long long)hr;
+        cudaGraphNode_t rnode;
+        cudaGraph_t rbody;
+        TRY(add_conditional(ctx, body, nullptr, 0, hr, cudaGraphCondTypeIf, 1, &rnode, &rbody));
+        TRY(capture_into(ctx, rbody, nullptr, 0, [&] { return enqueue_refresh<T>(L); }, nullptr));
+        deps.push_back(rnode);
+    }
+    TRY(capture_into(ctx, body, deps.data(), deps.size(), [&] { return enqueue_sweep<T>(L, cd); },
+                     nullptr));
+    return RLGL_OK;
+}
+
+static rlgl_status build_sweep_graph(rlgl_ctx* ctx) {
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaGraphCreate(&g, 0));
+    rlgl_status s = (ctx->prec == RLGL_MIXED) ? build_sweep_graph_t<float>(ctx, g)
+                                              : build_sweep_graph_t<double>(ctx, g);
+    if (s != RLGL_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e);
+    ctx->sweep_graph = exec;
+    return RLGL_OK;
+}
+
 static rlgl_status build_graph(rlgl_ctx* ctx, int sched) {
     cudaGraph_t g = nullptr;
     CK(ctx, cudaGraphCreate(&g, 0));
@@ -1008,9 +1164,20 @@ static rlgl_status solve_launch(rlgl_ctx* ctx, rlgl_schedule sched, double theta
     if (max_steps < 1 || max_steps > 100000000ll) return fail(ctx, RLGL_EINVAL, "max_steps out of range");
     const bool batch_tols = ctx->nchains > 1 && tol < 0.0;  // per-chain tolerances
     if (!(tol >= 0.0) && !batch_tols) return fail(ctx, RLGL_EINVAL, "tol must be >= 0");
-    if (!ctx->graph[sched]) TRY(build_graph(ctx, sched));
+    bool sweep = use_sweep(ctx, sched);
+    if (sweep && !ctx->sweep_graph && build_sweep_graph(ctx) != RLGL_OK) {
+        // The device or driver would not take the cooperative kernel into a
+        // graph: use one kernel per phase from now on (params.persistent
+        // then reads 0, and rlgl_last_error keeps the reason).
+        ctx->params.persistent = 0;
+        ctx->grid_sweep = 0;
+        sweep = false;
+        cudaGetLastError();
+    }
+    if (!sweep && !ctx->graph[sched]) TRY(build_graph(ctx, sched));
     TRY(begin(ctx, sched, theta, batch_tols ? 0.0 : tol, max_steps, 1, batch_tols ? -1.0 : tol));
-    CK(ctx, cudaGraphLaunch(ctx->graph[sched], ctx->stream));
+    if (sweep) CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
+    CK(ctx, cudaGraphLaunch(sweep ? ctx->sweep_graph : ctx->graph[sched], ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->host_st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaEventRecord(ctx->done_ev, ctx->stream));
     ctx->pending = true;
@@ -1039,6 +1206,8 @@ static rlgl_status solve_finish(rlgl_ctx* ctx, rlgl_solve_info* info) {
         case ST_DEGENERATE: return fail(ctx, RLGL_EDEGENERATE, "degenerate history: |H 1| ~ 0");
         case ST_NOCONV: return fail(ctx, RLGL_ENOCONV, "no convergence in %lld moves", ctx->pending_max);
         case ST_TIMEOUT: return fail(ctx, RLGL_ETIMEOUT, "solve exceeded its time limit");
+        case ST_BARRIER:
+            return fail(ctx, RLGL_ETIMEOUT, "a grid-barrier wait of the persistent sweep gave up");
         default: return fail(ctx, RLGL_ECUDA, "unexpected device status %d", h->status);
     }
 }
@@ -1170,7 +1339,8 @@ rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
     if (!ctx || !p) return fail(ctx, RLGL_EINVAL, "NULL argument");
     if (!(p->theta_scale > 0.0) || p->r < 1 || !(p->top_frac > 0.0 && p->top_frac <= 1.0) ||
         !(p->pull_crossover >= 0.0) || p->safety_every < 0 || !(p->refresh_factor >= 0.0 && p->refresh_factor < 1.0) ||
-        !(p->time_limit_s > 0.0))
+        !(p->time_limit_s > 0.0) || (p->persistent != 0 && p->persistent != 1) || p->rr_blocks < 1 ||
+        !(p->pc_frac > 0.0 && p->pc_frac <= 1e30))
         return fail(ctx, RLGL_EINVAL, "parameter out of range");
     ctx->params = *p;
     return RLGL_OK;
@@ -1242,6 +1412,42 @@ rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta,
     return prof_collect(ctx);
 }
 
+}  // extern "C"
+
+template <typename T>
+static rlgl_status profile_sweep_t(rlgl_ctx* ctx, int64_t moves) {
+    Launch L{ctx, false};
+    Conds none;
+    // every launch makes at least one move or ends the solve
+    for (int64_t k = 0; k < moves + 4; ++k) {
+        TRY(enqueue_refresh<T>(L));  // runs only when a re-derivation is pending
+        TRY(enqueue_sweep<T>(L, none));
+        TRY(read_state(ctx));
+        if (ctx->host_st->done) break;
+    }
+    return RLGL_OK;
+}
+
+extern "C" {
+
+rlgl_status rlgl_profile_sweep(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    NOT_PENDING(ctx);
+    TRY(check_sched(ctx, sched));
+    if (moves < 1 || moves > 100000000ll) return fail(ctx, RLGL_EINVAL, "moves out of range");
+    if (!use_sweep(ctx, sched))
+        return fail(ctx, RLGL_EINVAL, "the persistent sweep does not serve this schedule or context");
+    const int prev = ctx->profiling;
+    ctx->profiling = 1;
+    TRY(begin(ctx, sched, theta, 0.0, moves, 1));
+    CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
+    rlgl_status s = ctx->prec == RLGL_MIXED ? profile_sweep_t<float>(ctx, moves)
+                                            : profile_sweep_t<double>(ctx, moves);
+    ctx->profiling = prev;
+    if (s != RLGL_OK) return s;
+    return prof_collect(ctx);
+}
+
 rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, int64_t* written) {
     if (!ctx || !out || count < 0) return fail(ctx, RLGL_EINVAL, "bad argument");
     static_assert(sizeof(rlgl_move_record) == sizeof(MoveRecord), "log record layout");
@@ -1281,7 +1487,7 @@ int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision 
     b += n * (cs + 8 + cs + 8 + 8 + 8 + 8 + cs);                     // c H mt y hsrc f_eoff f_base f_m
     b += (nnz / kPushChunk + 2) * 4;                                 // chunk index
     b += (4 * kMaxGrid + 8) * 8 + 8 + (int64_t)kLogCap * (int64_t)sizeof(MoveRecord) +
-         (int64_t)sizeof(DevState);
+         (int64_t)sizeof(DevState) + (int64_t)sizeof(SweepState);
     if (n_chains > 1) b += (n_chains + 1) * 8 + n * 4 + n_chains * ((int64_t)sizeof(ChainState) + 16);
     return b;
 }
@@ -1312,11 +1518,12 @@ void rlgl_destroy(rlgl_ctx* ctx) {
         std::lock_guard<std::mutex> lk(g_retired_mu);
         for (auto& g : ctx->graph)
             if (g) g_retired.push_back(g);
+        if (ctx->sweep_graph) g_retired.push_back(ctx->sweep_graph);
     }
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
-                   ctx->err, ctx->log, ctx->st, ctx->node_ptr, ctx->chain_of, ctx->cs,
+                   ctx->err, ctx->log, ctx->st, ctx->sw, ctx->node_ptr, ctx->chain_of, ctx->cs,
                    ctx->bsums};
     for (void* p : dev)
         dfree(ctx, p);

@@ -70,7 +70,9 @@ enum Sched : int {
     SCHED_THRESHOLD = 1,
     SCHED_TOPFRAC = 2,
     SCHED_MASK = 3,
-    SCHED_LINK = 4
+    SCHED_LINK = 4,
+    SCHED_BLOCK_RR = 5,
+    SCHED_PC = 6
 };
 enum Status : int { ST_OK = 0, ST_DEGENERATE = 5, ST_NOCONV = 6, ST_TIMEOUT = 7 };
 
@@ -86,6 +88,9 @@ struct Control {
     long long max_steps;
     long long max_iters;
     long long nnz;
+    long long rr_blocks;     // BLOCK_RR: K
+    double pc_frac;          // PC: k = pc_frac N
+    unsigned long long seed; // PC: generator seed
     int sched;
     int r;
     int safety_every;
@@ -216,6 +221,15 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
+// Loads of data that other blocks of the same kernel may have written: from
+// L2 (ld.global.cg) when kCg, so that no stale L1 line is read.
+template <bool kCg, typename T>
+__device__ __forceinline__ T ld_shared_data(const T* p) {
+    if (kCg) return __ldcg(p);
+    return *p;
+}
+
+
 // In the last block: out[k] = sum over blocks b of part[K b + k], with all
 // threads of the block, in a fixed order (per-thread strided sums, then a
 // fixed tree), so the result does not depend on block scheduling. The
@@ -274,6 +288,62 @@ __device__ __forceinline__ void st_stage_out(DevState* st, const StStage* sh) {
 __device__ __forceinline__ void set_theta(DevState* st, double theta, int sched) {
     st->theta = theta;
     st->theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+}
+
+// Per-move constants of the cash-independent and sampled schedules.
+//   BLOCK_RR: nodes in contiguous blocks of rr_b = ceil(N / K) (K clipped to
+//             [1, N]); move t greens block t mod ceil(N / rr_b).
+//   PC      : node i is green when C_i != 0 and u_{t,i} ||C||_1 < k |C_i|,
+//             i.e. u_{t,i} < min(1, k |C_i| / ||C||_1) (k = pc_frac N), with
+//             u_{t,i} the counter-based SplitMix64 draw (Steele, Lea and
+//             Flood 2014): key_t = mix(seed + (t + 1) g), u_{t,i} =
+//             2^-53 floor(mix(key_t + (i + 1) g) / 2^11).
+struct SchedAux {
+    long long rr_b, rr_cur;
+    double pc_k, pc_l1;
+    unsigned long long pc_key;
+};
+
+constexpr unsigned long long kSm64Gamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ SchedAux sched_aux(const Control& c, long long n, long long move, double l1) {
+    SchedAux a;
+    long long K = c.rr_blocks < 1 ? 1 : (c.rr_blocks > n ? n : c.rr_blocks);
+    a.rr_b = (n + K - 1) / K;
+    const long long nb = (n + a.rr_b - 1) / a.rr_b;
+    a.rr_cur = move % nb;
+    a.pc_k = c.pc_frac * (double)n;
+    a.pc_l1 = l1;
+    a.pc_key = sm64_mix(c.seed + (unsigned long long)(move + 1) * kSm64Gamma);
+    return a;
+}
+
+// Whether node i (cash v) is green under `sched` (ALL_GREEN, THRESHOLD,
+// LINK_THRESHOLD, MASK, BLOCK_RR, PC; TOPFRAC uses THRESHOLD's test with its
+// radix-selected theta).
+template <typename T>
+__device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
+                                           const unsigned char* mask, const T* __restrict__ ideg,
+                                           const SchedAux& ax) {
+    switch (sched) {
+        case SCHED_ALL_GREEN: return true;
+        case SCHED_MASK: return mask[i] != 0;
+        case SCHED_LINK: return (v != T(0)) && (fabs(v) * __ldg(ideg + i) >= th);
+        case SCHED_BLOCK_RR: return i / ax.rr_b == ax.rr_cur;
+        case SCHED_PC: {
+            if (v == T(0)) return false;
+            const double u = (double)(sm64_mix(ax.pc_key + (unsigned long long)(i + 1) * kSm64Gamma) >> 11) *
+                             0x1.0p-53;
+            return u * ax.pc_l1 < ax.pc_k * fabs((double)v);
+        }
+        default: return (v != T(0)) && (fabs(v) >= th);
+    }
 }
 
 // Decides, after the cash statistics of C_t are known, whether the solve
@@ -522,6 +592,55 @@ __global__ void __launch_bounds__(kThreads) k_bstats(const T* __restrict__ c,
     batch_control(st, bv, cond_handle, cond_refresh, use_cond);
 }
 
+// Per-thread sums over the nodes first, first + stride, ... of ||C||_1,
+// sum C and sum v^r (v = |C_i|, or |C_i| / d_i for the per-link test), in
+// the cash type (FP32 on the MIXED path: GB300's FP64 rate is low).
+template <typename T, bool kCg>
+__device__ __forceinline__ void stats_slice(const T* __restrict__ c, const T* __restrict__ ideg,
+                                            long long n, bool link, int r, int vec_ok,
+                                            long long first, long long stride, T& a, T& s, T& pr) {
+    auto add = [&](T v, T idg) {
+        const T av = fabs(v);
+        a += av;
+        s += v;
+        const T tv = link ? av * idg : av;
+        if (link && r == 1) pr += tv;
+        else if (r == 2) pr += tv * tv;
+        else if (r > 2) pr += pow(tv, (T)r);
+    };
+    // 16-byte vector loads (4 FP32 / 2 FP64 values), two vectors in flight
+    // per thread, then the scalar tail.
+    using V = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+    constexpr int kW = sizeof(V) / sizeof(T);
+    const long long nv = vec_ok ? n / kW : 0;
+    const V* cv = reinterpret_cast<const V*>(c);
+    const V* iv = reinterpret_cast<const V*>(ideg);
+    long long k = first;
+    for (; k + stride < nv; k += 2 * stride) {
+        const V x0 = ld_shared_data<kCg>(cv + k), x1 = ld_shared_data<kCg>(cv + k + stride);
+        V d0, d1;
+        if (link) { d0 = iv[k]; d1 = iv[k + stride]; } else { d0 = x0; d1 = x1; }
+        const T* p0 = reinterpret_cast<const T*>(&x0);
+        const T* p1 = reinterpret_cast<const T*>(&x1);
+        const T* q0 = reinterpret_cast<const T*>(&d0);
+        const T* q1 = reinterpret_cast<const T*>(&d1);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p1[u], q1[u]);
+    }
+    for (; k < nv; k += stride) {
+        const V x0 = ld_shared_data<kCg>(cv + k);
+        V d0 = link ? iv[k] : x0;
+        const T* p0 = reinterpret_cast<const T*>(&x0);
+        const T* q0 = reinterpret_cast<const T*>(&d0);
+#pragma unroll
+        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
+    }
+    for (long long i = nv * kW + first; i < n; i += stride)
+        add(ld_shared_data<kCg>(c + i), link ? ideg[i] : T(0));
+}
+
 // ||C||_1, sum C and sum v^r (v = |C_i|, or |C_i| / d_i for the per-link
 // test) of the current cash, then control. Each thread sums its nodes in the
 // cash type (FP32 on the MIXED path: GB300's FP64 rate is low) and the
@@ -541,47 +660,8 @@ __global__ void __launch_bounds__(kThreads) k_stats(const T* __restrict__ c,
     T a = T(0), s = T(0), pr = T(0);
     const int r = st->ctl.r;
     const bool link = st->ctl.sched == SCHED_LINK;
-    auto add = [&](T v, T idg) {
-        const T av = fabs(v);
-        a += av;
-        s += v;
-        const T tv = link ? av * idg : av;
-        if (link && r == 1) pr += tv;
-        else if (r == 2) pr += tv * tv;
-        else if (r > 2) pr += pow(tv, (T)r);
-    };
-    // 16-byte vector loads (4 FP32 / 2 FP64 values), two vectors in flight
-    // per thread, then the scalar tail.
-    using V = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
-    constexpr int kW = sizeof(V) / sizeof(T);
-    const long long nv = vec_ok ? n / kW : 0;
-    const V* cv = reinterpret_cast<const V*>(c);
-    const V* iv = reinterpret_cast<const V*>(ideg);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    for (; k + stride < nv; k += 2 * stride) {
-        const V x0 = cv[k], x1 = cv[k + stride];
-        V d0, d1;
-        if (link) { d0 = iv[k]; d1 = iv[k + stride]; } else { d0 = x0; d1 = x1; }
-        const T* p0 = reinterpret_cast<const T*>(&x0);
-        const T* p1 = reinterpret_cast<const T*>(&x1);
-        const T* q0 = reinterpret_cast<const T*>(&d0);
-        const T* q1 = reinterpret_cast<const T*>(&d1);
-#pragma unroll
-        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
-#pragma unroll
-        for (int u = 0; u < kW; ++u) add(p1[u], q1[u]);
-    }
-    for (; k < nv; k += stride) {
-        const V x0 = cv[k];
-        V d0 = link ? iv[k] : x0;
-        const T* p0 = reinterpret_cast<const T*>(&x0);
-        const T* q0 = reinterpret_cast<const T*>(&d0);
-#pragma unroll
-        for (int u = 0; u < kW; ++u) add(p0[u], q0[u]);
-    }
-    for (long long i = nv * kW + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
-        add(c[i], link ? ideg[i] : T(0));
+    stats_slice<T, false>(c, ideg, n, link, r, vec_ok, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                          (long long)gridDim.x * blockDim.x, a, s, pr);
     // block sums in the cash type too; the partials of the blocks are
     // combined in FP64
     __shared__ T tscratch[32];
@@ -719,6 +799,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
     const T theta = std::is_same<T, float>::value ? (T)st->theta_f : (T)st->theta;
     const unsigned char* mask = nullptr;
     if (sched == SCHED_MASK) mask = masks + (size_t)(st->mask_cursor % ctl.n_masks) * (size_t)n;
+    const SchedAux ax = sched_aux(ctl, n, st->moves, st->l1);
 
     __shared__ double scratch[32];
     __shared__ T tscratch[32];
@@ -768,11 +849,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
                     active = !ch.done;
                     th = std::is_same<T, float>::value ? (T)ch.theta_f : (T)ch.theta;
                 }
-                if (!active) g[q] = false;
-                else if (sched == SCHED_ALL_GREEN) g[q] = true;
-                else if (sched == SCHED_MASK) g[q] = mask[i] != 0;
-                else if (sched == SCHED_LINK) g[q] = (v != T(0)) && (fabs(v) * ideg[i] >= th);
-                else g[q] = (v != T(0)) && (fabs(v) >= th);
+                g[q] = active && green_test<T>(sched, v, i, th, mask, ideg, ax);
             }
             if (g[q] && !dense_all) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
         }
@@ -923,36 +1000,44 @@ __global__ void __launch_bounds__(kThreads) k_select(
 // edge slot is labelled with its row by marking the row starts and taking a
 // block-wide running maximum, so every edge costs one shared-memory read;
 // edges are then handled in a coalesced order (slot = thread + q * threads).
-template <typename T, bool kHasW>
-__global__ void __launch_bounds__(kThreads) k_push(
-    T* __restrict__ c, const int* __restrict__ col, const float* __restrict__ w,
-    const long long* __restrict__ f_eoff, const long long* __restrict__ f_base,
-    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st) {
-    if (st->done || st->skip_move || st->mode != MODE_PUSH) return;
+// Shared memory of the push chunk loop.
+template <typename T>
+struct PushSmem {
+    int row[kPushChunk];
+    long long base[kPushChunk + 1];
+    T m[kPushChunk + 1];
+    int wmax[kThreads / 32];
+};
+
+// The chunks b = first, first + step, ... of a push over E frontier edges of
+// K frontier rows (see k_push).
+template <typename T, bool kHasW, bool kCg>
+__device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __restrict__ col,
+                                            const float* __restrict__ w,
+                                            const long long* __restrict__ f_eoff,
+                                            const long long* __restrict__ f_base,
+                                            const T* __restrict__ f_m,
+                                            const int* __restrict__ chunk_row, long long E,
+                                            long long K, long long first, long long step,
+                                            PushSmem<T>& sm) {
     constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread (8)
-    const long long E = st->edges;
-    const long long K = st->green;
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
-    __shared__ int s_row[kPushChunk];
-    __shared__ long long s_base[kPushChunk + 1];
-    __shared__ T s_m[kPushChunk + 1];
-    __shared__ int s_wmax[kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long b = blockIdx.x; b < nchunks; b += gridDim.x) {
+    for (long long b = first; b < nchunks; b += step) {
         const long long e0 = b * kPushChunk;
         const int ne = (int)min((long long)kPushChunk, E - e0);
-        const long long k0 = chunk_row[b];
-        const long long k1 = (b + 1 < nchunks) ? (long long)chunk_row[b + 1] : K - 1;
+        const long long k0 = ld_shared_data<kCg>(chunk_row + b);
+        const long long k1 = (b + 1 < nchunks) ? (long long)ld_shared_data<kCg>(chunk_row + b + 1) : K - 1;
         const int nr = (int)(k1 - k0 + 1);
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = 0;
+        for (int q = 0; q < kPer; ++q) sm.row[threadIdx.x * kPer + q] = 0;
         __syncthreads();
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-            const long long eo = f_eoff[k0 + r];
-            s_base[r] = f_base[k0 + r];
-            s_m[r] = f_m[k0 + r];
+            const long long eo = ld_shared_data<kCg>(f_eoff + k0 + r);
+            sm.base[r] = ld_shared_data<kCg>(f_base + k0 + r);
+            sm.m[r] = ld_shared_data<kCg>(f_m + k0 + r);
             const long long off = eo - e0;  // row 0 starts at or before the chunk
-            if (r > 0 && off < ne) s_row[(int)off] = r;
+            if (r > 0 && off < ne) sm.row[(int)off] = r;
         }
         __syncthreads();
         // running maximum over the slots: slot -> row
@@ -960,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads) k_push(
         int run = 0;
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
-            run = max(run, s_row[threadIdx.x * kPer + q]);
+            run = max(run, sm.row[threadIdx.x * kPer + q]);
             v[q] = run;
         }
         int incl = run;
@@ -969,28 +1054,39 @@ __global__ void __launch_bounds__(kThreads) k_push(
             int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl = max(incl, y);
         }
-        if (lane == 31) s_wmax[wid] = incl;
+        if (lane == 31) sm.wmax[wid] = incl;
         __syncthreads();
         int before = __shfl_up_sync(0xffffffffu, incl, 1);
         if (lane == 0) before = 0;
-        for (int k = 0; k < wid; ++k) before = max(before, s_wmax[k]);
+        for (int k = 0; k < wid; ++k) before = max(before, sm.wmax[k]);
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = max(v[q], before);
+        for (int q = 0; q < kPer; ++q) sm.row[threadIdx.x * kPer + q] = max(v[q], before);
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int le = threadIdx.x + q * kThreads;
             if (le < ne) {
-                const int r = s_row[le];
-                const long long pos = s_base[r] + e0 + le;
+                const int r = sm.row[le];
+                const long long pos = sm.base[r] + e0 + le;
                 const int j = __ldg(col + pos);
-                T val = s_m[r];
+                T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
                 atomicAdd(c + j, val);
             }
         }
         __syncthreads();
     }
+}
+
+template <typename T, bool kHasW>
+__global__ void __launch_bounds__(kThreads) k_push(
+    T* __restrict__ c, const int* __restrict__ col, const float* __restrict__ w,
+    const long long* __restrict__ f_eoff, const long long* __restrict__ f_base,
+    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st) {
+    if (st->done || st->skip_move || st->mode != MODE_PUSH) return;
+    __shared__ PushSmem<T> sm;
+    push_chunks<T, kHasW, false>(c, col, w, f_eoff, f_base, f_m, chunk_row, st->edges, st->green,
+                                 blockIdx.x, gridDim.x, sm);
 }
 
 // ------------------------------------------------------ merge-path pull
@@ -1045,25 +1141,27 @@ __device__ __forceinline__ TV block_segscan(long long key, TV val, long long* s_
 // thread ends are written once; the pieces of a row split between threads
 // are joined by a segmented scan over the block, so only rows that cross a
 // tile boundary use atomic adds.
-// kind 0: cash pull (guarded by mode == PULL); kind 1: FP64 residual pull
-// into y (guarded by want_refresh / force_refresh).
-template <typename TV, typename TO, bool kHasW, int kKind>
-__global__ void __launch_bounds__(kThreads) k_pull(
-    TO* __restrict__ out, const TV* __restrict__ src, const long long* __restrict__ t_ptr,
-    const int* __restrict__ t_src, const float* __restrict__ t_w,
-    const long long* __restrict__ tile_r, const long long* __restrict__ tile_e, long long ntiles,
-    const DevState* st) {
-    if (kKind == 0) {
-        if (st->done || st->skip_move || st->mode != MODE_PULL) return;
-    } else {
-        if (!(st->force_refresh || (st->want_refresh && !st->done))) return;
-    }
-    __shared__ TV s_val[kMpItems];
-    __shared__ int s_end[kMpItems + 1];
-    __shared__ int s_start0;
-    __shared__ long long s_ckey[kThreads];
-    __shared__ TV s_cval[kThreads];
-    for (long long b = blockIdx.x; b < ntiles; b += gridDim.x) {
+
+// Shared memory of the merge-path tile loop.
+template <typename TV>
+struct PullSmem {
+    TV val[kMpItems];
+    int end[kMpItems + 1];
+    int start0;
+    long long ckey[kThreads];
+    TV cval[kThreads];
+};
+
+// The tiles b = first, first + step, ... of a merge-path pull (see k_pull).
+template <typename TV, typename TO, bool kHasW, bool kCg>
+__device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __restrict__ src,
+                                           const long long* __restrict__ t_ptr,
+                                           const int* __restrict__ t_src,
+                                           const float* __restrict__ t_w,
+                                           const long long* __restrict__ tile_r,
+                                           const long long* __restrict__ tile_e, long long ntiles,
+                                           long long first, long long step, PullSmem<TV>& sm) {
+    for (long long b = first; b < ntiles; b += step) {
         const long long r0 = tile_r[b], e0 = tile_e[b];
         const int nrows = (int)(tile_r[b + 1] - r0);
         const int nedges = (int)(tile_e[b + 1] - e0);
@@ -1080,17 +1178,17 @@ __global__ void __launch_bounds__(kThreads) k_pull(
             }
             TV v[kMpIpt];
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? src[sidx[q]] : TV(0);
+            for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? ld_shared_data<kCg>(src + sidx[q]) : TV(0);
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) {
                 const int k = threadIdx.x + q * kThreads;
-                if (k < nedges) s_val[k] = kHasW ? v[q] * (TV)wv[q] : v[q];
-                if (k < nrows) s_end[k] = (int)(re[q] - e0);
+                if (k < nedges) sm.val[k] = kHasW ? v[q] * (TV)wv[q] : v[q];
+                if (k < nrows) sm.end[k] = (int)(re[q] - e0);
             }
         }
         if (threadIdx.x == 0) {
-            s_end[nrows] = 0x7fffffff;
-            s_start0 = (int)(t_ptr[r0] - e0);
+            sm.end[nrows] = 0x7fffffff;
+            sm.start0 = (int)(t_ptr[r0] - e0);
         }
         __syncthreads();
         const int total = nrows + nedges;
@@ -1105,16 +1203,16 @@ __global__ void __launch_bounds__(kThreads) k_pull(
             int lo = max(0, d - nedges), hi = min(d, nrows);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
-                if (s_end[mid] >= d - mid) hi = mid; else lo = mid + 1;
+                if (sm.end[mid] >= d - mid) hi = mid; else lo = mid + 1;
             }
             int i = lo, j = d - lo;
-            const int row_start = (i == 0) ? s_start0 : s_end[i - 1];
+            const int row_start = (i == 0) ? sm.start0 : sm.end[i - 1];
             bool whole = (j == row_start);  // no edge of row i before this thread
             TV acc = TV(0);
             int cnt = 0;
             for (; d < dend; ++d) {
-                if (j < s_end[i]) {
-                    acc += s_val[j];
+                if (j < sm.end[i]) {
+                    acc += sm.val[j];
                     ++j;
                     ++cnt;
                 } else {
@@ -1123,7 +1221,7 @@ __global__ void __launch_bounds__(kThreads) k_pull(
                         accA = acc;
                     } else if (cnt > 0) {
                         TO* o = out + (r0 + i);
-                        *o = (TO)(*o + (TO)acc);
+                        *o = (TO)(ld_shared_data<kCg>(o) + (TO)acc);
                     }
                     acc = TV(0);
                     cnt = 0;
@@ -1140,20 +1238,38 @@ __global__ void __launch_bounds__(kThreads) k_pull(
         }
         // Join the pieces: carry of thread t plus the carries of the threads
         // before it on the same row.
-        const TV run = block_segscan<TV>(rowB, accB, s_ckey, s_cval);
+        const TV run = block_segscan<TV>(rowB, accB, sm.ckey, sm.cval);
         if (rowA >= 0) {
             TV sum = accA;
-            if (threadIdx.x > 0 && s_ckey[threadIdx.x - 1] == rowA) sum += s_cval[threadIdx.x - 1];
+            if (threadIdx.x > 0 && sm.ckey[threadIdx.x - 1] == rowA) sum += sm.cval[threadIdx.x - 1];
             TO* o = out + rowA;
             // the tile's first row may have begun in the previous tile
-            if (rowA == r0 && s_start0 < 0) atomicAdd(o, (TO)sum);
-            else *o = (TO)(*o + (TO)sum);
+            if (rowA == r0 && sm.start0 < 0) atomicAdd(o, (TO)sum);
+            else *o = (TO)(ld_shared_data<kCg>(o) + (TO)sum);
         }
         // last active thread: its carry leaves the tile
         const int last = (total - 1) / kMpIpt;
         if ((int)threadIdx.x == last && rowB >= 0) atomicAdd(out + rowB, (TO)run);
         __syncthreads();
     }
+}
+
+// kind 0: cash pull (guarded by mode == PULL); kind 1: FP64 residual pull
+// into y (guarded by want_refresh / force_refresh).
+template <typename TV, typename TO, bool kHasW, int kKind>
+__global__ void __launch_bounds__(kThreads) k_pull(
+    TO* __restrict__ out, const TV* __restrict__ src, const long long* __restrict__ t_ptr,
+    const int* __restrict__ t_src, const float* __restrict__ t_w,
+    const long long* __restrict__ tile_r, const long long* __restrict__ tile_e, long long ntiles,
+    const DevState* st) {
+    if (kKind == 0) {
+        if (st->done || st->skip_move || st->mode != MODE_PULL) return;
+    } else {
+        if (!(st->force_refresh || (st->want_refresh && !st->done))) return;
+    }
+    __shared__ PullSmem<TV> sm;
+    pull_tiles<TV, TO, kHasW, false>(out, src, t_ptr, t_src, t_w, tile_r, tile_e, ntiles, blockIdx.x,
+                                     gridDim.x, sm);
 }
 
 // ------------------------------------------------------------ refresh

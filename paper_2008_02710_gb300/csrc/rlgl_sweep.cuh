@@ -1,0 +1,494 @@
+// The persistent sweep: the moves of a single-chain solve (Alg. 1 lines
+// (2)-(7)) in one cooperative kernel, so that a move costs three grid
+// barriers instead of three to four kernel launches, their drain and their
+// serial last-block tails.
+//
+// Every block runs every phase of a move on its share of the work:
+//   stats   : its slice of the nodes; block sums go to one FP64 atomic per
+//             statistic in the move's slot;
+//   barrier ; every block reads the totals and takes the same decisions
+//             (stop, re-derivation, theta) from the same numbers;
+//   select  : its slice of the nodes (the same compaction as k_select);
+//   barrier ; every block reads the frontier size and picks push or pull;
+//   push    : its share of the frontier's edge chunks, or
+//   pull    : its share of the merge-path tiles;
+//   barrier.
+// The kernel returns when the solve stops (it then ends the graph's loop) or
+// when the FP32 cash of the MIXED path must be re-derived in FP64 (the
+// graph's re-derivation runs and the loop launches the sweep again).
+//
+// Co-residency: the kernel is launched cooperatively with at most as many
+// blocks as fit on the GPU at once. Every barrier wait is bounded in time;
+// a wait that gives up raises an abort flag on which every block leaves,
+// and the solve ends with the status ST_BARRIER.
+#pragma once
+#include "rlgl_kernels.cuh"
+
+namespace rlgl {
+
+constexpr int kSweepMinBlocks = 4;                            // blocks per SM (launch bounds)
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s per barrier wait
+constexpr int ST_BARRIER = 9;
+
+// Per-move accumulators, zero at rest. Two slots alternate: the slot of
+// move t is cleared by block 0 during move t + 1, after the first barrier,
+// when every block has finished reading it.
+struct SweepSlot {
+    double a, s, pr;             // ||C||_1, sum C, sum v^r of the cash
+    double msum, mabs;           // sum m_i, sum |m_i| of the moved cash
+    unsigned long long reserve;  // packed frontier reservation
+    unsigned long long tstamp;   // block 0's timer at the end of its stats
+    unsigned long long pad;
+};
+
+struct GridBar {
+    unsigned int count;  // blocks arrived at the current barrier
+    unsigned int gen;    // barriers completed
+    unsigned int abort;  // a wait gave up: every block leaves
+    unsigned int parity; // slot of the next move (kept across launches)
+};
+
+struct SweepState {
+    GridBar bar;
+    SweepSlot slot[2];
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch. Thread 0 of each block
+// arrives; the last one to arrive resets the count and publishes the next
+// generation; the others wait for it, at most kBarrierLimitNs. Returns false
+// (in every thread of the block) when the sweep must stop.
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen) {
+    // gen: the block's barrier count (shared memory; thread 0 keeps it)
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int target = gen + 1u;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicExch(&bar->gen, target);
+        } else {
+            const unsigned long long t0 = globaltimer();
+            while (ld_acquire_u32(&bar->gen) != target) {
+                if (ld_acquire_u32(&bar->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer() - t0 > kBarrierLimitNs) {
+                    atomicExch(&bar->abort, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (ld_acquire_u32(&bar->abort)) ok = 0;
+        __threadfence();
+        s_ok = ok;
+        gen = target;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+struct SweepArgs {
+    T* c;
+    double* H;
+    const double* s;
+    const float* sf;
+    const long long* row_ptr;
+    const T* ideg;
+    const unsigned char* masks;
+    T* mt;
+    long long* f_eoff;
+    long long* f_base;
+    T* f_m;
+    int* chunk_row;
+    const int* col;
+    const float* w;
+    const long long* t_ptr;
+    const int* t_src;
+    const float* t_w;
+    const long long* tile_r;
+    const long long* tile_e;
+    long long ntiles;
+    DevState* st;
+    SweepState* sw;
+    MoveRecord* log;
+    unsigned long long cond_loop;
+    unsigned long long cond_refresh;
+    int use_cond;
+    int n;
+    int vec_ok;
+};
+
+// Select on this block's node slices (the single-chain form of k_select):
+// green nodes give their cash (m_i = C_i, C_i <- 0, H_i += m_i), reserve
+// frontier slots with one atomic per block-iteration and write their
+// frontier entries and push-chunk starts; mt holds m~_i (0 for red nodes).
+// Returns the block's sums of m_i and |m_i| in thread 0.
+template <typename T>
+__device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T th,
+                                             const unsigned char* mask, const SchedAux& ax,
+                                             SweepSlot* sl, double& bmsum, double& bmabs) {
+    __shared__ T tscratch[32];
+    __shared__ unsigned long long base_sh;
+    const int n = A.n;
+    T msum = T(0), mabs = T(0);
+    const bool dense_all = sched == SCHED_ALL_GREEN;
+    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+         it0 += (long long)gridDim.x * kNodesPerIter) {
+        T val[kNodesPerThread];
+        long long rb[kNodesPerThread];
+        int rdeg[kNodesPerThread];
+        bool g[kNodesPerThread];
+        unsigned long long mine = 0ull;
+        if (!dense_all) {
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
+                rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            g[q] = false;
+            val[q] = T(0);
+            if (i < n) {
+                const T v = __ldcg(A.c + i);
+                val[q] = v;
+                g[q] = green_test<T>(sched, v, i, th, mask, A.ideg, ax);
+            }
+            if (g[q] && !dense_all) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+        }
+        if (dense_all) {
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                if (i >= n) continue;
+                const T v = val[q];
+                A.c[i] = T(0);
+                A.H[i] += (double)v;
+                msum += v;
+                mabs += fabs(v);
+                A.mt[i] = moved_per_weight(v, A.s, A.sf, i);
+            }
+            continue;
+        }
+        unsigned long long total;
+        const unsigned long long pre = block_exscan(mine, &total);
+        if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
+        __syncthreads();
+        const unsigned long long base = base_sh + pre;
+        long long k = (long long)(base & ((1ull << kCountBits) - 1ull));
+        long long e = (long long)(base >> kCountBits);
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            if (i >= n) continue;
+            if (g[q]) {
+                const T v = val[q];
+                const T mtil = moved_per_weight(v, A.s, A.sf, i);
+                A.c[i] = T(0);
+                A.H[i] += (double)v;
+                msum += v;
+                mabs += fabs(v);
+                A.mt[i] = mtil;
+                A.f_eoff[k] = e;
+                A.f_base[k] = rb[q] - e;
+                A.f_m[k] = mtil;
+                const long long b0 = (e + kPushChunk - 1) / kPushChunk;
+                const long long b1 = (e + rdeg[q] + kPushChunk - 1) / kPushChunk;
+                for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)k;
+                ++k;
+                e += rdeg[q];
+            } else {
+                A.mt[i] = T(0);
+            }
+        }
+        __syncthreads();  // base_sh is rewritten by the next iteration
+    }
+    bmsum = (double)block_sum(msum, tscratch);
+    bmabs = (double)block_sum(mabs, tscratch);
+}
+
+template <typename T>
+union SweepSmem {
+    PushSmem<T> push;
+    PullSmem<T> pull;
+};
+
+// The evolving scalars of the solve, one copy per block in shared memory,
+// kept by the block's thread 0. Every block's copy goes through the same
+// updates from the same values read after the barriers, so all copies stay
+// identical and every block takes the same decisions.
+struct SweepCtl {
+    long long moves, solve_moves, iters, mask_cursor;
+    long long tot_green, tot_edges, push_moves, pull_moves;
+    long long green, edges;
+    double hsum, habs, theta, l1;
+    unsigned long long t_start;
+    float theta_f;
+    int fresh, sched, mode;
+    int leave;         // 1: return now (stop, or re-derive before testing again)
+    int want_refresh;  // return after this move for a re-derivation
+    int p;             // slot parity
+    unsigned int gen;  // barrier generation
+};
+
+template <typename T, bool kHasW>
+__global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T> A) {
+    DevState* st = A.st;
+    SweepState* sw = A.sw;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    if (st->done) {
+        if (A.use_cond && lead) cudaGraphSetConditional(A.cond_loop, 0u);
+        return;
+    }
+    __shared__ SweepSmem<T> sm;
+    __shared__ T tscratch[32];
+    __shared__ SweepCtl sc;
+    const Control& ctl = st->ctl;  // not written while the kernel runs
+    const int n = A.n;
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    if (threadIdx.x == 0) {
+        sc.moves = st->moves;
+        sc.solve_moves = st->solve_moves;
+        sc.iters = st->iters;
+        sc.mask_cursor = st->mask_cursor;
+        sc.tot_green = st->tot_green;
+        sc.tot_edges = st->tot_edges;
+        sc.push_moves = st->push_moves;
+        sc.pull_moves = st->pull_moves;
+        sc.hsum = st->hsum;
+        sc.habs = st->habs;
+        sc.t_start = st->t_start;
+        sc.fresh = st->fresh;
+        sc.gen = ld_acquire_u32(&sw->bar.gen);
+        sc.p = (int)(sw->bar.parity & 1u);
+    }
+    __syncthreads();
+
+    for (;;) {
+        SweepSlot* sl = &sw->slot[sc.p];
+        // ---------------------------------------------------------- stats
+        {
+            const bool link = ctl.sched == SCHED_LINK;
+            T a = T(0), s = T(0), pr = T(0);
+            stats_slice<T, true>(A.c, A.ideg, n, link, ctl.r, A.vec_ok,
+                                 blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                 (long long)gridDim.x * blockDim.x, a, s, pr);
+            const T ba = block_sum(a, tscratch);
+            const T bs = block_sum(s, tscratch);
+            const T bp = block_sum(pr, tscratch);
+            if (threadIdx.x == 0) {
+                if (ba != T(0)) atomicAdd(&sl->a, (double)ba);
+                if (bs != T(0)) atomicAdd(&sl->s, (double)bs);
+                if (bp != T(0)) atomicAdd(&sl->pr, (double)bp);
+                if (blockIdx.x == 0) sl->tstamp = globaltimer();
+            }
+        }
+        if (!grid_barrier(&sw->bar, sc.gen)) break;
+
+        // -------------------------------------------------------- control
+        if (threadIdx.x == 0) {
+            if (blockIdx.x == 0) {
+                SweepSlot* o = &sw->slot[sc.p ^ 1];
+                o->a = 0.0;
+                o->s = 0.0;
+                o->pr = 0.0;
+                o->msum = 0.0;
+                o->mabs = 0.0;
+                o->reserve = 0ull;
+            }
+            const int r = ctl.r;
+            const bool link = ctl.sched == SCHED_LINK;
+            const double l1 = __ldcg(&sl->a), sum = __ldcg(&sl->s);
+            const double sumr = (r == 1 && !link) ? l1 : __ldcg(&sl->pr);
+            sc.l1 = l1;
+            const unsigned long long now = __ldcg(&sl->tstamp);
+            if (sc.iters == 0) sc.t_start = now;
+            sc.iters++;
+            int stop = -1;
+            bool skip = false, want_refresh = false;
+            const bool degenerate = !(fabs(sc.hsum) > 1e-12 * sc.habs) || sc.habs == 0.0;
+            const bool converged = sc.moves >= 1 && l1 / fabs(sc.hsum) < ctl.tol;
+            if (degenerate) {
+                stop = ST_DEGENERATE;
+            } else if (converged) {
+                if (ctl.mixed && !sc.fresh) {
+                    want_refresh = true;  // re-derive, then test again
+                    skip = true;
+                } else {
+                    stop = ST_OK;
+                }
+            } else if (sc.solve_moves >= ctl.max_steps) {
+                stop = ST_NOCONV;
+            } else if ((double)(now - sc.t_start) > ctl.time_limit_ns || sc.iters > ctl.max_iters) {
+                stop = ST_TIMEOUT;
+            }
+            if (stop < 0 && !skip && ctl.mixed && ctl.refresh_factor > 0.0 &&
+                l1 < ctl.refresh_factor * st->l1_refresh)
+                want_refresh = true;  // after this move
+            sc.leave = (stop >= 0 || skip) ? 1 : 0;
+            sc.want_refresh = want_refresh ? 1 : 0;
+            int sched = ctl.sched;
+            if (ctl.safety_every > 0 && ((sc.solve_moves + 1) % ctl.safety_every) == 0)
+                sched = SCHED_ALL_GREEN;
+            double theta = 0.0;
+            if (sched == SCHED_THRESHOLD || sched == SCHED_LINK) {
+                const double mean = sumr / (double)n;
+                theta = ctl.theta_arg > 0.0 ? ctl.theta_arg
+                                            : (r == 1 ? ctl.theta_scale * mean
+                                                      : ctl.theta_scale * pow(mean, 1.0 / r));
+            }
+            sc.sched = sched;
+            sc.theta = theta;
+            sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+            if (blockIdx.x == 0) {
+                st->l1 = l1;
+                st->sum = sum;
+                st->sumr = sumr;
+                st->iters = sc.iters;
+                st->t_start = sc.t_start;
+                if (sc.leave) {
+                    st->mode = MODE_NONE;
+                    sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                    if (stop >= 0) {
+                        st->done = 1;
+                        st->status = stop;
+                    } else {
+                        st->want_refresh = 1;
+                        st->skip_move = 1;
+                    }
+                    if (A.use_cond) {
+                        if (stop >= 0) cudaGraphSetConditional(A.cond_loop, 0u);
+                        if (ctl.mixed) cudaGraphSetConditional(A.cond_refresh, stop >= 0 ? 0u : 1u);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (sc.leave) return;
+
+        // --------------------------------------------------------- select
+        {
+            const int sched = sc.sched;
+            const T th = kF32 ? (T)sc.theta_f : (T)sc.theta;
+            const unsigned char* mask =
+                (sched == SCHED_MASK) ? A.masks + (size_t)(sc.mask_cursor % ctl.n_masks) * (size_t)n : nullptr;
+            const SchedAux ax = sched_aux(ctl, n, sc.moves, sc.l1);
+            double bmsum, bmabs;
+            sweep_select<T>(A, sched, th, mask, ax, sl, bmsum, bmabs);
+            if (threadIdx.x == 0) {
+                if (bmsum != 0.0) atomicAdd(&sl->msum, bmsum);
+                if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
+            }
+        }
+        if (!grid_barrier(&sw->bar, sc.gen)) break;
+
+        // ---------------------------------------------------- choose move
+        if (threadIdx.x == 0) {
+            const int sched = sc.sched;
+            const unsigned long long rsv = __ldcg(&sl->reserve);
+            long long green = (long long)(rsv & ((1ull << kCountBits) - 1ull));
+            long long edges = (long long)(rsv >> kCountBits);
+            if (sched == SCHED_ALL_GREEN) {
+                green = n;
+                edges = ctl.nnz;
+            }
+            const double ms = __ldcg(&sl->msum), ma = __ldcg(&sl->mabs);
+            sc.hsum += ms;
+            sc.habs += ma;
+            sc.moves++;
+            sc.solve_moves++;
+            sc.tot_green += green;
+            sc.tot_edges += edges;
+            sc.fresh = 0;
+            if (sched == SCHED_MASK) sc.mask_cursor++;
+            int mode;
+            if (green == 0) mode = MODE_NONE;
+            else if (sched == SCHED_ALL_GREEN || (double)edges >= ctl.pull_crossover * (double)ctl.nnz)
+                mode = MODE_PULL;
+            else
+                mode = MODE_PUSH;
+            if (mode == MODE_PUSH) sc.push_moves++;
+            if (mode == MODE_PULL) sc.pull_moves++;
+            sc.mode = mode;
+            sc.green = green;
+            sc.edges = edges;
+            if (blockIdx.x == 0) {
+                st->theta = sc.theta;
+                st->theta_f = sc.theta_f;
+                st->green = green;
+                st->edges = edges;
+                st->hsum = sc.hsum;
+                st->habs = sc.habs;
+                st->last_mabs = ma;
+                st->moves = sc.moves;
+                st->solve_moves = sc.solve_moves;
+                st->tot_green = sc.tot_green;
+                st->tot_edges = sc.tot_edges;
+                st->push_moves = sc.push_moves;
+                st->pull_moves = sc.pull_moves;
+                st->fresh = 0;
+                st->skip_move = 0;
+                st->mask_cursor = sc.mask_cursor;
+                st->mode = mode;
+                MoveRecord rec;
+                rec.move = sc.moves - 1;
+                rec.green = green;
+                rec.edges = edges;
+                rec.mode = mode;
+                rec.pad = 0;
+                rec.theta = sc.theta;
+                rec.l1 = st->l1;
+                rec.hsum = sc.hsum;
+                A.log[rec.move % kLogCap] = rec;
+            }
+        }
+        __syncthreads();
+
+        // ----------------------------------------------------------- move
+        if (sc.mode == MODE_PUSH)
+            push_chunks<T, kHasW, true>(A.c, A.col, A.w, A.f_eoff, A.f_base, A.f_m, A.chunk_row,
+                                        sc.edges, sc.green, blockIdx.x, gridDim.x, sm.push);
+        else if (sc.mode == MODE_PULL)
+            pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
+                                          A.ntiles, blockIdx.x, gridDim.x, sm.pull);
+        if (!grid_barrier(&sw->bar, sc.gen)) break;
+        if (sc.want_refresh) {
+            if (lead) {
+                st->want_refresh = 1;
+                sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                if (A.use_cond) cudaGraphSetConditional(A.cond_refresh, 1u);
+            }
+            return;
+        }
+        if (threadIdx.x == 0) sc.p ^= 1;
+        __syncthreads();
+    }
+    // A barrier wait gave up: end the solve with an error status.
+    if (threadIdx.x == 0) {
+        st->done = 1;
+        st->status = ST_BARRIER;
+        if (A.use_cond) {
+            cudaGraphSetConditional(A.cond_loop, 0u);
+            if (ctl.mixed) cudaGraphSetConditional(A.cond_refresh, 0u);
+        }
+    }
+}
+
+}  // namespace rlgl

@@ -19,13 +19,13 @@ import numpy as np
 
 from . import _build
 
-ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD = 0, 1, 2, 3, 4
+ALL_GREEN, THRESHOLD, TOPFRAC, MASK, LINK_THRESHOLD, BLOCK_RR, PC = 0, 1, 2, 3, 4, 5, 6
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 SCHEDULES = {"all_green": ALL_GREEN, "threshold": THRESHOLD, "topfrac": TOPFRAC, "mask": MASK,
-             "link_threshold": LINK_THRESHOLD}
+             "link_threshold": LINK_THRESHOLD, "block_rr": BLOCK_RR, "pc": PC}
 PRECISIONS = {"fp64": FP64, "mixed": MIXED}
-KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh")
+KERNEL_CLASSES = ("stats", "select", "push", "pull", "topk", "refresh", "sweep")
 
 _STATUS = {0: "RLGL_OK", 1: "RLGL_EINVAL", 2: "RLGL_ENOTSTOCHASTIC", 3: "RLGL_ENOMEM",
            4: "RLGL_ECUDA", 5: "RLGL_EDEGENERATE", 6: "RLGL_ENOCONV", 7: "RLGL_ETIMEOUT"}
@@ -42,7 +42,9 @@ class Params(ctypes.Structure):
     _fields_ = [("theta_scale", ctypes.c_double), ("r", ctypes.c_int32),
                 ("top_frac", ctypes.c_double), ("pull_crossover", ctypes.c_double),
                 ("safety_every", ctypes.c_int32), ("refresh_factor", ctypes.c_double),
-                ("time_limit_s", ctypes.c_double)]
+                ("time_limit_s", ctypes.c_double), ("rr_blocks", ctypes.c_int64),
+                ("pc_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("persistent", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):
@@ -107,6 +109,7 @@ SIGNATURES = {
     "rlgl_profile": (_ST, [_VP, _I32]),
     "rlgl_kernel_times": (_ST, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "rlgl_profile_moves": (_ST, [_VP, _I32, _D, _I64]),
+    "rlgl_profile_sweep": (_ST, [_VP, _I32, _D, _I64]),
     "rlgl_move_log": (_ST, [_VP, ctypes.POINTER(MoveRecord), _I64, ctypes.POINTER(_I64)]),
     "rlgl_invariant_residual_noalloc": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                               _VP]),
@@ -333,6 +336,12 @@ class Chain:
         self._c(self.lib.rlgl_profile_moves(self.ctx, _sched(schedule), float(theta), int(moves)))
         return self.kernel_times()
 
+    def profile_sweep(self, schedule, theta: float, moves: int):
+        """`moves` moves of the persistent sweep launched eagerly, each launch
+        timed with CUDA events (class "sweep"); returns kernel_times()."""
+        self._c(self.lib.rlgl_profile_sweep(self.ctx, _sched(schedule), float(theta), int(moves)))
+        return self.kernel_times()
+
     def move_log(self, count: int):
         buf = (MoveRecord * int(count))()
         n = ctypes.c_int64()
@@ -340,8 +349,8 @@ class Chain:
         return [buf[i].asdict() for i in range(n.value)]
 
     def kernel_times(self):
-        ms = (ctypes.c_double * 6)()
-        n = (ctypes.c_int64 * 6)()
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        n = (ctypes.c_int64 * len(KERNEL_CLASSES))()
         self._c(self.lib.rlgl_kernel_times(self.ctx, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
 

@@ -104,7 +104,10 @@ class Server:
                 queue.popleft()
                 start = now()
                 ch = rlgl.Chain(r.csr, precision=self.precision)
-                ch.set_params(theta_scale=self.theta_scale)
+                # Solves run side by side here: the persistent sweep (a
+                # cooperative kernel that takes the whole GPU) is for a
+                # solve that has the device to itself.
+                ch.set_params(theta_scale=self.theta_scale, persistent=0)
                 ch.solve_async(r.schedule, 0.0, r.tol, r.max_steps)
                 active[r.id] = (r, ch, need, start)
                 used += need

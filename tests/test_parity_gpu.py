@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 FP64_PI_TOL = 1e-12
 MIXED_PI_TOL = 1e-6
 SCHEDS = {"all_green": oracle.ALL_GREEN, "threshold": oracle.THRESHOLD, "topfrac": oracle.TOPFRAC,
-          "link_threshold": oracle.LINK_THRESHOLD}
+          "link_threshold": oracle.LINK_THRESHOLD, "block_rr": oracle.BLOCK_RR, "pc": oracle.PC}
 
 
 def Chain(*a, **k):
@@ -84,14 +84,17 @@ def rounding_budget(csr, p, c, green, unit):
     return (adds + 4.0) * unit * A + 1e-300
 
 
-def _one_move_parity(csr, p, ch, sched, theta=0.0, top_frac=0.01):
+def _one_move_parity(csr, p, ch, sched, theta=0.0, top_frac=0.01, move=0):
     """From the GPU's current state, one oracle move and one GPU move must
     agree: the same green set (up to ties within rounding of theta) and, node
-    by node, the same new cash within the rounding budget."""
+    by node, the same new cash within the rounding budget. `move` is the
+    number of moves made since step 0 (BLOCK_RR and PC)."""
     unit = 2.0 ** -53 if ch.precision == "fp64" else 2.0 ** -24
     c, h = ch.get_state()
+    prm = ch.get_params()
     g_or, th = oracle.select(c, SCHEDS[sched], abs_theta=theta, top_frac=top_frac,
-                             theta_scale=ch.get_params().theta_scale, row_ptr=csr.row_ptr)
+                             theta_scale=prm.theta_scale, row_ptr=csr.row_ptr, move=move,
+                             rr_blocks=prm.rr_blocks, pc_frac=prm.pc_frac, seed=prm.seed)
     info = ch.step(sched, theta if sched != "topfrac" else top_frac)
     c2, h2 = ch.get_state()
     # green sets: nodes whose history changed on the GPU vs the oracle's set
@@ -106,6 +109,14 @@ def _one_move_parity(csr, p, ch, sched, theta=0.0, top_frac=0.01):
     band = 1e-12 if ch.precision == "fp64" else 1e-4
     deg = np.diff(csr.row_ptr)
     for i in diff:
+        if sched == "pc":
+            # u_{t,i} against k |C_i| / ||C||_1, with ||C||_1 summed in
+            # another order
+            pr = prm.pc_frac * csr.n * abs(c[i]) / np.abs(c).sum()
+            u = oracle.pc_uniform(prm.seed, move, int(i))
+            assert abs(u - pr) <= band * pr, (i, u, pr)
+            continue
+        assert sched != "block_rr", i  # no arithmetic: exact
         v = abs(c[i]) / deg[i] if sched == "link_threshold" else abs(c[i])
         assert abs(v - th) <= band * max(th, 1e-300), (i, c[i], th)
     if not diff:
@@ -148,6 +159,49 @@ def test_moves_medium_push_pull(medium, sched, mode, prec):
             info = _one_move_parity(csr, p, ch, sched, top_frac=0.02)
             if info["green"]:
                 assert info["mode"] == (2 if mode == "pull" else 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("sched,kw", [("block_rr", dict(rr_blocks=7)), ("block_rr", dict(rr_blocks=1)),
+                                      ("pc", dict(pc_frac=0.02, seed=9)), ("pc", dict(pc_frac=0.5, seed=1))])
+def test_moves_block_rr_and_pc(medium, sched, kw, prec):
+    """Block round robin and PC sampling, one move at a time from the GPU's
+    state: the same green sets (PC: the same counter-based draws) and cash."""
+    csr, p = medium
+    with Chain(csr, precision=prec) as ch:
+        ch.set_params(**kw)
+        for t in range(10):
+            info = _one_move_parity(csr, p, ch, sched, move=t)
+            if sched == "block_rr" and kw["rr_blocks"] == 1:
+                assert info["green"] == csr.n
+
+
+@pytest.mark.parametrize("sched,kw", [("block_rr", dict(rr_blocks=5)), ("pc", dict(pc_frac=0.2, seed=3))])
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_solve_block_rr_and_pc_vs_oracle(tiny, sched, kw, persistent):
+    csr, p, ref = tiny
+    pi_or, C, H, info_or = oracle.run(csr, sched=SCHEDS[sched], tol=1e-12, max_steps=200000, **kw)
+    with Chain(csr) as ch:
+        ch.set_params(persistent=persistent, **kw)
+        info = ch.solve(sched, tol=1e-12, max_steps=200000)
+        pi_tol = ch.estimate()
+        ch.reset()
+        ch.solve(sched, tol=0.0, max_steps=info_or["moves"], raise_on_noconv=False)
+        pi = ch.estimate()
+    assert info["status"] == "RLGL_OK"
+    assert abs(info["moves"] - info_or["moves"]) <= max(1, info_or["moves"] // 1000)
+    assert np.abs(pi - pi_or).sum() <= FP64_PI_TOL
+    assert np.abs(pi_tol - ref).sum() <= 1e-11
+
+
+def test_block_rr_and_pc_rejected_for_a_batch():
+    from paper_2008_02710_gb300.rlgl import RLGLError
+    big, node_ptr = synth.stack_chains([synth.tiny_chain(200, seed=s) for s in (1, 2)])
+    with Chain(big, node_ptr=node_ptr) as ch:
+        for sched in ("block_rr", "pc"):
+            with pytest.raises(RLGLError) as e:
+                ch.solve(sched, tol=1e-9)
+            assert e.value.name == "RLGL_EINVAL"
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -1,0 +1,128 @@
+"""The persistent sweep (one cooperative kernel per stretch of a solve,
+grid barriers between the phases of a move) against the path with one
+kernel per phase, on the same seeded chains, and its profiling entry point.
+Both paths make the moves of Alg. 1; they differ only in the order in
+which floating-point atomic additions land, so trajectories agree up to
+rounding and the stop test may fire a move apart."""
+import numpy as np
+import pytest
+
+from paper_2008_02710_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def Chain(*a, **k):
+    from paper_2008_02710_gb300.rlgl import Chain as C
+    return C(*a, **k)
+
+
+@pytest.fixture(scope="module")
+def weighted():
+    # 2^14 nodes, ~300k weighted edges: many push chunks and merge-path tiles
+    return synth.rmat_chain(14, 16, seed=5, weighted=True)
+
+
+@pytest.fixture(scope="module")
+def unweighted():
+    # ragged size: not a multiple of the vector width or of a block-iteration
+    return synth.rmat_chain_n(10007, 8, seed=3)
+
+
+def _solve(csr, prec, sched, persistent, tol, max_steps=100000, **params):
+    with Chain(csr, precision=prec) as ch:
+        ch.set_params(persistent=persistent, **params)
+        info = ch.solve(sched, tol=tol, max_steps=max_steps, raise_on_noconv=False)
+        # the sweep was not turned off for want of a cooperative graph node
+        assert ch.get_params().persistent == persistent, ch.lib.rlgl_last_error(ch.ctx)
+        pi = ch.estimate()
+        log = ch.move_log(min(info["moves"], 65536))
+        inv = ch.invariant_residual()
+    return info, pi, log, inv
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("sched", ["all_green", "threshold", "link_threshold"])
+@pytest.mark.parametrize("which", ["weighted", "unweighted"])
+def test_sweep_matches_phase_kernels(request, which, sched, prec):
+    csr = request.getfixturevalue(which)
+    tol = 1e-12 if prec == "fp64" else 1e-9
+    ia, pa, la, inva = _solve(csr, prec, sched, 1, tol, theta_scale=0.5)
+    ib, pb, lb, invb = _solve(csr, prec, sched, 0, tol, theta_scale=0.5)
+    assert ia["status"] == ib["status"] == "RLGL_OK"
+    assert abs(ia["moves"] - ib["moves"]) <= max(1, ib["moves"] // 1000)
+    assert abs(ia["refreshes"] - ib["refreshes"]) <= 1
+    # the first moves choose the same green sets up to nodes within
+    # rounding of the threshold
+    for ra, rb in list(zip(la, lb))[:20]:
+        assert abs(ra["green"] - rb["green"]) <= max(2, rb["green"] // 10000)
+        assert ra["mode"] == rb["mode"] or abs(ra["green"] - rb["green"]) > 0
+        if prec == "fp64":
+            assert abs(ra["theta"] - rb["theta"]) <= 1e-12 * max(rb["theta"], 1e-300)
+    bound = 1e-10 if prec == "fp64" else 2e-6
+    assert np.abs(pa - pb).sum() <= bound
+    assert abs(pa.sum() - 1) < 1e-12
+    assert inva <= max(10 * invb, 1e-12)
+
+
+def test_sweep_relaunches_for_each_rederivation(weighted):
+    """MIXED with a large refresh factor re-derives the cash many times: the
+    sweep returns for each and the graph launches it again."""
+    ia, pa, _, inva = _solve(weighted, "mixed", "link_threshold", 1, 1e-10, refresh_factor=0.1,
+                             theta_scale=0.5)
+    ib, pb, _, invb = _solve(weighted, "mixed", "link_threshold", 0, 1e-10, refresh_factor=0.1,
+                             theta_scale=0.5)
+    assert ia["status"] == ib["status"] == "RLGL_OK"
+    assert ia["refreshes"] >= 5
+    assert abs(ia["refreshes"] - ib["refreshes"]) <= 1
+    assert np.abs(pa - pb).sum() <= 1e-7
+    assert inva <= 1e-9
+
+
+def test_sweep_exact_move_count_and_resume(unweighted):
+    """tol 0 stops after exactly max_steps moves; a second solve continues
+    from the state the first one left."""
+    with Chain(unweighted, precision="fp64") as a, Chain(unweighted, precision="fp64") as b:
+        for ch in (a, b):
+            ch.set_params(theta_scale=0.5)
+        b.set_params(theta_scale=0.5, persistent=0)
+        i1 = a.solve("link_threshold", tol=0.0, max_steps=13, raise_on_noconv=False)
+        i2 = a.solve("link_threshold", tol=0.0, max_steps=17, raise_on_noconv=False)
+        i3 = b.solve("link_threshold", tol=0.0, max_steps=30, raise_on_noconv=False)
+        assert i1["status"] == i2["status"] == "RLGL_ENOCONV"
+        assert (i1["moves"], i2["moves"], i3["moves"]) == (13, 17, 30)
+        ca, ha = a.get_state()
+        cb, hb = b.get_state()
+    assert np.abs(ha - hb).max() <= 1e-12 * np.abs(hb).max()
+    assert np.abs(ca - cb).max() <= 1e-12 * np.abs(cb).max()
+
+
+def test_profile_sweep_times_the_kernel(weighted):
+    with Chain(weighted, precision="mixed") as a, Chain(weighted, precision="mixed") as b:
+        for ch in (a, b):
+            ch.set_params(theta_scale=0.5)
+        a.profile(2)
+        kt = a.profile_sweep("link_threshold", 0.0, 25)
+        b.solve("link_threshold", tol=0.0, max_steps=25, raise_on_noconv=False)
+        assert kt["sweep"][1] >= 1 and kt["sweep"][0] > 0
+        log = a.move_log(100)
+        assert [r["move"] for r in log] == list(range(25))
+        _, ha = a.get_state()
+        _, hb = b.get_state()
+    assert np.abs(ha - hb).sum() <= 1e-6 * np.abs(hb).sum()
+
+
+def test_sweep_not_used_where_it_does_not_apply(weighted):
+    """TOPFRAC and batches keep the one-kernel-per-phase path; asking to
+    profile the sweep there is an error."""
+    from paper_2008_02710_gb300.rlgl import RLGLError
+    with Chain(weighted) as ch:
+        info = ch.solve("topfrac", 0.05, tol=1e-10, max_steps=100000)
+        assert info["status"] == "RLGL_OK"
+        with pytest.raises(RLGLError) as e:
+            ch.profile_sweep("topfrac", 0.05, 5)
+        assert e.value.name == "RLGL_EINVAL"
+    big, node_ptr = synth.stack_chains([synth.tiny_chain(300, seed=s) for s in (1, 2, 3)])
+    with Chain(big, node_ptr=node_ptr) as ch:
+        with pytest.raises(RLGLError):
+            ch.profile_sweep("threshold", 0.0, 5)
