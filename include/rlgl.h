@@ -113,6 +113,12 @@ typedef struct {
                                as one persistent cooperative kernel per stretch between FP64
                                re-derivations of the cash, with grid barriers between the phases
                                of a move; 0: one kernel per phase. Same moves either way. */
+    double barrier_limit_s; /* persistent sweep: longest wait at a grid barrier (default 2,
+                               at most 60); a wait that runs out ends the solve with
+                               RLGL_ETIMEOUT and leaves the context usable */
+    int32_t test_skip_barrier; /* testing only (default 0): 1 makes one block of the sweep
+                                  leave before its first barrier, so that the others' wait
+                                  runs out (exercises the bounded wait without a fault) */
 } rlgl_params;
 
 typedef struct {

@@ -525,6 +525,8 @@ static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, dou
     c->rr_blocks = ctx->params.rr_blocks;
     c->pc_frac = ctx->params.pc_frac;
     c->seed = ctx->params.seed;
+    c->barrier_limit_ns = (unsigned long long)(ctx->params.barrier_limit_s * 1e9);
+    c->test_skip_barrier = ctx->params.test_skip_barrier;
     c->sched = sched;
     c->r = ctx->params.r;
     c->safety_every = solving ? ctx->params.safety_every : 0;
@@ -769,6 +771,8 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->pc_frac = 0.05;
     p->seed = 0;
     p->persistent = 1;
+    p->barrier_limit_s = 2.0;
+    p->test_skip_barrier = 0;
     return RLGL_OK;
 }
 
@@ -1340,7 +1344,8 @@ rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
     if (!(p->theta_scale > 0.0) || p->r < 1 || !(p->top_frac > 0.0 && p->top_frac <= 1.0) ||
         !(p->pull_crossover >= 0.0) || p->safety_every < 0 || !(p->refresh_factor >= 0.0 && p->refresh_factor < 1.0) ||
         !(p->time_limit_s > 0.0) || (p->persistent != 0 && p->persistent != 1) || p->rr_blocks < 1 ||
-        !(p->pc_frac > 0.0 && p->pc_frac <= 1e30))
+        !(p->pc_frac > 0.0 && p->pc_frac <= 1e30) || !(p->barrier_limit_s > 0.0 && p->barrier_limit_s <= 60.0) ||
+        (p->test_skip_barrier != 0 && p->test_skip_barrier != 1))
         return fail(ctx, RLGL_EINVAL, "parameter out of range");
     ctx->params = *p;
     return RLGL_OK;

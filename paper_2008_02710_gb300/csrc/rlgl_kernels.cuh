@@ -91,6 +91,9 @@ struct Control {
     long long rr_blocks;     // BLOCK_RR: K
     double pc_frac;          // PC: k = pc_frac N
     unsigned long long seed; // PC: generator seed
+    unsigned long long barrier_limit_ns;  // persistent sweep: longest barrier wait
+    int test_skip_barrier;   // persistent sweep: one block leaves before its first barrier
+    int pad2;
     int sched;
     int r;
     int safety_every;

@@ -26,8 +26,7 @@
 
 namespace rlgl {
 
-constexpr int kSweepMinBlocks = 4;                            // blocks per SM (launch bounds)
-constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s per barrier wait
+constexpr int kSweepMinBlocks = 4;  // blocks per SM (launch bounds)
 constexpr int ST_BARRIER = 9;
 
 // Per-move accumulators, zero at rest. Two slots alternate: the slot of
@@ -61,9 +60,10 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 
 // Grid-wide barrier of a cooperative launch. Thread 0 of each block
 // arrives; the last one to arrive resets the count and publishes the next
-// generation; the others wait for it, at most kBarrierLimitNs. Returns false
-// (in every thread of the block) when the sweep must stop.
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen) {
+// generation; the others wait for it, at most limit_ns. Returns false (in
+// every thread of the block) when the sweep must stop.
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen,
+                                             unsigned long long limit_ns) {
     // gen: the block's barrier count (shared memory; thread 0 keeps it)
     __shared__ int s_ok;
     __syncthreads();
@@ -83,7 +83,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen) {
                     ok = 0;
                     break;
                 }
-                if (globaltimer() - t0 > kBarrierLimitNs) {
+                if (globaltimer() - t0 > limit_ns) {
                     atomicExch(&bar->abort, 1u);
                     ok = 0;
                     break;
@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         sc.p = (int)(sw->bar.parity & 1u);
     }
     __syncthreads();
+    // Test of the bounded wait: the last block leaves without arriving, so
+    // the others' first barrier wait runs out.
+    if (ctl.test_skip_barrier && blockIdx.x == gridDim.x - 1 && gridDim.x > 1) return;
 
     for (;;) {
         SweepSlot* sl = &sw->slot[sc.p];
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (blockIdx.x == 0) sl->tstamp = globaltimer();
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
 
         // -------------------------------------------------------- control
         if (threadIdx.x == 0) {
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
 
         // ---------------------------------------------------- choose move
         if (threadIdx.x == 0) {
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull);
-        if (!grid_barrier(&sw->bar, sc.gen)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
         if (sc.want_refresh) {
             if (lead) {
                 st->want_refresh = 1;

@@ -126,3 +126,23 @@ def test_sweep_not_used_where_it_does_not_apply(weighted):
     with Chain(big, node_ptr=node_ptr) as ch:
         with pytest.raises(RLGLError):
             ch.profile_sweep("threshold", 0.0, 5)
+
+
+def test_barrier_wait_is_bounded_and_context_survives(weighted):
+    """One block leaves before its first barrier (test hook): the others'
+    wait runs out after the limit, the solve ends with RLGL_ETIMEOUT, and
+    the next solve on the same context runs normally."""
+    import time
+    with Chain(weighted, precision="mixed") as ch:
+        ch.set_params(theta_scale=0.5, barrier_limit_s=0.05, test_skip_barrier=1)
+        t0 = time.perf_counter()
+        info = ch.solve("link_threshold", tol=1e-9, raise_on_noconv=False)
+        dt = time.perf_counter() - t0
+        assert info["status"] == "RLGL_ETIMEOUT"
+        assert dt < 5.0
+        assert "barrier" in ch.lib.rlgl_last_error(ch.ctx).decode()
+        ch.set_params(test_skip_barrier=0, barrier_limit_s=2.0)
+        ch.reset()
+        info = ch.solve("link_threshold", tol=1e-9)
+        assert info["status"] == "RLGL_OK"
+        assert ch.get_params().persistent == 1
