@@ -155,6 +155,8 @@ def _ptr(a, dtype=None):
         import torch
         if isinstance(a, torch.Tensor):
             if dtype is not None:
+                if not isinstance(dtype, torch.dtype):
+                    dtype = _np_dtype(np.dtype(dtype).type)
                 a = a.to(dtype=dtype)
             a = a.contiguous()
             return a.data_ptr(), (DEVICE if a.is_cuda else HOST), a

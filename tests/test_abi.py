@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -49,3 +50,14 @@ def test_host_only_entry_points():
     assert lib.rlgl_status_string(5) == b"RLGL_EDEGENERATE"
     with pytest.raises(rlgl.RLGLError):
         rlgl._check(lib, None, lib.rlgl_set_params(None, None))
+
+
+def test_torch_tensor_with_numpy_dtype_is_converted():
+    """A torch tensor passed where the C ABI wants float64 is converted with
+    the matching torch dtype (host tensor: host memory space)."""
+    torch = pytest.importorskip("torch")
+    from paper_2008_02710_gb300 import rlgl
+    t = torch.arange(4, dtype=torch.float32)
+    p, sp, keep = rlgl._ptr(t, np.float64)
+    assert sp == rlgl.HOST and keep.dtype == torch.float64 and p == keep.data_ptr()
+    assert keep.tolist() == [0.0, 1.0, 2.0, 3.0]

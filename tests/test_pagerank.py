@@ -70,7 +70,11 @@ def test_pagerank_degenerate_schedule_on_gpu():
         _, h = ch.get_state()
         assert abs(h.sum() - 0.85 ** 10) < 1e-14
         info = ch.solve("threshold", tol=1e-12, max_steps=3000, raise_on_noconv=False)
-    assert info["status"] == "RLGL_ENOCONV" and abs(info["sum_hist"]) < 1e-9
+    # The device tests |H 1| against an upper bound of sum |H| (the moved
+    # mass), the oracle against sum |H| itself: the device may call the run
+    # degenerate where the oracle runs out of moves. Neither converges.
+    assert info["status"] in ("RLGL_ENOCONV", "RLGL_EDEGENERATE")
+    assert abs(info["sum_hist"]) < 1e-9
 
 
 def test_dangling_nodes_follow_restart_law():
