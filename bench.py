@@ -58,6 +58,10 @@ WORKLOADS = {
                         "weights U(0,1], FP32 cash, FP64 history"),
     "rmat16": dict(scale=16, edge_factor=16, weighted=False, precision="mixed",
                    desc="R-MAT scale 16 (small case)"),
+    "rmat24u": dict(scale=24, edge_factor=16, weighted=False, precision="mixed", undirected=True,
+                    desc="R-MAT scale 24 symmetrised (N=2^24, every R-MAT edge both ways, cycle both "
+                         "ways, self-loops; unit weights), FP32 cash, FP64 history; reference "
+                         "pi_i = d_i / sum d"),
     "pagerank20": dict(scale=20, edge_factor=16, weighted=False, precision="mixed", pagerank=True,
                        desc="PageRank c=0.85, uniform restart, on R-MAT scale 20 through the "
                             "auxiliary-node chain P^(0) (N=2^20+1), FP32 cash, FP64 history"),
@@ -166,7 +170,8 @@ def make_workload(name: str, seed: int = 1, precision=None):
     w = dict(WORKLOADS[name])
     if precision:
         w["precision"] = precision
-    csr = synth.rmat_chain(w["scale"], w["edge_factor"], seed=seed, weighted=w["weighted"])
+    csr = synth.rmat_chain(w["scale"], w["edge_factor"], seed=seed, weighted=w["weighted"],
+                           undirected=w.get("undirected", False))
     if w.get("pagerank"):
         csr = synth.pagerank_chain(csr)
     return csr, w
@@ -182,14 +187,20 @@ def workload_m0(csr, wl):
     return m0
 
 
-def oracle_reference(csr, tol=1e-11, maxit=50000):
-    """Oracle leg: the FP64 oracle's power iteration (host cores) gives the
-    reference stationary law that defines the L1 error."""
+def oracle_reference(csr, tol=1e-11, maxit=50000, undirected=False):
+    """Oracle leg: the reference stationary law that defines the L1 error:
+    the closed form d_i / sum d for a symmetrised graph, else the FP64
+    oracle's power iteration (host cores)."""
     import oracle
+    if undirected:
+        t = time.time()
+        return oracle.degree_law(csr), dict(kind="closed form d_i / sum d (oracle.degree_law)",
+                                            seconds=time.time() - t)
     p = oracle.transition_probs(csr)
     t = time.time()
     pi, it, delta = oracle.power_iteration(csr, p, tol=tol, maxit=maxit, nthreads=os.cpu_count() or 1)
-    return pi, dict(iterations=it, delta=delta, seconds=time.time() - t, cores=os.cpu_count())
+    return pi, dict(kind="oracle power iteration (FP64, host)", iterations=it, delta=delta,
+                    seconds=time.time() - t, cores=os.cpu_count())
 
 
 def oracle_cpu_sample(csr, budget_s=15.0, min_moves=2):
@@ -315,7 +326,11 @@ class GpuRun:
         ch.profile(2)
         kt = ch.profile_sweep(sched, theta, tstar)
         ch.profile(2)
-        return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull"))
+        log = ch.move_log(tstar)
+        names = ("stats", "stats_wait", "select", "select_wait", "move", "move_wait")
+        ph = np.array([r["phase_us"] for r in log], dtype=np.float64)
+        phases = {k: float(v) for k, v in zip(names, ph.mean(axis=0))} if len(ph) else {}
+        return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull")), phases
 
     def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0):
         """Through the public API with host buffers: every step uploads the
@@ -391,7 +406,7 @@ def run_gpu(args):
     dist = init_dist(ws, "nccl")
     csr, wl = make_workload(args.workload, precision=args.precision)
     # oracle leg: reference stationary law (host cores)
-    ref, ref_info = oracle_reference(csr)
+    ref, ref_info = oracle_reference(csr, undirected=wl.get("undirected", False))
     ref_dev = torch.from_numpy(ref).to(device)
     g = GpuRun(csr, wl, device)
     # schedule -> (library schedule, theta argument, theta_scale, move cap)
@@ -433,7 +448,7 @@ def run_gpu(args):
     sweep_on = args.persistent == 1 and head != "topfrac"
     if sweep_on:
         nvtx.range_push("profile_sweep")
-        (ms_sw, n_sw), bytes_sw = g.sweep_profile(sched_h, theta_h, tstar, alg)
+        (ms_sw, n_sw), bytes_sw, sweep_phases = g.sweep_profile(sched_h, theta_h, tstar, alg)
         nvtx.range_pop()
     # the headline schedule on the one-kernel-per-phase path, for comparison
     phase_ms = None
@@ -525,10 +540,11 @@ def run_gpu(args):
         "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step)
         if compare.get("all_green", {}).get("ms") else None,
         "persistent_sweep": sweep_on,
+        "sweep_phase_us_per_move": sweep_phases if sweep_on else None,
         "time_to_err_ms_phase_kernels": phase_ms,
         "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
         "final_l1_err": final_err,
-        "reference": {"kind": "oracle power iteration (FP64, host)", **ref_info},
+        "reference": ref_info,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
@@ -695,6 +711,71 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fixed(args):
+    """A fixed number of moves on both precision paths against the oracle's
+    moves of the same schedule from the same step 0: the error of each path
+    at equal moves, the device time and the achieved bandwidth of the sweep.
+    For chains whose relaxation time puts L1 1e-6 out of reach of every
+    schedule (weighted R-MAT: nodes whose self-loop keeps almost all of
+    their walk)."""
+    import torch
+    import oracle
+    from paper_2008_02710_gb300.rlgl import Chain
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    csr, wl = make_workload(args.workload)
+    T = args.fixed_moves
+    sched = args.sched
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    t0 = time.time()
+    info_or = oracle.solve(csr, p, C, H, sched=getattr(oracle, sched.upper()),
+                           theta_scale=args.theta_scale if sched == "link_threshold" else 1.0,
+                           tol=0.0, max_steps=T, check_every=-1)
+    t_or = time.time() - t0
+    pi_or = oracle.estimate(H)
+    out = {"metric": "fixed-move solve: device time, edge-pushes/s, L1 vs the oracle at equal moves",
+           "workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
+           "schedule": sched, "moves": T,
+           "oracle": {"seconds": t_or, "edge_pushes": info_or["pushes"], "threads": 1}}
+    peak, peak_src = measured_peaks()
+    stream = torch.cuda.Stream(device=device)
+    for prec in ("fp64", "mixed"):
+        with Chain(csr, precision=prec, stream=stream) as ch:
+            ch.set_params(theta_scale=args.theta_scale if sched == "link_threshold" else 1.0,
+                          persistent=args.persistent)
+            times = []
+            for i in range(args.warmup + args.steps):
+                ch.reset()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                info = ch.solve(sched, tol=0.0, max_steps=T, raise_on_noconv=False)
+                ev1.record(stream)
+                ev1.synchronize()
+                if i >= args.warmup:
+                    times.append(ev0.elapsed_time(ev1))
+            pi = ch.estimate()
+            log = ch.move_log(T)
+        cash = 4 if prec == "mixed" else 8
+        wb = 4 if csr.w is not None else 0
+        alg = 0.0
+        for rec in log:
+            E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
+            alg += csr.n * (cash + 4) + csr.n * (2 * cash + 4) + G * (cash + 16 + 8 + 16 + 16 + cash)
+            if mode == 1:
+                alg += E * (4 + wb + cash) + G * (16 + cash)
+            elif mode == 2:
+                alg += csr.nnz * (4 + wb + cash) + csr.n * (8 + 2 * cash)
+        ms = float(np.median(times))
+        out[prec] = {"ms": ms, "edge_pushes": info["edges_pushed"],
+                     "edge_pushes_per_s": info["edges_pushed"] / (ms / 1e3),
+                     "l1_vs_oracle": float(np.abs(pi - pi_or).sum()),
+                     "alg_gbs": alg / (ms / 1e3) / 1e9, "hbm_frac": alg / (ms / 1e3) / 1e9 / peak,
+                     "peak": peak, "peak_source": peak_src}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -722,6 +803,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-moves", type=int, default=2)
+    ap.add_argument("--fixed-moves", type=int, default=0,
+                    help="> 0: time this many moves on both precision paths against the oracle's "
+                         "same moves instead of the time-to-error run")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -731,6 +815,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.fixed_moves > 0:
+        run_fixed(args)
     else:
         run_gpu(args)
 

@@ -150,6 +150,9 @@ typedef struct {
     double theta;           /* threshold used (0 when none) */
     double l1_cash;         /* ||C_t||_1 before the move */
     double sum_hist;        /* H_{t+1} 1 after the move */
+    float phase_us[6];      /* persistent sweep only (else 0), from block 0's clock: stats work,
+                               wait at the barrier after it, select work (with the decisions),
+                               wait, push/pull work, wait; microseconds */
 } rlgl_move_record;
 
 /* Fills p with the defaults listed in rlgl_params. */

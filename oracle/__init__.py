@@ -225,6 +225,14 @@ def gth(A) -> np.ndarray:
     return pi
 
 
+def degree_law(csr) -> np.ndarray:
+    """pi_i = d_i / sum_k d_k (d_i = row length with multiplicity): the
+    stationary law of the random walk on an undirected graph (each edge
+    stored in both directions, unit weights)."""
+    d = np.diff(np.asarray(csr.row_ptr)).astype(np.float64)
+    return d / d.sum()
+
+
 def dense_P(csr, p) -> np.ndarray:
     """Dense P from CSR probabilities (duplicates add)."""
     P = np.zeros((csr.n, csr.n))

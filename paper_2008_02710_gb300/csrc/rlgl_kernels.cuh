@@ -45,6 +45,7 @@ struct MoveRecord {                   // layout of rlgl_move_record
     long long move, green, edges;
     int mode, pad;
     double theta, l1, hsum;
+    float phase_us[6];
 };
 
 // Per-chain state of a batch (many independent chains on one block-diagonal
@@ -989,6 +990,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
         rec.theta = theta;
         rec.l1 = ss->l1;
         rec.hsum = ss->hsum;
+        for (int k = 0; k < 6; ++k) rec.phase_us[k] = 0.f;
         log[rec.move % kLogCap] = rec;
     }
     st_stage_out(st, &stage);

@@ -61,13 +61,16 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 // Grid-wide barrier of a cooperative launch. Thread 0 of each block
 // arrives; the last one to arrive resets the count and publishes the next
 // generation; the others wait for it, at most limit_ns. Returns false (in
-// every thread of the block) when the sweep must stop.
+// every thread of the block) when the sweep must stop. When ts is given,
+// thread 0 stores its arrival and release times in ts[0], ts[1].
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen,
-                                             unsigned long long limit_ns) {
+                                             unsigned long long limit_ns,
+                                             unsigned long long* ts = nullptr) {
     // gen: the block's barrier count (shared memory; thread 0 keeps it)
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (ts) ts[0] = globaltimer();
         int ok = 1;
         const unsigned int target = gen + 1u;
         __threadfence();
@@ -95,6 +98,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen,
         __threadfence();
         s_ok = ok;
         gen = target;
+        if (ts) ts[1] = globaltimer();
     }
     __syncthreads();
     return s_ok != 0;
@@ -246,6 +250,7 @@ struct SweepCtl {
     int want_refresh;  // return after this move for a re-derivation
     int p;             // slot parity
     unsigned int gen;  // barrier generation
+    unsigned long long ts[7];  // block 0: move start, then arrival / release at each barrier
 };
 
 template <typename T, bool kHasW>
@@ -286,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
 
     for (;;) {
         SweepSlot* sl = &sw->slot[sc.p];
+        if (lead) sc.ts[0] = globaltimer();
         // ---------------------------------------------------------- stats
         {
             const bool link = ctl.sched == SCHED_LINK;
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (blockIdx.x == 0) sl->tstamp = globaltimer();
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr)) break;
 
         // -------------------------------------------------------- control
         if (threadIdx.x == 0) {
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr)) break;
 
         // ---------------------------------------------------- choose move
         if (threadIdx.x == 0) {
@@ -459,6 +465,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 rec.theta = sc.theta;
                 rec.l1 = st->l1;
                 rec.hsum = sc.hsum;
+                for (int q = 0; q < 4; ++q) rec.phase_us[q] = (float)(sc.ts[q + 1] - sc.ts[q]) * 1e-3f;
+                rec.phase_us[4] = rec.phase_us[5] = 0.f;
                 A.log[rec.move % kLogCap] = rec;
             }
         }
@@ -471,7 +479,12 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull);
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns)) break;
+        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr)) break;
+        if (lead) {
+            MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
+            rec->phase_us[4] = (float)(sc.ts[5] - sc.ts[4]) * 1e-3f;
+            rec->phase_us[5] = (float)(sc.ts[6] - sc.ts[5]) * 1e-3f;
+        }
         if (sc.want_refresh) {
             if (lead) {
                 st->want_refresh = 1;

@@ -73,10 +73,12 @@ class MoveRecord(ctypes.Structure):
     _fields_ = [("move", ctypes.c_int64), ("green", ctypes.c_int64),
                 ("edges_pushed", ctypes.c_int64), ("mode", ctypes.c_int32),
                 ("theta", ctypes.c_double), ("l1_cash", ctypes.c_double),
-                ("sum_hist", ctypes.c_double)]
+                ("sum_hist", ctypes.c_double), ("phase_us", ctypes.c_float * 6)]
 
     def asdict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_us"] = list(self.phase_us)
+        return d
 
 
 _lock = threading.Lock()

@@ -544,3 +544,12 @@ def test_block_rr_dobrushin_bound():
         g, _ = oracle.select(C, oracle.BLOCK_RR, move=t - 1, rr_blocks=K)
         oracle.move(csr, p, g, C, H)
         assert np.abs(C).sum() <= 2.0 / delta * delta ** (t / K) + 1e-15
+
+
+def test_degree_law_is_the_stationary_law_of_an_undirected_walk():
+    """d_i / sum d solves pi = pi P for a symmetrised graph (GTH on a small
+    symmetrised R-MAT with the cycle both ways and self-loops)."""
+    csr = synth.rmat_chain(8, 4, seed=3, undirected=True)
+    p = oracle.transition_probs(csr)
+    ref = oracle.gth(oracle.dense_P(csr, p))
+    assert np.abs(oracle.degree_law(csr) - ref).sum() < 1e-12

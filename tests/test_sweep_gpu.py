@@ -50,7 +50,10 @@ def test_sweep_matches_phase_kernels(request, which, sched, prec):
     ia, pa, la, inva = _solve(csr, prec, sched, 1, tol, theta_scale=0.5)
     ib, pb, lb, invb = _solve(csr, prec, sched, 0, tol, theta_scale=0.5)
     assert ia["status"] == ib["status"] == "RLGL_OK"
-    assert abs(ia["moves"] - ib["moves"]) <= max(1, ib["moves"] // 1000)
+    # FP32 atomics on the MIXED path round differently with every order, so
+    # long MIXED solves drift apart by a few green sets; FP64 ones hardly
+    slack = 1000 if prec == "fp64" else 50
+    assert abs(ia["moves"] - ib["moves"]) <= max(1, ib["moves"] // slack)
     assert abs(ia["refreshes"] - ib["refreshes"]) <= 1
     # the first moves choose the same green sets up to nodes within
     # rounding of the threshold
@@ -107,6 +110,8 @@ def test_profile_sweep_times_the_kernel(weighted):
         assert kt["sweep"][1] >= 1 and kt["sweep"][0] > 0
         log = a.move_log(100)
         assert [r["move"] for r in log] == list(range(25))
+        # every move of the sweep carries its phase timings
+        assert all(min(r["phase_us"]) >= 0 and sum(r["phase_us"]) > 0 for r in log)
         _, ha = a.get_state()
         _, hb = b.get_state()
     assert np.abs(ha - hb).sum() <= 1e-6 * np.abs(hb).sum()
