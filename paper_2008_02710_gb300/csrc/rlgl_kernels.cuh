@@ -225,6 +225,15 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
+// Reductions into global memory whose old value nobody reads: red.global
+// (no value comes back, so the issuing warp tracks nothing).
+__device__ __forceinline__ void red_add(float* p, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 // Loads of data that other blocks of the same kernel may have written: from
 // L2 (ld.global.cg) when kCg, so that no stale L1 line is read.
 template <bool kCg, typename T>
@@ -1076,7 +1085,7 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                 const int j = __ldg(col + pos);
                 T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
-                atomicAdd(c + j, val);
+                red_add(c + j, val);
             }
         }
         __syncthreads();
@@ -1249,12 +1258,12 @@ __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __res
             if (threadIdx.x > 0 && sm.ckey[threadIdx.x - 1] == rowA) sum += sm.cval[threadIdx.x - 1];
             TO* o = out + rowA;
             // the tile's first row may have begun in the previous tile
-            if (rowA == r0 && sm.start0 < 0) atomicAdd(o, (TO)sum);
+            if (rowA == r0 && sm.start0 < 0) red_add(o, (TO)sum);
             else *o = (TO)(ld_shared_data<kCg>(o) + (TO)sum);
         }
         // last active thread: its carry leaves the tile
         const int last = (total - 1) / kMpIpt;
-        if ((int)threadIdx.x == last && rowB >= 0) atomicAdd(out + rowB, (TO)run);
+        if ((int)threadIdx.x == last && rowB >= 0) red_add(out + rowB, (TO)run);
         __syncthreads();
     }
 }
