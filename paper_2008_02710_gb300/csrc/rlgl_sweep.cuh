@@ -136,74 +136,118 @@ struct SweepArgs {
     int vec_ok;
 };
 
+// Shared cache of the select phase: the first kSelCached nodes of a block
+// (two block-iterations) keep their cash, row offset and degree between the
+// counting pass and the writing pass.
+constexpr int kSelCachedIters = 2;
+constexpr int kSelCached = kSelCachedIters * kNodesPerIter;
+template <typename T>
+struct SelSmem {
+    T val[kSelCached];
+    long long rb[kSelCached];
+    int rdeg[kSelCached];
+    unsigned char g[kSelCached];
+};
+
 // Select on this block's node slices (the single-chain form of k_select):
-// green nodes give their cash (m_i = C_i, C_i <- 0, H_i += m_i), reserve
-// frontier slots with one atomic per block-iteration and write their
+// green nodes give their cash (m_i = C_i, C_i <- 0, H_i += m_i) and get
 // frontier entries and push-chunk starts; mt holds m~_i (0 for red nodes).
-// Returns the block's sums of m_i and |m_i| in thread 0.
+// Two passes over the block's nodes: the first counts green nodes and their
+// edges, one atomic per block reserves the block's frontier range, the
+// second writes it (from the shared cache for the first two
+// block-iterations, re-reading beyond). Returns the block's sums of m_i and
+// |m_i| in thread 0.
 template <typename T>
 __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T th,
                                              const unsigned char* mask, const SchedAux& ax,
-                                             SweepSlot* sl, double& bmsum, double& bmabs) {
+                                             SweepSlot* sl, SelSmem<T>& cs, double& bmsum,
+                                             double& bmabs) {
     __shared__ T tscratch[32];
     __shared__ unsigned long long base_sh;
     const int n = A.n;
     T msum = T(0), mabs = T(0);
-    const bool dense_all = sched == SCHED_ALL_GREEN;
-    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
-         it0 += (long long)gridDim.x * kNodesPerIter) {
-        T val[kNodesPerThread];
-        long long rb[kNodesPerThread];
-        int rdeg[kNodesPerThread];
-        bool g[kNodesPerThread];
-        unsigned long long mine = 0ull;
-        if (!dense_all) {
-#pragma unroll
-            for (int q = 0; q < kNodesPerThread; ++q) {
-                const long long i = it0 + q * kThreads + threadIdx.x;
-                rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
-                rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kNodesPerThread; ++q) {
-            const long long i = it0 + q * kThreads + threadIdx.x;
-            g[q] = false;
-            val[q] = T(0);
-            if (i < n) {
-                const T v = __ldcg(A.c + i);
-                val[q] = v;
-                g[q] = green_test<T>(sched, v, i, th, mask, A.ideg, ax);
-            }
-            if (g[q] && !dense_all) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
-        }
-        if (dense_all) {
+    if (sched == SCHED_ALL_GREEN) {
+        // every node moves; the pull needs no frontier
+        for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+             it0 += (long long)gridDim.x * kNodesPerIter) {
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
                 const long long i = it0 + q * kThreads + threadIdx.x;
                 if (i >= n) continue;
-                const T v = val[q];
+                const T v = __ldcg(A.c + i);
                 A.c[i] = T(0);
                 A.H[i] += (double)v;
                 msum += v;
                 mabs += fabs(v);
                 A.mt[i] = moved_per_weight(v, A.s, A.sf, i);
             }
-            continue;
         }
-        unsigned long long total;
-        const unsigned long long pre = block_exscan(mine, &total);
-        if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
-        __syncthreads();
-        const unsigned long long base = base_sh + pre;
-        long long k = (long long)(base & ((1ull << kCountBits) - 1ull));
-        long long e = (long long)(base >> kCountBits);
+        bmsum = (double)block_sum(msum, tscratch);
+        bmabs = (double)block_sum(mabs, tscratch);
+        return;
+    }
+    // pass 1: count
+    unsigned long long mine = 0ull;
+    int j = 0;
+    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+         it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
+        long long rb[kNodesPerThread];
+        int rdeg[kNodesPerThread];
+        T val[kNodesPerThread];
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
+            rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
+            val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kNodesPerThread; ++q) {
+            const long long i = it0 + q * kThreads + threadIdx.x;
+            const bool g = (i < n) && green_test<T>(sched, val[q], i, th, mask, A.ideg, ax);
+            if (g) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+            if (j < kSelCachedIters) {
+                const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
+                cs.val[slot] = val[q];
+                cs.rb[slot] = rb[q];
+                cs.rdeg[slot] = rdeg[q];
+                cs.g[slot] = g ? 1 : 0;
+            }
+        }
+    }
+    // one reservation for the whole block
+    unsigned long long total;
+    const unsigned long long pre = block_exscan(mine, &total);
+    if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
+    __syncthreads();
+    const unsigned long long base = base_sh + pre;
+    long long k = (long long)(base & ((1ull << kCountBits) - 1ull));
+    long long e = (long long)(base >> kCountBits);
+    // pass 2: write
+    j = 0;
+    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+         it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
             if (i >= n) continue;
-            if (g[q]) {
-                const T v = val[q];
+            T v;
+            long long rb;
+            int rdeg;
+            bool g;
+            if (j < kSelCachedIters) {
+                const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
+                v = cs.val[slot];
+                rb = cs.rb[slot];
+                rdeg = cs.rdeg[slot];
+                g = cs.g[slot] != 0;
+            } else {
+                rb = __ldg(A.row_ptr + i);
+                rdeg = (int)(__ldg(A.row_ptr + i + 1) - rb);
+                v = __ldcg(A.c + i);
+                g = green_test<T>(sched, v, i, th, mask, A.ideg, ax);
+            }
+            if (g) {
                 const T mtil = moved_per_weight(v, A.s, A.sf, i);
                 A.c[i] = T(0);
                 A.H[i] += (double)v;
@@ -211,18 +255,17 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 mabs += fabs(v);
                 A.mt[i] = mtil;
                 A.f_eoff[k] = e;
-                A.f_base[k] = rb[q] - e;
+                A.f_base[k] = rb - e;
                 A.f_m[k] = mtil;
                 const long long b0 = (e + kPushChunk - 1) / kPushChunk;
-                const long long b1 = (e + rdeg[q] + kPushChunk - 1) / kPushChunk;
+                const long long b1 = (e + rdeg + kPushChunk - 1) / kPushChunk;
                 for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)k;
                 ++k;
-                e += rdeg[q];
+                e += rdeg;
             } else {
                 A.mt[i] = T(0);
             }
         }
-        __syncthreads();  // base_sh is rewritten by the next iteration
     }
     bmsum = (double)block_sum(msum, tscratch);
     bmabs = (double)block_sum(mabs, tscratch);
@@ -232,6 +275,7 @@ template <typename T>
 union SweepSmem {
     PushSmem<T> push;
     PullSmem<T> pull;
+    SelSmem<T> sel;
 };
 
 // The evolving scalars of the solve, one copy per block in shared memory,
@@ -400,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 (sched == SCHED_MASK) ? A.masks + (size_t)(sc.mask_cursor % ctl.n_masks) * (size_t)n : nullptr;
             const SchedAux ax = sched_aux(ctl, n, sc.moves, sc.l1);
             double bmsum, bmabs;
-            sweep_select<T>(A, sched, th, mask, ax, sl, bmsum, bmabs);
+            sweep_select<T>(A, sched, th, mask, ax, sl, sm.sel, bmsum, bmabs);
             if (threadIdx.x == 0) {
                 if (bmsum != 0.0) atomicAdd(&sl->msum, bmsum);
                 if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
