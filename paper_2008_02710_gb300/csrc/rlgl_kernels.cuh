@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
                 if (i >= n) continue;
                 const T v = val[q];
                 c[i] = T(0);
-                H[i] += (double)v;
+                red_add(H + i, (double)v);  // no load: the L2 adds
                 msum += v;
                 mabs += fabs(v);
                 mt[i] = moved_per_weight(v, s, sf, i);
@@ -896,7 +896,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
                 const T v = val[q];
                 const T mtil = moved_per_weight(v, s, sf, i);
                 c[i] = T(0);
-                H[i] += (double)v;
+                red_add(H + i, (double)v);  // no load: the L2 adds
                 if (kBatch && uni < 0) {
                     const int ch = bv.chain_of[i];
                     atomicAdd(&bv.cs[ch].acc[3], (double)v);

@@ -176,7 +176,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 if (i >= n) continue;
                 const T v = __ldcg(A.c + i);
                 A.c[i] = T(0);
-                A.H[i] += (double)v;
+                red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
                 mabs += fabs(v);
                 A.mt[i] = moved_per_weight(v, A.s, A.sf, i);
@@ -250,7 +250,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             if (g) {
                 const T mtil = moved_per_weight(v, A.s, A.sf, i);
                 A.c[i] = T(0);
-                A.H[i] += (double)v;
+                red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
                 mabs += fabs(v);
                 A.mt[i] = mtil;
@@ -309,7 +309,16 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
     __shared__ SweepSmem<T> sm;
     __shared__ T tscratch[32];
     __shared__ SweepCtl sc;
-    const Control& ctl = st->ctl;  // not written while the kernel runs
+    // The solve's parameters, copied once: after every barrier a global read
+    // would go to L2 again (and 600 blocks would queue on the same lines).
+    __shared__ Control ctl;
+    __shared__ double s_l1_refresh;
+    {
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(&st->ctl);
+        unsigned int* dst = reinterpret_cast<unsigned int*>(&ctl);
+        for (int k = threadIdx.x; k < (int)(sizeof(Control) / 4); k += blockDim.x) dst[k] = src[k];
+        if (threadIdx.x == 0) s_l1_refresh = st->l1_refresh;
+    }
     const int n = A.n;
     constexpr bool kF32 = std::is_same<T, float>::value;
     if (threadIdx.x == 0) {
@@ -393,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 stop = ST_TIMEOUT;
             }
             if (stop < 0 && !skip && ctl.mixed && ctl.refresh_factor > 0.0 &&
-                l1 < ctl.refresh_factor * st->l1_refresh)
+                l1 < ctl.refresh_factor * s_l1_refresh)
                 want_refresh = true;  // after this move
             sc.leave = (stop >= 0 || skip) ? 1 : 0;
             sc.want_refresh = want_refresh ? 1 : 0;
