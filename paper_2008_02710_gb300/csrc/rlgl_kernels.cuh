@@ -312,7 +312,7 @@ __device__ __forceinline__ void set_theta(DevState* st, double theta, int sched)
 //             Flood 2014): key_t = mix(seed + (t + 1) g), u_{t,i} =
 //             2^-53 floor(mix(key_t + (i + 1) g) / 2^11).
 struct SchedAux {
-    long long rr_b, rr_cur;
+    long long rr_lo, rr_hi;   // BLOCK_RR: the green block [rr_lo, rr_hi)
     double pc_k, pc_l1;
     unsigned long long pc_key;
 };
@@ -328,9 +328,10 @@ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
 __device__ __forceinline__ SchedAux sched_aux(const Control& c, long long n, long long move, double l1) {
     SchedAux a;
     long long K = c.rr_blocks < 1 ? 1 : (c.rr_blocks > n ? n : c.rr_blocks);
-    a.rr_b = (n + K - 1) / K;
-    const long long nb = (n + a.rr_b - 1) / a.rr_b;
-    a.rr_cur = move % nb;
+    const long long b = (n + K - 1) / K;
+    const long long nb = (n + b - 1) / b;
+    a.rr_lo = (move % nb) * b;
+    a.rr_hi = a.rr_lo + b < n ? a.rr_lo + b : n;
     a.pc_k = c.pc_frac * (double)n;
     a.pc_l1 = l1;
     a.pc_key = sm64_mix(c.seed + (unsigned long long)(move + 1) * kSm64Gamma);
@@ -348,7 +349,7 @@ __device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
         case SCHED_ALL_GREEN: return true;
         case SCHED_MASK: return mask[i] != 0;
         case SCHED_LINK: return (v != T(0)) && (fabs(v) * __ldg(ideg + i) >= th);
-        case SCHED_BLOCK_RR: return i / ax.rr_b == ax.rr_cur;
+        case SCHED_BLOCK_RR: return i >= ax.rr_lo && i < ax.rr_hi;
         case SCHED_PC: {
             if (v == T(0)) return false;
             const double u = (double)(sm64_mix(ax.pc_key + (unsigned long long)(i + 1) * kSm64Gamma) >> 11) *

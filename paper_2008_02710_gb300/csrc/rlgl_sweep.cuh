@@ -137,16 +137,19 @@ struct SweepArgs {
 };
 
 // Shared cache of the select phase: the first kSelCached nodes of a block
-// (two block-iterations) keep their cash, row offset and degree between the
-// counting pass and the writing pass.
+// (two block-iterations) keep their cash, row offset, degree and test
+// result between the counting pass and the writing pass, and every warp's
+// green count and edge sum for each of its node groups there.
 constexpr int kSelCachedIters = 2;
 constexpr int kSelCached = kSelCachedIters * kNodesPerIter;
+constexpr int kSelGroups = kSelCachedIters * kNodesPerThread * (kThreads / 32);
 template <typename T>
 struct SelSmem {
     T val[kSelCached];
     long long rb[kSelCached];
     int rdeg[kSelCached];
     unsigned char g[kSelCached];
+    unsigned long long wsum[kSelGroups];  // packed (edges << kCountBits) | count
 };
 
 // Select on this block's node slices (the single-chain form of k_select):
@@ -154,17 +157,20 @@ struct SelSmem {
 // frontier entries and push-chunk starts; mt holds m~_i (0 for red nodes).
 // Two passes over the block's nodes: the first counts green nodes and their
 // edges, one atomic per block reserves the block's frontier range, the
-// second writes it (from the shared cache for the first two
-// block-iterations, re-reading beyond). Returns the block's sums of m_i and
-// |m_i| in thread 0.
+// second writes it. For the first two block-iterations (cached in shared
+// memory) the frontier slots follow node order within each warp, so a
+// warp's frontier writes are contiguous; beyond, each thread's green nodes
+// take consecutive slots. Returns the block's sums of m_i and |m_i| in
+// thread 0.
 template <typename T>
 __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T th,
                                              const unsigned char* mask, const SchedAux& ax,
                                              SweepSlot* sl, SelSmem<T>& cs, double& bmsum,
                                              double& bmabs) {
     __shared__ T tscratch[32];
-    __shared__ unsigned long long base_sh;
+    __shared__ unsigned long long base_sh, cached_sh;
     const int n = A.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T msum = T(0), mabs = T(0);
     if (sched == SCHED_ALL_GREEN) {
         // every node moves; the pull needs no frontier
@@ -186,7 +192,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         bmabs = (double)block_sum(mabs, tscratch);
         return;
     }
-    // pass 1: count
+    // pass 1: count (per warp and group for the cached nodes, per thread beyond)
     unsigned long long mine = 0ull;
     int j = 0;
     for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
@@ -205,48 +211,94 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
             const bool g = (i < n) && green_test<T>(sched, val[q], i, th, mask, A.ideg, ax);
-            if (g) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+            const unsigned long long pk = g ? ((unsigned long long)rdeg[q] << kCountBits) + 1ull : 0ull;
             if (j < kSelCachedIters) {
                 const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
                 cs.val[slot] = val[q];
                 cs.rb[slot] = rb[q];
                 cs.rdeg[slot] = rdeg[q];
                 cs.g[slot] = g ? 1 : 0;
+                const unsigned long long w = warp_sum(pk);
+                if (lane == 0) cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid] = w;
+            } else {
+                mine += pk;
             }
         }
     }
+    const int ncached = (j < kSelCachedIters ? j : kSelCachedIters) * kNodesPerThread * (kThreads / 32);
+    __syncthreads();
+    // exclusive prefix of the cached groups' counts, in group order (warp 0)
+    if (wid == 0) {
+        unsigned long long run = 0ull;
+        for (int g0 = 0; g0 < ncached; g0 += 32) {
+            const int gi = g0 + lane;
+            const unsigned long long v = gi < ncached ? cs.wsum[gi] : 0ull;
+            unsigned long long x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (gi < ncached) cs.wsum[gi] = run + x - v;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) cached_sh = run;
+    }
     // one reservation for the whole block
     unsigned long long total;
-    const unsigned long long pre = block_exscan(mine, &total);
-    if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
+    const unsigned long long pre = block_exscan(mine, &total);  // synchronises
+    if (threadIdx.x == 0) {
+        const unsigned long long all = total + cached_sh;
+        base_sh = all ? atomicAdd(&sl->reserve, all) : 0ull;
+    }
     __syncthreads();
-    const unsigned long long base = base_sh + pre;
-    long long k = (long long)(base & ((1ull << kCountBits) - 1ull));
-    long long e = (long long)(base >> kCountBits);
+    const unsigned long long base = base_sh;
     // pass 2: write
+    long long k = (long long)((base + cached_sh + pre) & ((1ull << kCountBits) - 1ull));
+    long long e = (long long)((base + cached_sh + pre) >> kCountBits);
     j = 0;
     for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
          it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
+        const bool cached = j < kSelCachedIters;
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
-            if (i >= n) continue;
-            T v;
-            long long rb;
-            int rdeg;
-            bool g;
-            if (j < kSelCachedIters) {
+            T v = T(0);
+            long long rb = 0;
+            int rdeg = 0;
+            bool g = false;
+            long long kk = 0, ee = 0;
+            if (cached) {
                 const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
                 v = cs.val[slot];
                 rb = cs.rb[slot];
                 rdeg = cs.rdeg[slot];
                 g = cs.g[slot] != 0;
-            } else {
+                // slots in node order within the warp
+                const unsigned int bal = __ballot_sync(0xffffffffu, g);
+                long long x = g ? (long long)rdeg : 0ll;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const unsigned long long wb =
+                    base + cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid];
+                kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
+                ee = (long long)(wb >> kCountBits) + x - (g ? (long long)rdeg : 0ll);
+            } else if (i < n) {
                 rb = __ldg(A.row_ptr + i);
                 rdeg = (int)(__ldg(A.row_ptr + i + 1) - rb);
                 v = __ldcg(A.c + i);
                 g = green_test<T>(sched, v, i, th, mask, A.ideg, ax);
+                kk = k;
+                ee = e;
+                if (g) {
+                    ++k;
+                    e += rdeg;
+                }
             }
+            if (i >= n) continue;
             if (g) {
                 const T mtil = moved_per_weight(v, A.s, A.sf, i);
                 A.c[i] = T(0);
@@ -254,14 +306,12 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 msum += v;
                 mabs += fabs(v);
                 A.mt[i] = mtil;
-                A.f_eoff[k] = e;
-                A.f_base[k] = rb - e;
-                A.f_m[k] = mtil;
-                const long long b0 = (e + kPushChunk - 1) / kPushChunk;
-                const long long b1 = (e + rdeg + kPushChunk - 1) / kPushChunk;
-                for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)k;
-                ++k;
-                e += rdeg;
+                A.f_eoff[kk] = ee;
+                A.f_base[kk] = rb - ee;
+                A.f_m[kk] = mtil;
+                const long long b0 = (ee + kPushChunk - 1) / kPushChunk;
+                const long long b1 = (ee + rdeg + kPushChunk - 1) / kPushChunk;
+                for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)kk;
             } else {
                 A.mt[i] = T(0);
             }
@@ -295,6 +345,8 @@ struct SweepCtl {
     int p;             // slot parity
     unsigned int gen;  // barrier generation
     unsigned long long ts[7];  // block 0: move start, then arrival / release at each barrier
+    SchedAux ax;       // this move's block-round-robin range and PC constants
+    long long mask_off;  // MASK: offset of this move's mask
 };
 
 template <typename T, bool kHasW>
@@ -418,6 +470,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             }
             sc.sched = sched;
             sc.theta = theta;
+            sc.ax = sched_aux(ctl, n, sc.moves, l1);
+            sc.mask_off = (sched == SCHED_MASK) ? (sc.mask_cursor % ctl.n_masks) * (long long)n : 0;
             sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
             if (blockIdx.x == 0) {
                 st->l1 = l1;
@@ -449,9 +503,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         {
             const int sched = sc.sched;
             const T th = kF32 ? (T)sc.theta_f : (T)sc.theta;
-            const unsigned char* mask =
-                (sched == SCHED_MASK) ? A.masks + (size_t)(sc.mask_cursor % ctl.n_masks) * (size_t)n : nullptr;
-            const SchedAux ax = sched_aux(ctl, n, sc.moves, sc.l1);
+            const unsigned char* mask = (sched == SCHED_MASK) ? A.masks + sc.mask_off : nullptr;
+            const SchedAux& ax = sc.ax;
             double bmsum, bmabs;
             sweep_select<T>(A, sched, th, mask, ax, sl, sm.sel, bmsum, bmabs);
             if (threadIdx.x == 0) {

@@ -380,9 +380,16 @@ def test_resume_from_state_continues_identically(medium):
             assert b.invariant_residual() <= 1e-15
             cb, hb = b.get_state()
             assert np.array_equal(cb, c) and np.array_equal(hb, h)
+            # the same moves from the same state: equal up to the order of
+            # the FP64 atomic additions
+            a.solve("threshold", tol=0.0, max_steps=200, raise_on_noconv=False)
+            b.solve("threshold", tol=0.0, max_steps=200, raise_on_noconv=False)
+            assert np.abs(a.estimate() - b.estimate()).sum() <= 1e-13
+            # to the tolerance: the stop test may fire a move apart, and two
+            # estimates that both meet tol 1e-12 differ by O(tol)
             ia = a.solve("threshold", tol=1e-12, max_steps=100000)
             ib = b.solve("threshold", tol=1e-12, max_steps=100000)
-            assert np.abs(a.estimate() - b.estimate()).sum() <= FP64_PI_TOL
+            assert np.abs(a.estimate() - b.estimate()).sum() <= 1e-11
     assert abs(ia["moves"] - ib["moves"]) <= 1
 
 
