@@ -32,7 +32,7 @@ namespace rlgl {
 constexpr int kThreads = 256;         // threads per block, every kernel
 constexpr int kNodesPerThread = 4;    // node kernels: nodes per thread per block-iteration
 constexpr int kNodesPerIter = kThreads * kNodesPerThread;
-constexpr int kPushChunk = 2048;      // edges per push chunk
+constexpr int kPushChunk = 1024;      // edges per push chunk
 constexpr int kMpIpt = 8;             // merge-path items per thread
 constexpr int kMpItems = kThreads * kMpIpt;  // merge-path items (rows + edges) per tile
 constexpr int kCountBits = 27;        // frontier reservation: (edges << 27) | count
