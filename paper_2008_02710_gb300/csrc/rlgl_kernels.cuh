@@ -325,30 +325,36 @@ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ SchedAux sched_aux(const Control& c, long long n, long long move, double l1) {
+__device__ __forceinline__ SchedAux sched_aux(const Control& c, long long n, long long move, double l1,
+                                              int sched) {
     SchedAux a;
-    long long K = c.rr_blocks < 1 ? 1 : (c.rr_blocks > n ? n : c.rr_blocks);
-    const long long b = (n + K - 1) / K;
-    const long long nb = (n + b - 1) / b;
-    a.rr_lo = (move % nb) * b;
-    a.rr_hi = a.rr_lo + b < n ? a.rr_lo + b : n;
-    a.pc_k = c.pc_frac * (double)n;
-    a.pc_l1 = l1;
-    a.pc_key = sm64_mix(c.seed + (unsigned long long)(move + 1) * kSm64Gamma);
+    a.rr_lo = a.rr_hi = 0;
+    a.pc_k = a.pc_l1 = 0.0;
+    a.pc_key = 0ull;
+    if (sched == SCHED_BLOCK_RR) {
+        long long K = c.rr_blocks < 1 ? 1 : (c.rr_blocks > n ? n : c.rr_blocks);
+        const long long b = (n + K - 1) / K;
+        const long long nb = (n + b - 1) / b;
+        a.rr_lo = (move % nb) * b;
+        a.rr_hi = a.rr_lo + b < n ? a.rr_lo + b : n;
+    } else if (sched == SCHED_PC) {
+        a.pc_k = c.pc_frac * (double)n;
+        a.pc_l1 = l1;
+        a.pc_key = sm64_mix(c.seed + (unsigned long long)(move + 1) * kSm64Gamma);
+    }
     return a;
 }
 
-// Whether node i (cash v) is green under `sched` (ALL_GREEN, THRESHOLD,
-// LINK_THRESHOLD, MASK, BLOCK_RR, PC; TOPFRAC uses THRESHOLD's test with its
-// radix-selected theta).
+// Whether node i (cash v, 1/out-degree idg) is green under `sched`
+// (ALL_GREEN, THRESHOLD, LINK_THRESHOLD, MASK, BLOCK_RR, PC; TOPFRAC uses
+// THRESHOLD's test with its radix-selected theta).
 template <typename T>
-__device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
-                                           const unsigned char* mask, const T* __restrict__ ideg,
-                                           const SchedAux& ax) {
+__device__ __forceinline__ bool green_test_v(int sched, T v, T idg, long long i, T th,
+                                             const unsigned char* mask, const SchedAux& ax) {
     switch (sched) {
         case SCHED_ALL_GREEN: return true;
         case SCHED_MASK: return mask[i] != 0;
-        case SCHED_LINK: return (v != T(0)) && (fabs(v) * __ldg(ideg + i) >= th);
+        case SCHED_LINK: return (v != T(0)) && (fabs(v) * idg >= th);
         case SCHED_BLOCK_RR: return i >= ax.rr_lo && i < ax.rr_hi;
         case SCHED_PC: {
             if (v == T(0)) return false;
@@ -358,6 +364,14 @@ __device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
         }
         default: return (v != T(0)) && (fabs(v) >= th);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
+                                           const unsigned char* mask, const T* __restrict__ ideg,
+                                           const SchedAux& ax) {
+    const T idg = (sched == SCHED_LINK) ? __ldg(ideg + i) : T(0);
+    return green_test_v<T>(sched, v, idg, i, th, mask, ax);
 }
 
 // Decides, after the cash statistics of C_t are known, whether the solve
@@ -813,7 +827,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
     const T theta = std::is_same<T, float>::value ? (T)st->theta_f : (T)st->theta;
     const unsigned char* mask = nullptr;
     if (sched == SCHED_MASK) mask = masks + (size_t)(st->mask_cursor % ctl.n_masks) * (size_t)n;
-    const SchedAux ax = sched_aux(ctl, n, st->moves, st->l1);
+    const SchedAux ax = sched_aux(ctl, n, st->moves, st->l1, sched);
 
     __shared__ double scratch[32];
     __shared__ T tscratch[32];
@@ -1024,8 +1038,11 @@ struct PushSmem {
     int wmax[kThreads / 32];
 };
 
-// The chunks b = first, first + step, ... of a push over E frontier edges of
-// K frontier rows (see k_push).
+// The chunks of a push over E frontier edges of K frontier rows (see
+// k_push): b = first, first + step, ..., or, when `next` is given, chunks
+// handed out one at a time by that counter (thread 0 asks for the next one
+// while the block works on the current one), so that blocks that meet slow
+// atomics take fewer chunks.
 template <typename T, bool kHasW, bool kCg>
 __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __restrict__ col,
                                             const float* __restrict__ w,
@@ -1034,11 +1051,21 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                                             const T* __restrict__ f_m,
                                             const int* __restrict__ chunk_row, long long E,
                                             long long K, long long first, long long step,
-                                            PushSmem<T>& sm) {
-    constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread (8)
+                                            PushSmem<T>& sm,
+                                            unsigned long long* next = nullptr) {
+    constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long b = first; b < nchunks; b += step) {
+    __shared__ long long s_next;
+    long long b = first;
+    if (next) {
+        if (threadIdx.x == 0) s_next = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        b = s_next;
+        __syncthreads();
+    }
+    while (b < nchunks) {
+        if (next && threadIdx.x == 0) s_next = (long long)atomicAdd(next, 1ull);  // read below
         const long long e0 = b * kPushChunk;
         const int ne = (int)min((long long)kPushChunk, E - e0);
         const long long k0 = ld_shared_data<kCg>(chunk_row + b);
@@ -1090,6 +1117,12 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             }
         }
         __syncthreads();
+        if (next) {
+            b = s_next;
+            __syncthreads();  // everyone has read s_next before thread 0 rewrites it
+        } else {
+            b += step;
+        }
     }
 }
 

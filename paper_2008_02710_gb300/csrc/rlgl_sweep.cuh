@@ -37,14 +37,13 @@ struct SweepSlot {
     double msum, mabs;           // sum m_i, sum |m_i| of the moved cash
     unsigned long long reserve;  // packed frontier reservation
     unsigned long long tstamp;   // block 0's timer at the end of its stats
-    unsigned long long pad;
+    unsigned long long chunk_next;  // next push chunk to hand out
 };
 
 struct GridBar {
-    unsigned int count;  // blocks arrived at the current barrier
-    unsigned int gen;    // barriers completed
-    unsigned int abort;  // a wait gave up: every block leaves
-    unsigned int parity; // slot of the next move (kept across launches)
+    unsigned long long arrived;  // arrivals since the solve began (grid size per barrier)
+    unsigned int abort;          // a wait gave up: every block leaves
+    unsigned int parity;         // slot of the next move (kept across launches)
 };
 
 struct SweepState {
@@ -57,31 +56,36 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
-// Grid-wide barrier of a cooperative launch. Thread 0 of each block
-// arrives; the last one to arrive resets the count and publishes the next
-// generation; the others wait for it, at most limit_ns. Returns false (in
-// every thread of the block) when the sweep must stop. When ts is given,
-// thread 0 stores its arrival and release times in ts[0], ts[1].
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen,
+// Grid-wide barrier of a cooperative launch. Thread 0 of each block makes
+// the block's writes visible (fence), adds one to the arrival count (no
+// value returned) and waits until the count reaches `target`, the number of
+// arrivals once every block has reached this barrier: the count only grows,
+// so no block has to reset or release anything. The wait is bounded by
+// limit_ns. Returns false (in every thread of the block) when the sweep must
+// stop. When ts is given, thread 0 stores its arrival and release times in
+// ts[0], ts[1].
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned long long& target,
                                              unsigned long long limit_ns,
                                              unsigned long long* ts = nullptr) {
-    // gen: the block's barrier count (shared memory; thread 0 keeps it)
+    // target: the block's expected arrival count (shared memory; thread 0 keeps it)
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         if (ts) ts[0] = globaltimer();
         int ok = 1;
-        const unsigned int target = gen + 1u;
+        target += gridDim.x;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicExch(&bar->gen, target);
-        } else {
-            const unsigned long long t0 = globaltimer();
-            while (ld_acquire_u32(&bar->gen) != target) {
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(&bar->arrived) : "memory");
+        const unsigned long long t0 = globaltimer();
+        unsigned int spins = 0;
+        while (ld_acquire_u64(&bar->arrived) < target) {
+            if ((++spins & 15u) == 0u) {
                 if (ld_acquire_u32(&bar->abort)) {
                     ok = 0;
                     break;
@@ -91,13 +95,10 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned int& gen,
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
+            __nanosleep(32);
         }
-        if (ld_acquire_u32(&bar->abort)) ok = 0;
-        __threadfence();
         s_ok = ok;
-        gen = target;
         if (ts) ts[1] = globaltimer();
     }
     __syncthreads();
@@ -199,18 +200,20 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
          it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
         long long rb[kNodesPerThread];
         int rdeg[kNodesPerThread];
-        T val[kNodesPerThread];
+        T val[kNodesPerThread], idg[kNodesPerThread];
+        // every load of the group issued before any is used
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
             rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
             rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
             val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
+            idg[q] = (i < n && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
         }
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
-            const bool g = (i < n) && green_test<T>(sched, val[q], i, th, mask, A.ideg, ax);
+            const bool g = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
             const unsigned long long pk = g ? ((unsigned long long)rdeg[q] << kCountBits) + 1ull : 0ull;
             if (j < kSelCachedIters) {
                 const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
@@ -343,7 +346,7 @@ struct SweepCtl {
     int leave;         // 1: return now (stop, or re-derive before testing again)
     int want_refresh;  // return after this move for a re-derivation
     int p;             // slot parity
-    unsigned int gen;  // barrier generation
+    unsigned long long target;  // expected arrival count at the next barrier
     unsigned long long ts[7];  // block 0: move start, then arrival / release at each barrier
     SchedAux ax;       // this move's block-round-robin range and PC constants
     long long mask_off;  // MASK: offset of this move's mask
@@ -386,7 +389,11 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         sc.habs = st->habs;
         sc.t_start = st->t_start;
         sc.fresh = st->fresh;
-        sc.gen = ld_acquire_u32(&sw->bar.gen);
+        // Every barrier adds exactly the grid size, and no barrier can
+        // complete before this block arrives: rounding down what has arrived
+        // gives the count at the start of this launch.
+        const unsigned long long arr = ld_acquire_u64(&sw->bar.arrived);
+        sc.target = arr - arr % gridDim.x;
         sc.p = (int)(sw->bar.parity & 1u);
     }
     __syncthreads();
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (blockIdx.x == 0) sl->tstamp = globaltimer();
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr)) break;
+        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr)) break;
 
         // -------------------------------------------------------- control
         if (threadIdx.x == 0) {
@@ -426,6 +433,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 o->msum = 0.0;
                 o->mabs = 0.0;
                 o->reserve = 0ull;
+                o->chunk_next = 0ull;
             }
             const int r = ctl.r;
             const bool link = ctl.sched == SCHED_LINK;
@@ -470,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             }
             sc.sched = sched;
             sc.theta = theta;
-            sc.ax = sched_aux(ctl, n, sc.moves, l1);
+            sc.ax = sched_aux(ctl, n, sc.moves, l1, sched);
             sc.mask_off = (sched == SCHED_MASK) ? (sc.mask_cursor % ctl.n_masks) * (long long)n : 0;
             sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
             if (blockIdx.x == 0) {
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
             }
         }
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr)) break;
+        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr)) break;
 
         // ---------------------------------------------------- choose move
         if (threadIdx.x == 0) {
@@ -581,11 +589,12 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         // ----------------------------------------------------------- move
         if (sc.mode == MODE_PUSH)
             push_chunks<T, kHasW, true>(A.c, A.col, A.w, A.f_eoff, A.f_base, A.f_m, A.chunk_row,
-                                        sc.edges, sc.green, blockIdx.x, gridDim.x, sm.push);
+                                        sc.edges, sc.green, blockIdx.x, gridDim.x, sm.push,
+                                        &sl->chunk_next);
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull);
-        if (!grid_barrier(&sw->bar, sc.gen, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr)) break;
+        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr)) break;
         if (lead) {
             MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
             rec->phase_us[4] = (float)(sc.ts[5] - sc.ts[4]) * 1e-3f;
