@@ -67,6 +67,7 @@ struct rlgl_ctx {
     double* y = nullptr;     // residual accumulator, all-zero at rest
     double* hsrc = nullptr;  // H_i s_i for residual pulls
     double* c0 = nullptr;    // recorded C_0 (rlgl_create_from_state), else null
+    double* colsum = nullptr;  // (1 P)_j in FP64: step 0 from the uniform M_0
     long long* f_eoff = nullptr;
     long long* f_base = nullptr;
     void* f_m = nullptr;
@@ -603,27 +604,34 @@ static rlgl_status device_inclusive_scan(rlgl_ctx* ctx, long long* x, long long 
     return RLGL_OK;
 }
 
+// Step 0 (Eq. init): H = M_0, C_1 = M_0 (P - I). The uniform M_0 (NULL; per
+// chain in a batch) is set on the device from the precomputed column sums;
+// a given M_0 goes through the FP64 re-derivation C = C_0 + H (P - I) with
+// C_0 = 0.
 static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) {
     const long long n = ctx->n;
-    if (m0) {
-        TRY(upload(ctx, ctx->H, m0, (size_t)n * sizeof(double), sp));
-    } else {
-        std::vector<double> u((size_t)n, 1.0 / (double)n);
-        CK(ctx, cudaMemcpyAsync(ctx->H, u.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
-                                ctx->stream));
-        CK(ctx, cudaStreamSynchronize(ctx->stream));
-    }
-    // C = 0 then C = C_0 + H (P - I) with H = M_0 and no recorded C_0: the
-    // result of step 0, C_1 = -M_0 (I - P).
     if (ctx->c0) {
         CK(ctx, cudaStreamSynchronize(ctx->stream));
         dfree(ctx, ctx->c0);
         ctx->c0 = nullptr;
         drop_graphs(ctx);  // captured launches hold the C_0 pointer
     }
-    CK(ctx, cudaMemsetAsync(ctx->c, 0, (size_t)n * cash_size(ctx), ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream));
-    TRY(forced_refresh(ctx, true));
+    if (m0) {
+        TRY(upload(ctx, ctx->H, m0, (size_t)n * sizeof(double), sp));
+        CK(ctx, cudaMemsetAsync(ctx->c, 0, (size_t)n * cash_size(ctx), ctx->stream));
+        TRY(forced_refresh(ctx, true));
+    } else {
+        const int* chain_of = ctx->nchains > 1 ? ctx->chain_of : nullptr;
+        const long long* node_ptr = ctx->nchains > 1 ? ctx->node_ptr : nullptr;
+        if (ctx->prec == RLGL_MIXED)
+            k_step0_uniform<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+                (float*)ctx->c, ctx->H, ctx->colsum, (int)n, chain_of, node_ptr, ctx->st, ctx->part);
+        else
+            k_step0_uniform<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
+                (double*)ctx->c, ctx->H, ctx->colsum, (int)n, chain_of, node_ptr, ctx->st, ctx->part);
+        CKL(ctx);
+    }
     k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
     CKL(ctx);
     if (ctx->nchains > 1) {
@@ -634,7 +642,6 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
         k_bhist_finish<<<grid_for(ctx->nchains, kThreads, 1024), kThreads, 0, ctx->stream>>>(bv, 1, nullptr);
         CKL(ctx);
     }
-    TRY(read_state(ctx));
     return RLGL_OK;
 }
 
@@ -695,6 +702,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc_bytes(ctx, &ctx->mt, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->y, (size_t)n));
     TRY(dalloc(ctx, &ctx->hsrc, (size_t)n));
+    TRY(dalloc(ctx, &ctx->colsum, (size_t)n));
     TRY(dalloc(ctx, &ctx->f_eoff, (size_t)n));
     TRY(dalloc(ctx, &ctx->f_base, (size_t)n));
     TRY(dalloc_bytes(ctx, &ctx->f_m, (size_t)n * cs));
@@ -751,6 +759,8 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
                                                       ctx->tile_e);
     CKL(ctx);
+    k_colsum<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->s, n, ctx->colsum);
+    CKL(ctx);
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     dfree(ctx, cursor);
     return RLGL_OK;
@@ -763,9 +773,9 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->theta_scale = 1.0;
     p->r = 1;
     p->top_frac = 0.01;
-    p->pull_crossover = 0.25;
+    p->pull_crossover = 0.9;
     p->safety_every = 0;
-    p->refresh_factor = 1e-3;
+    p->refresh_factor = 1e-4;
     p->time_limit_s = 600.0;
     p->rr_blocks = 8;
     p->pc_frac = 0.05;
@@ -884,11 +894,9 @@ rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t
     if ((s = dalloc(ctx, &ctx->bsums, 2 * (size_t)n_chains)) != RLGL_OK) return bail(s);
     std::vector<ChainState> cs((size_t)n_chains);
     memset(cs.data(), 0, cs.size() * sizeof(ChainState));
-    std::vector<double> m0((size_t)n);
     for (int64_t k = 0; k < n_chains; ++k) {
         cs[(size_t)k].n = np[(size_t)k + 1] - np[(size_t)k];
         cs[(size_t)k].tol = 1e-12;
-        for (int64_t i = np[(size_t)k]; i < np[(size_t)k + 1]; ++i) m0[(size_t)i] = 1.0 / (double)cs[(size_t)k].n;
     }
     if (cudaMemcpyAsync(ctx->node_ptr, np.data(), np.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                         ctx->stream) != cudaSuccess ||
@@ -907,7 +915,7 @@ rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t
         cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return bail(fail(ctx, RLGL_ECUDA, "chain map failed"));
     if (err) return bail(fail(ctx, RLGL_EINVAL, "an edge leaves its chain: the CSR must be block-diagonal"));
-    if ((s = set_step0(ctx, m0.data(), RLGL_HOST)) != RLGL_OK) return bail(s);
+    if ((s = set_step0(ctx, nullptr, RLGL_HOST)) != RLGL_OK) return bail(s);  // uniform per chain
     *out = ctx;
     return RLGL_OK;
 }
@@ -945,16 +953,7 @@ rlgl_status rlgl_batch_chains(rlgl_ctx* ctx, int32_t* status, int64_t* moves, do
 rlgl_status rlgl_reset(rlgl_ctx* ctx, const double* m0, rlgl_memspace src) {
     if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
     NOT_PENDING(ctx);
-    if (!m0 && ctx->nchains > 1) {
-        // uniform within each chain
-        std::vector<double> u((size_t)ctx->n);
-        for (int k = 0; k < ctx->nchains; ++k) {
-            const int64_t a = ctx->node_ptr_h[(size_t)k], b = ctx->node_ptr_h[(size_t)k + 1];
-            for (int64_t i = a; i < b; ++i) u[(size_t)i] = 1.0 / (double)(b - a);
-        }
-        return set_step0(ctx, u.data(), RLGL_HOST);
-    }
-    return set_step0(ctx, m0, src);
+    return set_step0(ctx, m0, src);  // NULL: uniform (within each chain of a batch)
 }
 
 rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period, rlgl_memspace src) {
@@ -1489,7 +1488,7 @@ int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision 
     b += 2 * ((n + 1) * 8 + nnz * 4 + (weighted ? nnz * 4 : 0));  // CSR and CSC
     b += n * (8 + (prec == RLGL_MIXED ? 4 : 0) + cs);                // s, sf, 1/deg
     b += 2 * (ntiles + 1) * 8;                                       // merge-path tiles
-    b += n * (cs + 8 + cs + 8 + 8 + 8 + 8 + cs);                     // c H mt y hsrc f_eoff f_base f_m
+    b += n * (cs + 8 + cs + 8 + 8 + 8 + 8 + cs + 8);                 // c H mt y hsrc f_eoff f_base f_m colsum
     b += (nnz / kPushChunk + 2) * 4;                                 // chunk index
     b += (4 * kMaxGrid + 8) * 8 + 8 + (int64_t)kLogCap * (int64_t)sizeof(MoveRecord) +
          (int64_t)sizeof(DevState) + (int64_t)sizeof(SweepState);
@@ -1527,6 +1526,7 @@ void rlgl_destroy(rlgl_ctx* ctx) {
     }
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
+                   ctx->colsum,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
                    ctx->err, ctx->log, ctx->st, ctx->sw, ctx->node_ptr, ctx->chain_of, ctx->cs,
                    ctx->bsums};

@@ -1404,6 +1404,60 @@ __global__ void __launch_bounds__(kThreads) k_hist_sums(const double* __restrict
     }
 }
 
+// colsum_j = sum over in-links (i, j) of s_i w_ij = (1 P)_j, in FP64; one
+// warp per row of the CSC. Computed once per chain: step 0 from the uniform
+// M_0 then needs no pass over the edges.
+__global__ void k_colsum(const long long* __restrict__ t_ptr, const int* __restrict__ t_src,
+                         const float* __restrict__ t_w, const double* __restrict__ s, long long n,
+                         double* __restrict__ colsum) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long j = warp; j < n; j += nwarps) {
+        double acc = 0.0;
+        for (long long e = t_ptr[j] + lane; e < t_ptr[j + 1]; e += 32)
+            acc += s[t_src[e]] * (t_w ? (double)t_w[e] : 1.0);
+        acc = warp_sum(acc);
+        if (lane == 0) colsum[j] = acc;
+    }
+}
+
+// Step 0 from the uniform M_0 (Eq. init): H = M_0 = 1/N (1/N_k within chain
+// k of a batch) and C_1 = M_0 (P - I), i.e. C_j = (colsum_j - 1) / N, in FP64
+// and then rounded to the cash type; ||C_1||_1 of the stored cash goes to
+// l1_refresh (the cash is exact: a fresh state).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_step0_uniform(T* __restrict__ c, double* __restrict__ H,
+                                                            const double* __restrict__ colsum, int n,
+                                                            const int* __restrict__ chain_of,
+                                                            const long long* __restrict__ node_ptr,
+                                                            DevState* st, double* part) {
+    __shared__ double scratch[32];
+    double a = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double inv = inv_n;
+        if (chain_of) {
+            const int k = chain_of[i];
+            inv = 1.0 / (double)(node_ptr[k + 1] - node_ptr[k]);
+        }
+        H[i] = inv;
+        const T v = (T)(colsum[i] * inv - inv);
+        c[i] = v;
+        a += fabs((double)v);
+    }
+    a = block_sum(a, scratch);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (!last_block(&st->ticket)) return;
+    double tot[1];
+    reduce_partials<1>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+        st->l1_refresh = tot[0];
+        st->resid_l1 = 0.0;
+        st->fresh = 1;
+    }
+}
+
 // Batch: per chain sum H and sum |H| into acc[5], acc[6] (zero at rest).
 __global__ void __launch_bounds__(kThreads) k_bhist_sums(const double* __restrict__ H, int n,
                                                          BatchView bv) {
