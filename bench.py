@@ -330,7 +330,10 @@ class GpuRun:
         names = ("stats", "stats_wait", "select", "select_wait", "move", "move_wait")
         ph = np.array([r["phase_us"] for r in log], dtype=np.float64)
         phases = {k: float(v) for k, v in zip(names, ph.mean(axis=0))} if len(ph) else {}
-        return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull")), phases
+        # edges pushed per second of push phase (work + wait at its barrier)
+        push = [(r["edges_pushed"], r["phase_us"][4] + r["phase_us"][5]) for r in log if r["mode"] == 1]
+        push_rate = (sum(e for e, _ in push) / (sum(t for _, t in push) * 1e-6) / 1e9) if push else None
+        return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull")), phases, push_rate
 
     def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0):
         """Through the public API with host buffers: every step uploads the
@@ -381,10 +384,23 @@ def traffic_from_profiles(kernel_cls, workload):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("rlgl.cu", "rlgl_kernels.cuh"):
+    for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh"):
         with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def random_access_peaks(n_words, m=1 << 22):
+    """Scatter (red.global.add.f32) and gather rates, G ops/s, of m random
+    4-byte accesses into n_words words on this GPU (libl2probe.so): the
+    ceiling of the push and the pull when the chain sits in L2."""
+    import ctypes
+    from paper_2008_02710_gb300 import _build
+    lib = ctypes.CDLL(_build.build_probe())
+    lib.l2_probe_rate.restype = ctypes.c_double
+    lib.l2_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
+    grid = 8 * 152
+    return lib.l2_probe_rate(0, n_words, m, grid, 5), lib.l2_probe_rate(1, n_words, m, grid, 5)
 
 
 def measured_peaks():
@@ -446,9 +462,10 @@ def run_gpu(args):
     nvtx.range_pop()
     g.chain.set_params(persistent=args.persistent)
     sweep_on = args.persistent == 1 and head != "topfrac"
+    push_rate = None
     if sweep_on:
         nvtx.range_push("profile_sweep")
-        (ms_sw, n_sw), bytes_sw, sweep_phases = g.sweep_profile(sched_h, theta_h, tstar, alg)
+        (ms_sw, n_sw), bytes_sw, sweep_phases, push_rate = g.sweep_profile(sched_h, theta_h, tstar, alg)
         nvtx.range_pop()
     # the headline schedule on the one-kernel-per-phase path, for comparison
     phase_ms = None
@@ -514,6 +531,7 @@ def run_gpu(args):
         bytes_dom = alg[dom]
     peak, peak_src = measured_peaks()
     achieved = bytes_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
+    scat_peak, gath_peak = random_access_peaks(csr.n)
     refreshes = infos[0]["refreshes"]
     if sweep_on:
         # reset (5), begin (1), sweep launches (1 + one per re-derivation),
@@ -551,6 +569,10 @@ def run_gpu(args):
                      "traffic": traffic_from_profiles(dom, args.workload),
                      "launches": n_dom, "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
                      "alg_bytes_per_launch": bytes_dom / max(n_dom, 1)},
+        "random_access": {"scatter_peak_gops": scat_peak, "gather_peak_gops": gath_peak,
+                          "probe": f"4M random 4-byte accesses into {csr.n} words, 1216 blocks",
+                          "push_phase_gops": push_rate if sweep_on else None,
+                          "push_frac_of_scatter_peak": (push_rate / scat_peak) if (sweep_on and push_rate and scat_peak > 0) else None},
         "phase_kernel_ms": {k: v[0] for k, v in kt.items() if k != "sweep"},
         "phase_kernel_launches": {k: v[1] for k, v in kt.items() if k != "sweep"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
