@@ -449,7 +449,9 @@ def run_gpu(args):
         cal[name] = dict(tstar=tstar, err=e, traj=traj)
     nvtx.range_pop()
     if cal[head]["tstar"] is None:
-        raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves")
+        tr = cal[head]["traj"]
+        raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves; "
+                         f"(move, L1) along the way: {tr[:4] + tr[4::max(1, len(tr) // 12)]}")
     tstar = cal[head]["tstar"]
 
     # kernel profile of the headline schedule (CUDA events on the context
