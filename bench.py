@@ -247,19 +247,37 @@ class GpuRun:
         return float(e.item())
 
     def calibrate(self, sched, theta, ref_dev, max_moves=20000):
-        """Untimed: the first move count T* with L1 error <= 1e-6."""
+        """Untimed: the least move count T* whose solve (the timed path: step
+        0, then T* moves as one device-loop solve with its re-derivations,
+        then the estimate) has L1 error <= 1e-6 against the reference. Doubles
+        T until the error is met, then bisects; returns (T*, error, the
+        (moves, error) pairs tried)."""
         ch = self.chain
-        ch.reset(self.m0)
         traj = []
-        for k in range(1, max_moves + 1):
-            ch.step(sched, theta, info=False)
+
+        def err_at(k):
+            ch.reset(self.m0)
+            ch.solve(sched, theta, tol=0.0, max_steps=k, raise_on_noconv=False)
             e = self.err(ref_dev)
-            if k <= 3 or k % 25 == 0:
-                traj.append((k, e))
+            traj.append((k, e))
+            return e
+
+        lo, hi = 0, 8
+        e = err_at(hi)
+        while e > ERR_TARGET:
+            if hi >= max_moves:
+                return None, e, sorted(traj)
+            lo, hi = hi, min(2 * hi, max_moves)
+            e = err_at(hi)
+        e_hi = e
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            e = err_at(mid)
             if e <= ERR_TARGET:
-                traj.append((k, e))
-                return k, e, traj
-        return None, e, traj
+                hi, e_hi = mid, e
+            else:
+                lo = mid
+        return hi, e_hi, sorted(traj)
 
     def flush_l2(self):
         with self.torch.cuda.stream(self.stream):

@@ -91,8 +91,8 @@ typedef enum {
  * MIXED: cash and per-edge products in FP32, history and every reduction in
  * FP64; the cash is re-derived in FP64 from the history, C = C_0 + H (P - I)
  * (Eq. recursion_H_res), whenever ||C||_1 has fallen by params.refresh_factor
- * since the last re-derivation and always before a solve reports
- * convergence. */
+ * since the last re-derivation, when it has stopped falling (params.stall_moves),
+ * and always before a solve reports convergence. */
 typedef enum { RLGL_FP64 = 0, RLGL_MIXED = 1 } rlgl_precision;
 
 typedef enum { RLGL_HOST = 0, RLGL_DEVICE = 1 } rlgl_memspace;
@@ -105,7 +105,7 @@ typedef struct {
                                the in-links instead of pushing (default 0.9: on GB300 a pull
                                over all in-links costs about as much as pushing every edge) */
     int32_t safety_every;   /* every K-th move of a solve is all-green (0 = never, default) */
-    double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-4; 0 = only at the end) */
+    double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-3; 0 = only at the end) */
     double time_limit_s;    /* wall-clock limit of one rlgl_solve, checked on the device (default 600) */
     int64_t rr_blocks;      /* BLOCK_RR: number of blocks K (default 8) */
     double pc_frac;         /* PC: expected green fraction k / N before capping (default 0.05) */
@@ -120,6 +120,9 @@ typedef struct {
     int32_t test_skip_barrier; /* testing only (default 0): 1 makes one block of the sweep
                                   leave before its first barrier, so that the others' wait
                                   runs out (exercises the bounded wait without a fault) */
+    int32_t stall_moves;    /* MIXED only: re-derive the cash also when ||C||_1 has not fallen
+                               below its value of this many moves ago (FP32 rounding floor, e.g.
+                               in a node with a million in-links); 0 = off (default 32) */
 } rlgl_params;
 
 typedef struct {

@@ -528,6 +528,7 @@ static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, dou
     c->seed = ctx->params.seed;
     c->barrier_limit_ns = (unsigned long long)(ctx->params.barrier_limit_s * 1e9);
     c->test_skip_barrier = ctx->params.test_skip_barrier;
+    c->stall_moves = ctx->params.stall_moves;
     c->sched = sched;
     c->r = ctx->params.r;
     c->safety_every = solving ? ctx->params.safety_every : 0;
@@ -553,6 +554,8 @@ __global__ void k_begin(DevState* st) {
     st->apply_refresh = 0;
     st->green = 0;
     st->edges = 0;
+    st->stall_mark = kNoMark;
+    st->stall_count = 0;
 }
 
 static rlgl_status begin(rlgl_ctx* ctx, int sched, double theta, double tol, long long max_steps,
@@ -775,7 +778,7 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->top_frac = 0.01;
     p->pull_crossover = 0.9;
     p->safety_every = 0;
-    p->refresh_factor = 1e-4;
+    p->refresh_factor = 1e-3;
     p->time_limit_s = 600.0;
     p->rr_blocks = 8;
     p->pc_frac = 0.05;
@@ -783,6 +786,7 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->persistent = 1;
     p->barrier_limit_s = 2.0;
     p->test_skip_barrier = 0;
+    p->stall_moves = 32;
     return RLGL_OK;
 }
 
@@ -1344,7 +1348,7 @@ rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
         !(p->pull_crossover >= 0.0) || p->safety_every < 0 || !(p->refresh_factor >= 0.0 && p->refresh_factor < 1.0) ||
         !(p->time_limit_s > 0.0) || (p->persistent != 0 && p->persistent != 1) || p->rr_blocks < 1 ||
         !(p->pc_frac > 0.0 && p->pc_frac <= 1e30) || !(p->barrier_limit_s > 0.0 && p->barrier_limit_s <= 60.0) ||
-        (p->test_skip_barrier != 0 && p->test_skip_barrier != 1))
+        (p->test_skip_barrier != 0 && p->test_skip_barrier != 1) || p->stall_moves < 0)
         return fail(ctx, RLGL_EINVAL, "parameter out of range");
     ctx->params = *p;
     return RLGL_OK;

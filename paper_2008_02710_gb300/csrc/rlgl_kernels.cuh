@@ -94,7 +94,7 @@ struct Control {
     unsigned long long seed; // PC: generator seed
     unsigned long long barrier_limit_ns;  // persistent sweep: longest barrier wait
     int test_skip_barrier;   // persistent sweep: one block leaves before its first barrier
-    int pad2;
+    int stall_moves;         // MIXED: re-derive when ||C||_1 has not fallen in this many moves
     int sched;
     int r;
     int safety_every;
@@ -112,6 +112,8 @@ struct DevState {
     float pad_f;
     double hsum, habs;       // H 1 (kept incrementally) and an upper bound of sum |H|
     double l1_refresh;       // ||C||_1 right after the last re-derivation
+    double stall_mark;       // ||C||_1 at the start of the current stall window (MIXED)
+    long long stall_count;   // moves in the current stall window
     double resid_l1;         // residual measured by the last refresh pass
     double last_mabs;
     // last move and totals
@@ -374,6 +376,22 @@ __device__ __forceinline__ bool green_test(int sched, T v, long long i, T th,
     return green_test_v<T>(sched, v, idg, i, th, mask, ax);
 }
 
+constexpr double kNoMark = 1e300;
+
+// MIXED path: FP32 rounding of the cash (above all in nodes that receive
+// very many additions, like the auxiliary node of a PageRank chain) leaves
+// a floor under ||C||_1 that the re-derivation trigger may never reach.
+// True when ||C||_1 has not gone below its value of stall_moves moves ago;
+// advances the window.
+__device__ __forceinline__ bool cash_stalled(double l1, double& mark, long long& count, int stall_moves) {
+    if (stall_moves <= 0) return false;
+    if (++count < stall_moves) return false;
+    const bool stalled = l1 >= mark;
+    mark = l1;
+    count = 0;
+    return stalled;
+}
+
 // Decides, after the cash statistics of C_t are known, whether the solve
 // stops (Alg. 1 line (7): t >= 2 and ||C_t||_1 / |H_t 1| < tol) and sets the
 // threshold for this move. Runs in one thread.
@@ -414,7 +432,8 @@ __device__ void control_after_stats(DevState* st, unsigned long long cond_handle
             }
             return;
         }
-        if (c.mixed && c.refresh_factor > 0.0 && st->l1 < c.refresh_factor * st->l1_refresh)
+        if (c.mixed && ((c.refresh_factor > 0.0 && st->l1 < c.refresh_factor * st->l1_refresh) ||
+                        cash_stalled(st->l1, st->stall_mark, st->stall_count, c.stall_moves)))
             st->want_refresh = 1;  // applied at the start of the next iteration
         // the refresh of the next iteration runs only when requested
         if (use_cond && c.mixed) cudaGraphSetConditional(cond_refresh, st->want_refresh ? 1u : 0u);
@@ -1368,6 +1387,8 @@ __global__ void __launch_bounds__(kThreads) k_refresh_apply(
             st->fresh = 1;
             st->l1_refresh = L;
             st->refreshes++;
+            st->stall_mark = kNoMark;
+            st->stall_count = 0;
         }
         st->want_refresh = 0;
         st->force_refresh = 0;
@@ -1455,6 +1476,8 @@ __global__ void __launch_bounds__(kThreads) k_step0_uniform(T* __restrict__ c, d
         st->l1_refresh = tot[0];
         st->resid_l1 = 0.0;
         st->fresh = 1;
+        st->stall_mark = kNoMark;
+        st->stall_count = 0;
     }
 }
 

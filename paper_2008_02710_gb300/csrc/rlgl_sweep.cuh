@@ -340,6 +340,8 @@ struct SweepCtl {
     long long tot_green, tot_edges, push_moves, pull_moves;
     long long green, edges;
     double hsum, habs, theta, l1;
+    double stall_mark;
+    long long stall_count;
     unsigned long long t_start;
     float theta_f;
     int fresh, sched, mode;
@@ -389,6 +391,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         sc.habs = st->habs;
         sc.t_start = st->t_start;
         sc.fresh = st->fresh;
+        sc.stall_mark = st->stall_mark;
+        sc.stall_count = st->stall_count;
         // Every barrier adds exactly the grid size, and no barrier can
         // complete before this block arrives: rounding down what has arrived
         // gives the count at the start of this launch.
@@ -461,8 +465,9 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             } else if ((double)(now - sc.t_start) > ctl.time_limit_ns || sc.iters > ctl.max_iters) {
                 stop = ST_TIMEOUT;
             }
-            if (stop < 0 && !skip && ctl.mixed && ctl.refresh_factor > 0.0 &&
-                l1 < ctl.refresh_factor * s_l1_refresh)
+            if (stop < 0 && !skip && ctl.mixed &&
+                ((ctl.refresh_factor > 0.0 && l1 < ctl.refresh_factor * s_l1_refresh) ||
+                 cash_stalled(l1, sc.stall_mark, sc.stall_count, ctl.stall_moves)))
                 want_refresh = true;  // after this move
             sc.leave = (stop >= 0 || skip) ? 1 : 0;
             sc.want_refresh = want_refresh ? 1 : 0;
@@ -487,6 +492,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 st->sumr = sumr;
                 st->iters = sc.iters;
                 st->t_start = sc.t_start;
+                st->stall_mark = sc.stall_mark;
+                st->stall_count = sc.stall_count;
                 if (sc.leave) {
                     st->mode = MODE_NONE;
                     sw->bar.parity = (unsigned int)(sc.p ^ 1);

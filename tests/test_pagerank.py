@@ -131,3 +131,27 @@ def test_aux_node_alone_green_degenerates():
         assert abs(H.sum() - 0.85 ** t) < 1e-14
     pi, C, H, info = oracle.run(aug, sched=oracle.THRESHOLD, m0=m0, tol=1e-12, max_steps=3000)
     assert info["status"] == "ENOCONV" and abs(info["hsum"]) < 1e-9
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_pagerank_mixed_large_hub_converges(persistent):
+    """The auxiliary node takes an addition from every other node at every
+    move, so its FP32 cash carries a rounding floor above the re-derivation
+    trigger; the stall rule re-derives anyway and the MIXED solve reaches
+    its tolerance (L1 <= 1e-6 against the oracle's power iteration)."""
+    from paper_2008_02710_gb300.rlgl import Chain
+    g = synth.rmat_chain(17, 16, seed=1)
+    aug = synth.pagerank_chain(g)
+    p = oracle.transition_probs(aug)
+    ref, _, _ = oracle.power_iteration(aug, p, tol=1e-14, maxit=100000, nthreads=8)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    with Chain(aug, m0=m0, precision="mixed") as ch:
+        ch.set_params(theta_scale=0.5, persistent=persistent)
+        info = ch.solve("link_threshold", tol=1e-9, max_steps=5000)
+        pi = ch.estimate()
+        inv = ch.invariant_residual()
+    assert info["status"] == "RLGL_OK" and info["refreshes"] >= 1
+    assert np.abs(pi - ref).sum() <= 1e-6
+    assert inv <= 1e-8
