@@ -264,7 +264,7 @@ class GpuRun:
 
         lo, hi = 0, 8
         e = err_at(hi)
-        while e > ERR_TARGET:
+        while not e <= ERR_TARGET:  # NaN counts as not reached
             if hi >= max_moves:
                 return None, e, sorted(traj)
             lo, hi = hi, min(2 * hi, max_moves)

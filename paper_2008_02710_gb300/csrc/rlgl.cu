@@ -97,6 +97,7 @@ struct rlgl_ctx {
     // solve graph of the persistent sweep (any schedule it serves) and its grid
     cudaGraphExec_t sweep_graph = nullptr;
     int grid_sweep = 0;
+    int n_hot = 0;  // leading nodes whose in-links the push sums per block
     // profiling
     int profiling = 0;
     std::vector<ProfEv> prof;
@@ -354,12 +355,12 @@ static rlgl_status enqueue_push(Launch L) {
         LAUNCH(L, KC_PUSH,
                (k_push<T, true><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
                    (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
-                   ctx->chunk_row, ctx->st)));
+                   ctx->chunk_row, ctx->st, ctx->n_hot)));
     else
         LAUNCH(L, KC_PUSH,
                (k_push<T, false><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
                    (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
-                   ctx->chunk_row, ctx->st)));
+                   ctx->chunk_row, ctx->st, ctx->n_hot)));
     return RLGL_OK;
 }
 
@@ -431,6 +432,7 @@ static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
     a.use_cond = cd.use;
     a.n = (int)ctx->n;
     a.vec_ok = vec_aligned(ctx);
+    a.n_hot = ctx->n_hot;
     if (ctx->has_w)
         LAUNCH(L, KC_SWEEP, TRY((launch_sweep<T, true>(ctx, a))));
     else
@@ -764,6 +766,19 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     CKL(ctx);
     k_colsum<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->s, n, ctx->colsum);
     CKL(ctx);
+    // Hot targets: the leading nodes (at most kMaxHot) whose in-degree is at
+    // least 8192 and 32 times the mean; the push sums their in-links per block.
+    {
+        long long tp[kMaxHot + 1];
+        const long long m = n < kMaxHot ? n : kMaxHot;
+        CK(ctx, cudaMemcpyAsync(tp, ctx->t_ptr, (size_t)(m + 1) * sizeof(long long), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        const double mean = (double)nnz / (double)n;
+        int k = 0;
+        while (k < m && (double)(tp[k + 1] - tp[k]) >= (8192.0 > 32.0 * mean ? 8192.0 : 32.0 * mean)) ++k;
+        ctx->n_hot = k;
+    }
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     dfree(ctx, cursor);
     return RLGL_OK;

@@ -1048,6 +1048,9 @@ __global__ void __launch_bounds__(kThreads) k_select(
 // edge slot is labelled with its row by marking the row starts and taking a
 // block-wide running maximum, so every edge costs one shared-memory read;
 // edges are then handled in a coalesced order (slot = thread + q * threads).
+
+constexpr int kMaxHot = 32;  // hot-target slots of the push
+
 // Shared memory of the push chunk loop.
 template <typename T>
 struct PushSmem {
@@ -1055,6 +1058,7 @@ struct PushSmem {
     long long base[kPushChunk + 1];
     T m[kPushChunk + 1];
     int wmax[kThreads / 32];
+    double hot[kMaxHot];
 };
 
 // The chunks of a push over E frontier edges of K frontier rows (see
@@ -1062,6 +1066,11 @@ struct PushSmem {
 // handed out one at a time by that counter (thread 0 asks for the next one
 // while the block works on the current one), so that blocks that meet slow
 // atomics take fewer chunks.
+// Targets j < n_hot (nodes with a very large in-degree placed first, like
+// the auxiliary node of a PageRank chain, which every node feeds) are summed
+// per block in FP64 in shared memory and added to the cash once per block:
+// one global addition per block instead of one per in-link, all of which
+// would queue on one L2 address.
 template <typename T, bool kHasW, bool kCg>
 __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __restrict__ col,
                                             const float* __restrict__ w,
@@ -1070,13 +1079,17 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                                             const T* __restrict__ f_m,
                                             const int* __restrict__ chunk_row, long long E,
                                             long long K, long long first, long long step,
-                                            PushSmem<T>& sm,
+                                            PushSmem<T>& sm, int n_hot,
                                             unsigned long long* next = nullptr) {
     constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ long long s_next;
     long long b = first;
+    if (n_hot > 0) {
+        if (threadIdx.x < n_hot) sm.hot[threadIdx.x] = 0.0;
+        __syncthreads();
+    }
     if (next) {
         if (threadIdx.x == 0) s_next = (long long)atomicAdd(next, 1ull);
         __syncthreads();
@@ -1132,7 +1145,8 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                 const int j = __ldg(col + pos);
                 T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
-                red_add(c + j, val);
+                if (j < n_hot) atomicAdd(&sm.hot[j], (double)val);
+                else red_add(c + j, val);
             }
         }
         __syncthreads();
@@ -1143,17 +1157,21 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             b += step;
         }
     }
+    if (n_hot > 0) {
+        __syncthreads();
+        if (threadIdx.x < n_hot && sm.hot[threadIdx.x] != 0.0) red_add(c + threadIdx.x, (T)sm.hot[threadIdx.x]);
+    }
 }
 
 template <typename T, bool kHasW>
 __global__ void __launch_bounds__(kThreads) k_push(
     T* __restrict__ c, const int* __restrict__ col, const float* __restrict__ w,
     const long long* __restrict__ f_eoff, const long long* __restrict__ f_base,
-    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st) {
+    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st, int n_hot) {
     if (st->done || st->skip_move || st->mode != MODE_PUSH) return;
     __shared__ PushSmem<T> sm;
     push_chunks<T, kHasW, false>(c, col, w, f_eoff, f_base, f_m, chunk_row, st->edges, st->green,
-                                 blockIdx.x, gridDim.x, sm);
+                                 blockIdx.x, gridDim.x, sm, n_hot);
 }
 
 // ------------------------------------------------------ merge-path pull

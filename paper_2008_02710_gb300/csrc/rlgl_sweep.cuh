@@ -135,6 +135,7 @@ struct SweepArgs {
     int use_cond;
     int n;
     int vec_ok;
+    int n_hot;
 };
 
 // Shared cache of the select phase: the first kSelCached nodes of a block
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         if (sc.mode == MODE_PUSH)
             push_chunks<T, kHasW, true>(A.c, A.col, A.w, A.f_eoff, A.f_base, A.f_m, A.chunk_row,
                                         sc.edges, sc.green, blockIdx.x, gridDim.x, sm.push,
-                                        &sl->chunk_next);
+                                        A.n_hot, &sl->chunk_next);
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull);

@@ -155,3 +155,34 @@ def test_pagerank_mixed_large_hub_converges(persistent):
     assert info["status"] == "RLGL_OK" and info["refreshes"] >= 1
     assert np.abs(pi - ref).sum() <= 1e-6
     assert inv <= 1e-8
+
+
+@pytest.mark.gpu
+def test_pagerank_hot_node_push_matches_oracle_moves():
+    """The auxiliary node's in-links are summed per block before they reach
+    its cash: one FP64 move from the GPU's state equals the oracle's move of
+    that state within the FP64 rounding budget, node by node."""
+    from paper_2008_02710_gb300.rlgl import Chain
+    g = synth.rmat_chain(14, 16, seed=3)
+    aug = synth.pagerank_chain(g)
+    p = oracle.transition_probs(aug)
+    m0 = np.zeros(aug.n)
+    m0[0] = 1.0
+    with Chain(aug, m0=m0, precision="fp64") as ch:
+        ch.set_params(theta_scale=0.5, pull_crossover=10.0)  # always push
+        hot_moves = 0
+        for _ in range(8):
+            c, h = ch.get_state()
+            info = ch.step("link_threshold")
+            c2, h2 = ch.get_state()
+            g_ = (h2 != h).astype(np.uint8)
+            assert info["mode"] == 1
+            hot_moves += int(g_[0])
+            C, H = c.copy(), h.copy()
+            oracle.move(aug, p, g_, C, H)
+            A, HA = np.abs(c), np.zeros(aug.n)
+            oracle.move(aug, p, g_, A, HA)
+            deg_in = np.bincount(aug.col, minlength=aug.n).astype(float)
+            budget = (deg_in + 4) * 2.0 ** -53 * A + 1e-300
+            assert np.all(np.abs(c2 - C) <= budget)
+    assert hot_moves >= 1  # the auxiliary node was pushed at least once
