@@ -1136,17 +1136,38 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
 #pragma unroll
         for (int q = 0; q < kPer; ++q) sm.row[threadIdx.x * kPer + q] = max(v[q], before);
         __syncthreads();
+        int slot_j[kPer];
+        T slot_v[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int le = threadIdx.x + q * kThreads;
+            slot_j[q] = -1;
+            slot_v[q] = T(0);
             if (le < ne) {
                 const int r = sm.row[le];
                 const long long pos = sm.base[r] + e0 + le;
                 const int j = __ldg(col + pos);
                 T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
-                if (j < n_hot) atomicAdd(&sm.hot[j], (double)val);
-                else red_add(c + j, val);
+                if (j >= n_hot) red_add(c + j, val);
+                slot_j[q] = j;
+                slot_v[q] = val;
+            }
+        }
+        if (n_hot > 0) {
+            // hot targets: one shared-memory addition per warp and target
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int le = threadIdx.x + q * kThreads;
+                const bool hot = le < ne && slot_j[q] < n_hot;
+                unsigned int m = __ballot_sync(0xffffffffu, hot);
+                while (m) {
+                    const int t = __shfl_sync(0xffffffffu, slot_j[q], __ffs(m) - 1);
+                    const bool mine = hot && slot_j[q] == t;
+                    double v = warp_sum(mine ? (double)slot_v[q] : 0.0);
+                    if (lane == 0) atomicAdd(&sm.hot[t], v);
+                    m &= ~__ballot_sync(0xffffffffu, mine);
+                }
             }
         }
         __syncthreads();

@@ -171,6 +171,12 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                                              double& bmabs) {
     __shared__ T tscratch[32];
     __shared__ unsigned long long base_sh, cached_sh;
+    // rows with many push chunks: their chunk starts are written by the
+    // whole block after the second pass instead of by one thread
+    constexpr int kLongRows = 16;
+    constexpr int kLongChunks = 8;
+    __shared__ int s_nlong;
+    __shared__ long long s_long[kLongRows][3];  // frontier row, first chunk, end chunk
     const int n = A.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T msum = T(0), mabs = T(0);
@@ -255,6 +261,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         const unsigned long long all = total + cached_sh;
         base_sh = all ? atomicAdd(&sl->reserve, all) : 0ull;
     }
+    if (threadIdx.x == 0) s_nlong = 0;
     __syncthreads();
     const unsigned long long base = base_sh;
     // pass 2: write
@@ -315,12 +322,27 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 A.f_m[kk] = mtil;
                 const long long b0 = (ee + kPushChunk - 1) / kPushChunk;
                 const long long b1 = (ee + rdeg + kPushChunk - 1) / kPushChunk;
-                for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)kk;
+                int slot = -1;
+                if (b1 - b0 > kLongChunks) {
+                    slot = atomicAdd(&s_nlong, 1);
+                    if (slot < kLongRows) {
+                        s_long[slot][0] = kk;
+                        s_long[slot][1] = b0;
+                        s_long[slot][2] = b1;
+                    }
+                }
+                if (slot < 0 || slot >= kLongRows)
+                    for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)kk;
             } else {
                 A.mt[i] = T(0);
             }
         }
     }
+    __syncthreads();
+    const int nlong = s_nlong < kLongRows ? s_nlong : kLongRows;
+    for (int r = 0; r < nlong; ++r)
+        for (long long b = s_long[r][1] + threadIdx.x; b < s_long[r][2]; b += blockDim.x)
+            A.chunk_row[b] = (int)s_long[r][0];
     bmsum = (double)block_sum(msum, tscratch);
     bmabs = (double)block_sum(mabs, tscratch);
 }
