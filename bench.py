@@ -244,7 +244,9 @@ class GpuRun:
         self.chain.estimate(self.pi_dev)
         with self.torch.cuda.stream(self.stream):
             e = (self.pi_dev - ref_dev).abs().sum()
-        return float(e.item())
+            # read back on the stream that computed it (a read on another
+            # stream could see the previous result)
+            return float(e.item())
 
     def calibrate(self, sched, theta, ref_dev, max_moves=20000):
         """Untimed: the least move count T* whose solve (the timed path: step
@@ -522,7 +524,8 @@ def run_gpu(args):
     clk = clocks.stop()
     barrier(dist)
     # final error of the timed run's estimate
-    final_err = float((g.pi_dev - ref_dev).abs().sum().item())
+    with torch.cuda.stream(g.stream):
+        final_err = float((g.pi_dev - ref_dev).abs().sum().item())
     total_ms = float(np.sum(times))
     total_ms_max = max_over_ranks(dist, total_ms, device)
     pushes = float(sum(i["edges_pushed"] for i in infos))
@@ -638,7 +641,7 @@ def run_batch(args):
         with torch.cuda.stream(stream):
             e = torch.zeros(args.chains, dtype=torch.float64, device=device)
             e.index_add_(0, seg_dev, (pi - ref_dev).abs())
-        return e.cpu().numpy()
+            return e.cpu().numpy()  # on the stream that computed it
 
     out = {"metric": "batched: chains/s to L1 err 1e-6 per chain (4096-chain mix)", "unit": "chains/s",
            "workload": f"{args.chains} power-law chains, n={csr.n}, nnz={csr.nnz}",

@@ -168,6 +168,19 @@ def _ptr(a, dtype=None):
     return arr.ctypes.data, HOST, arr
 
 
+def _like(x, ref):
+    """x (numpy array or torch tensor, or None) in the memory space of ref."""
+    if x is None:
+        return None
+    if _is_torch(ref):
+        import torch
+        t = x if _is_torch(x) else torch.from_numpy(np.ascontiguousarray(x))
+        return t.to(device=ref.device)
+    if _is_torch(x):
+        return x.detach().cpu().numpy()
+    return x
+
+
 def _np_dtype(t):
     import torch
     return {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
@@ -190,6 +203,8 @@ class Chain:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         is_torch = _is_torch(csr.row_ptr)
         cv = (lambda t: _np_dtype(t)) if is_torch else (lambda t: t)
+        # m0 / c / h are read from the CSR's memory space: bring them there
+        m0, c, h = (_like(x, csr.row_ptr) for x in (m0, c, h))
         rp, sp, k1 = _ptr(csr.row_ptr, cv(np.int64))
         cp, _, k2 = _ptr(csr.col, cv(np.int32))
         wp, _, k3 = _ptr(csr.w, cv(np.float32))
