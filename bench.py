@@ -62,6 +62,9 @@ WORKLOADS = {
                     desc="R-MAT scale 24 symmetrised (N=2^24, every R-MAT edge both ways, cycle both "
                          "ways, self-loops; unit weights), FP32 cash, FP64 history; reference "
                          "pi_i = d_i / sum d"),
+    "rmat22u": dict(scale=22, edge_factor=16, weighted=False, precision="mixed", undirected=True,
+                    desc="R-MAT scale 22 symmetrised (N=2^22, unit weights; chain ~1.5 GB, beyond L2), "
+                         "FP32 cash, FP64 history; reference pi_i = d_i / sum d"),
     "pagerank20": dict(scale=20, edge_factor=16, weighted=False, precision="mixed", pagerank=True,
                        desc="PageRank c=0.85, uniform restart, on R-MAT scale 20 through the "
                             "auxiliary-node chain P^(0) (N=2^20+1), FP32 cash, FP64 history"),

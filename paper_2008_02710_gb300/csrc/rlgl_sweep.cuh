@@ -200,6 +200,68 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         bmabs = (double)block_sum(mabs, tscratch);
         return;
     }
+    if ((long long)n > (long long)gridDim.x * kSelCached) {
+        // Large chains (more block-iterations than the cache holds): one pass
+        // with one reservation per block-iteration, so that the nodes are
+        // read once (a second pass would read them again from memory).
+        for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
+             it0 += (long long)gridDim.x * kNodesPerIter) {
+            long long rb[kNodesPerThread];
+            int rdeg[kNodesPerThread];
+            T val[kNodesPerThread], idg[kNodesPerThread];
+            bool g[kNodesPerThread];
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
+                rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
+                val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
+                idg[q] = (i < n && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
+            }
+            unsigned long long mine = 0ull;
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                g[q] = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
+                if (g[q]) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+            }
+            unsigned long long total;
+            const unsigned long long pre = block_exscan(mine, &total);
+            if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
+            __syncthreads();
+            const unsigned long long base = base_sh + pre;
+            long long k = (long long)(base & ((1ull << kCountBits) - 1ull));
+            long long e = (long long)(base >> kCountBits);
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                if (i >= n) continue;
+                if (g[q]) {
+                    const T v = val[q];
+                    const T mtil = moved_per_weight(v, A.s, A.sf, i);
+                    A.c[i] = T(0);
+                    red_add(A.H + i, (double)v);  // no load: the L2 adds
+                    msum += v;
+                    mabs += fabs(v);
+                    A.mt[i] = mtil;
+                    A.f_eoff[k] = e;
+                    A.f_base[k] = rb[q] - e;
+                    A.f_m[k] = mtil;
+                    const long long b0 = (e + kPushChunk - 1) / kPushChunk;
+                    const long long b1 = (e + rdeg[q] + kPushChunk - 1) / kPushChunk;
+                    for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)k;
+                    ++k;
+                    e += rdeg[q];
+                } else {
+                    A.mt[i] = T(0);
+                }
+            }
+            __syncthreads();  // base_sh is rewritten by the next iteration
+        }
+        bmsum = (double)block_sum(msum, tscratch);
+        bmabs = (double)block_sum(mabs, tscratch);
+        return;
+    }
     // pass 1: count (per warp and group for the cached nodes, per thread beyond)
     unsigned long long mine = 0ull;
     int j = 0;

@@ -151,3 +151,26 @@ def test_barrier_wait_is_bounded_and_context_survives(weighted):
         info = ch.solve("link_threshold", tol=1e-9)
         assert info["status"] == "RLGL_OK"
         assert ch.get_params().persistent == 1
+
+
+def test_sweep_large_chain_single_pass_select():
+    """More nodes than the sweep's select cache covers (n > blocks x 2048):
+    the one-pass select. 25 FP64 moves agree with the oracle's 25 moves and
+    with the one-kernel-per-phase path."""
+    import oracle
+    csr = synth.rmat_chain_n((1 << 21) + 12345, 2, seed=11)
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    info_or = oracle.solve(csr, p, C, H, sched=oracle.LINK_THRESHOLD, theta_scale=0.5, tol=0.0,
+                           max_steps=25, check_every=-1)
+    pi_or = oracle.estimate(H)
+    pis = []
+    for persistent in (1, 0):
+        with Chain(csr, precision="fp64") as ch:
+            ch.set_params(theta_scale=0.5, persistent=persistent)
+            info = ch.solve("link_threshold", tol=0.0, max_steps=25, raise_on_noconv=False)
+            assert info["moves"] == 25 and ch.get_params().persistent == persistent
+            pis.append(ch.estimate())
+    assert np.abs(pis[0] - pi_or).sum() <= 1e-12
+    assert np.abs(pis[0] - pis[1]).sum() <= 1e-12
+    assert abs(info["edges_pushed"] - info_or["pushes"]) <= 1e-4 * info_or["pushes"]
