@@ -358,7 +358,7 @@ class GpuRun:
         push_rate = (sum(e for e, _ in push) / (sum(t for _, t in push) * 1e-6) / 1e9) if push else None
         return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull")), phases, push_rate
 
-    def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0):
+    def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0, r=1):
         """Through the public API with host buffers: every step uploads the
         chain from pinned host memory (create), solves, and reads pi back."""
         torch = self.torch
@@ -378,7 +378,7 @@ class GpuRun:
             torch.cuda.synchronize(self.device)
             t0 = time.perf_counter()
             with Chain(pinned, m0=m0, precision=self.wl["precision"], stream=self.stream) as ch:
-                ch.set_params(theta_scale=theta_scale)
+                ch.set_params(theta_scale=theta_scale, r=r)
                 info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
                 ch.estimate(pi_host)
             t1 = time.perf_counter()
@@ -457,13 +457,37 @@ def run_gpu(args):
     }
     head = args.sched
     order = [head] + ([] if args.skip_compare else [k for k in plan if k != head])
+    r_of = {name: 1 for name in plan}
 
     def use(name):
         sched, theta, scale, cap = plan[name]
-        g.chain.set_params(theta_scale=scale)
+        g.chain.set_params(theta_scale=scale, r=r_of[name])
         return sched, theta, cap
 
     nvtx = torch.cuda.nvtx
+    # autotuned threshold: the scale and exponent r of theta_t(r) with the
+    # least time to the error target (untimed search; the timed run below
+    # uses the winner)
+    tuning = None
+    if args.tune and head in ("link_threshold", "threshold"):
+        nvtx.range_push("tune")
+        tuning = []
+        sched, theta, _, cap = plan[head]
+        for r in (1, 2):
+            for scale in (0.25, 0.35, 0.5, 0.7, 1.0):
+                g.chain.set_params(theta_scale=scale, r=r)
+                ts_, e_, _ = g.calibrate(sched, theta, ref_dev, max_moves=cap)
+                if ts_ is None:
+                    tuning.append(dict(theta_scale=scale, r=r, tstar=None))
+                    continue
+                tt, _ = g.timed_solves(sched, theta, ts_, 3, 1)
+                tuning.append(dict(theta_scale=scale, r=r, tstar=ts_, ms=float(np.median(tt))))
+        done = [t for t in tuning if t.get("ms")]
+        if done:
+            best = min(done, key=lambda t: t["ms"])
+            plan[head] = (sched, theta, best["theta_scale"], cap)
+            r_of[head] = best["r"]
+        nvtx.range_pop()
     cal = {}
     nvtx.range_push("calibrate")
     for name in order:
@@ -541,7 +565,7 @@ def run_gpu(args):
     if args.no_e2e:
         et, ep, h2d, d2h = [float("nan")], [0], 0, 0
     else:
-        et, ep, h2d, d2h = g.e2e(sched_h, theta_h, tstar, max(3, args.steps // 2), 1, args.theta_scale if head == "link_threshold" else 1.0)
+        et, ep, h2d, d2h = g.e2e(sched_h, theta_h, tstar, max(3, args.steps // 2), 1, plan[head][2], r_of[head])
     e2e_t = max_over_ranks(dist, float(np.sum(et)), device)
     e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
 
@@ -573,7 +597,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 cash / f64 history" if wl["precision"] == "mixed" else "f64",
         "data": "synthetic (seeded R-MAT; stands in for the paper's web graphs)",
         "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
-                   "schedule": head, "theta_scale": plan[head][2], "precision": wl["precision"],
+                   "schedule": head, "theta_scale": plan[head][2], "r": r_of[head],
+                   "autotuned": tuning is not None, "precision": wl["precision"],
                    "tstar_moves": tstar,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -584,6 +609,7 @@ def run_gpu(args):
         "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step)
         if compare.get("all_green", {}).get("ms") else None,
         "persistent_sweep": sweep_on,
+        "tuning": tuning,
         "sweep_phase_us_per_move": sweep_phases if sweep_on else None,
         "time_to_err_ms_phase_kernels": phase_ms,
         "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
@@ -861,6 +887,8 @@ def main(argv=None):
     ap.add_argument("--max-moves", type=int, default=20000)
     ap.add_argument("--persistent", type=int, choices=[0, 1], default=1,
                     help="1: solves run as the persistent sweep; 0: one kernel per phase")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="keep --theta-scale and r = 1 instead of autotuning the threshold")
     ap.add_argument("--autotune", action="store_true",
                     help="batch: pick theta scale, r and the push/pull crossover with the autotuner first")
     ap.add_argument("--skip-compare", action="store_true")

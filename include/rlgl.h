@@ -105,7 +105,7 @@ typedef struct {
                                the in-links instead of pushing (default 0.9: on GB300 a pull
                                over all in-links costs about as much as pushing every edge) */
     int32_t safety_every;   /* every K-th move of a solve is all-green (0 = never, default) */
-    double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-3; 0 = only at the end) */
+    double refresh_factor;  /* MIXED only: see rlgl_precision (default 1e-4; 0 = only at the end) */
     double time_limit_s;    /* wall-clock limit of one rlgl_solve, checked on the device (default 600) */
     int64_t rr_blocks;      /* BLOCK_RR: number of blocks K (default 8) */
     double pc_frac;         /* PC: expected green fraction k / N before capping (default 0.05) */

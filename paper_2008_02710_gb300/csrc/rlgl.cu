@@ -793,7 +793,7 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->top_frac = 0.01;
     p->pull_crossover = 0.9;
     p->safety_every = 0;
-    p->refresh_factor = 1e-3;
+    p->refresh_factor = 1e-4;
     p->time_limit_s = 600.0;
     p->rr_blocks = 8;
     p->pc_frac = 0.05;
