@@ -213,22 +213,18 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
                 const long long i = it0 + q * kThreads + threadIdx.x;
+                rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
+                rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
                 val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
                 idg[q] = (i < n && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
             }
-            // row offsets only for green nodes: at this size the select is
-            // bound by HBM bandwidth, and most nodes are red
+            unsigned long long mine = 0ull;
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
                 const long long i = it0 + q * kThreads + threadIdx.x;
                 g[q] = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
-                rb[q] = g[q] ? __ldg(A.row_ptr + i) : 0;
-                rdeg[q] = g[q] ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
-            }
-            unsigned long long mine = 0ull;
-#pragma unroll
-            for (int q = 0; q < kNodesPerThread; ++q)
                 if (g[q]) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+            }
             unsigned long long total;
             const unsigned long long pre = block_exscan(mine, &total);
             if (threadIdx.x == 0) base_sh = total ? atomicAdd(&sl->reserve, total) : 0ull;
