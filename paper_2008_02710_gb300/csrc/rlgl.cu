@@ -741,7 +741,6 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     if (err & 8u) return fail(ctx, RLGL_ENOTSTOCHASTIC, "a weight is not positive and finite");
 
     const int gn = grid_for(n, kThreads, ctx->sms * 16);
-    const int gw = grid_for(n * 32, kThreads, ctx->sms * 16);
     k_row_scale<<<gn, kThreads, 0, ctx->stream>>>(
         ctx->row_ptr, ctx->w, n, ctx->s, ctx->sf,
         prec == RLGL_MIXED ? (float*)ctx->ideg : nullptr,
@@ -757,14 +756,25 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     if (sc != RLGL_OK) { dfree(ctx, cursor); return sc; }
     CK(ctx, cudaMemcpyAsync(cursor, ctx->t_ptr, ((size_t)n + 1) * sizeof(long long),
                             cudaMemcpyDeviceToDevice, ctx->stream));
-    k_scatter_in<<<gw, kThreads, 0, ctx->stream>>>(ctx->row_ptr, ctx->col, ctx->w, n, cursor,
-                                                    ctx->t_src, ctx->t_w);
+    // edge-balanced scatter (a warp per row would leave one warp with every
+    // edge of a hub row)
+    const long long nch = (nnz + kPushChunk - 1) / kPushChunk;
+    k_chunk_rows<<<grid_for(nch + 1, kThreads, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, n, nnz, ctx->chunk_row);
+    k_csc_scatter<<<grid_for(nch, 1, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, ctx->col, ctx->w, nnz, ctx->chunk_row, cursor, ctx->t_src, ctx->t_w);
     CKL(ctx);
     const int gt = grid_for(ctx->ntiles + 1, kThreads, ctx->sms * 16);
     k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
                                                       ctx->tile_e);
     CKL(ctx);
-    k_colsum<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->s, n, ctx->colsum);
+    CK(ctx, cudaMemsetAsync(ctx->colsum, 0, (size_t)n * sizeof(double), ctx->stream));
+    if (ctx->has_w)
+        k_colsum_tiles<true><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
+    else
+        k_colsum_tiles<false><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
     CKL(ctx);
     // Hot targets: the leading nodes (at most kMaxHot) whose in-degree is at
     // least 8192 and 32 times the mean; the push sums their in-links per block.

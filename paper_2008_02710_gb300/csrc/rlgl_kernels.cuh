@@ -1464,24 +1464,6 @@ __global__ void __launch_bounds__(kThreads) k_hist_sums(const double* __restrict
     }
 }
 
-// colsum_j = sum over in-links (i, j) of s_i w_ij = (1 P)_j, in FP64; one
-// warp per row of the CSC. Computed once per chain: step 0 from the uniform
-// M_0 then needs no pass over the edges.
-__global__ void k_colsum(const long long* __restrict__ t_ptr, const int* __restrict__ t_src,
-                         const float* __restrict__ t_w, const double* __restrict__ s, long long n,
-                         double* __restrict__ colsum) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long j = warp; j < n; j += nwarps) {
-        double acc = 0.0;
-        for (long long e = t_ptr[j] + lane; e < t_ptr[j + 1]; e += 32)
-            acc += s[t_src[e]] * (t_w ? (double)t_w[e] : 1.0);
-        acc = warp_sum(acc);
-        if (lane == 0) colsum[j] = acc;
-    }
-}
-
 // Step 0 from the uniform M_0 (Eq. init): H = M_0 = 1/N (1/N_k within chain
 // k of a batch) and C_1 = M_0 (P - I), i.e. C_j = (colsum_j - 1) / N, in FP64
 // and then rounded to the cash type; ||C_1||_1 of the stored cash goes to
@@ -1678,22 +1660,107 @@ __global__ void k_count_in(const int* __restrict__ col, long long nnz, long long
         atomicAdd((unsigned long long*)(cnt + col[k] + 1), 1ull);
 }
 
-// Scatter of the CSR into the CSC with per-row cursors, one warp per row
-// (order within a CSC row is arbitrary).
-__global__ void k_scatter_in(const long long* __restrict__ row_ptr, const int* __restrict__ col,
-                             const float* __restrict__ w, long long n, long long* cursor,
-                             int* __restrict__ t_src, float* __restrict__ t_w) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = warp; i < n; i += nwarps) {
-        for (long long k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
-            int j = col[k];
-            long long q = (long long)atomicAdd((unsigned long long*)(cursor + j), 1ull);
-            t_src[q] = (int)i;
-            if (w) t_w[q] = w[k];
+// Row of the first edge of every kPushChunk-edge chunk of the CSR (binary
+// search; every row has at least one edge), and out[nchunks] = n - 1.
+__global__ void k_chunk_rows(const long long* __restrict__ row_ptr, long long n, long long nnz,
+                             int* __restrict__ out) {
+    const long long nch = (nnz + kPushChunk - 1) / kPushChunk;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b <= nch;
+         b += (long long)gridDim.x * blockDim.x) {
+        if (b == nch) {
+            out[b] = (int)(n - 1);
+            continue;
         }
+        const long long e = b * kPushChunk;
+        long long lo = 0, hi = n - 1;  // largest i with row_ptr[i] <= e
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if (row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        out[b] = (int)lo;
     }
+}
+
+// Scatter of the CSR into the CSC with per-column cursors, edge-balanced:
+// chunks of kPushChunk consecutive edges whatever the row lengths (a row
+// with 10^5 edges spreads over many blocks), each edge labelled with its row
+// by marking the row starts in the chunk and a block-wide running maximum
+// (as in the push). Order within a CSC row is arbitrary.
+__global__ void __launch_bounds__(kThreads) k_csc_scatter(
+    const long long* __restrict__ row_ptr, const int* __restrict__ col, const float* __restrict__ w,
+    long long nnz, const int* __restrict__ chunk_first_row, long long* cursor, int* __restrict__ t_src,
+    float* __restrict__ t_w) {
+    constexpr int kPer = kPushChunk / kThreads;
+    __shared__ int s_row[kPushChunk];
+    __shared__ int s_wmax[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long nch = (nnz + kPushChunk - 1) / kPushChunk;
+    for (long long b = blockIdx.x; b < nch; b += gridDim.x) {
+        const long long e0 = b * kPushChunk;
+        const int ne = (int)min((long long)kPushChunk, nnz - e0);
+        const int k0 = chunk_first_row[b];
+        const int k1 = (b + 1 < nch) ? chunk_first_row[b + 1] : chunk_first_row[nch];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = 0;
+        __syncthreads();
+        // rows k0+1..k1 start inside this chunk (offsets relative to k0)
+        for (long long r = k0 + 1 + threadIdx.x; r <= k1; r += blockDim.x) {
+            const long long off = row_ptr[r] - e0;
+            if (off < ne) s_row[(int)off] = (int)(r - k0);
+        }
+        __syncthreads();
+        int v[kPer];
+        int run = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            run = max(run, s_row[threadIdx.x * kPer + q]);
+            v[q] = run;
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        if (lane == 31) s_wmax[wid] = incl;
+        __syncthreads();
+        int before = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) before = 0;
+        for (int k = 0; k < wid; ++k) before = max(before, s_wmax[k]);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) s_row[threadIdx.x * kPer + q] = max(v[q], before);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int le = threadIdx.x + q * kThreads;
+            if (le < ne) {
+                const long long e = e0 + le;
+                const int j = col[e];
+                const long long pos = (long long)atomicAdd((unsigned long long*)(cursor + j), 1ull);
+                t_src[pos] = k0 + s_row[le];
+                if (w) t_w[pos] = w[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// colsum_j = sum over in-links (i, j) of s_i w_ij = (1 P)_j in FP64, over the
+// CSC with merge-path tiles (balanced whatever the in-degrees); colsum must be
+// zero on entry. Computed once per chain: step 0 from the uniform M_0 then
+// needs no pass over the edges.
+template <bool kHasW>
+__global__ void __launch_bounds__(kThreads) k_colsum_tiles(double* __restrict__ colsum,
+                                                           const double* __restrict__ s,
+                                                           const long long* __restrict__ t_ptr,
+                                                           const int* __restrict__ t_src,
+                                                           const float* __restrict__ t_w,
+                                                           const long long* __restrict__ tile_r,
+                                                           const long long* __restrict__ tile_e,
+                                                           long long ntiles) {
+    __shared__ PullSmem<double> sm;
+    pull_tiles<double, double, kHasW, false>(colsum, s, t_ptr, t_src, t_w, tile_r, tile_e, ntiles,
+                                             blockIdx.x, gridDim.x, sm);
 }
 
 // Batch: every chain running again (and its tolerance, when tol >= 0).
