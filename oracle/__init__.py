@@ -53,7 +53,7 @@ def _load():
             L.oracle_initial_step.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.oracle_select.restype = dbl
             L.oracle_select.argtypes = [i64, vp, vp, i32, dbl, i32, dbl, dbl, vp, i64, i64, dbl,
-                                        ctypes.c_uint64, vp]
+                                        ctypes.c_uint64, vp, vp]
             L.oracle_pc_uniform.restype = dbl
             L.oracle_pc_uniform.argtypes = [ctypes.c_uint64, i64, i64]
             L.oracle_sm64_next.restype = ctypes.c_uint64
@@ -67,7 +67,7 @@ def _load():
             L.oracle_solve.restype = ctypes.c_int
             L.oracle_solve.argtypes = [i64, vp, vp, vp, i32, dbl, i32, dbl, dbl, vp, i64,
                                        i64, dbl, i64, vp, vp, i64, vp, vp, i64, i64, dbl,
-                                       ctypes.c_uint64]
+                                       ctypes.c_uint64, i32]
             L.oracle_estimate.restype = ctypes.c_int
             L.oracle_estimate.argtypes = [i64, vp, vp]
             L.oracle_power_iteration.restype = i64
@@ -108,19 +108,22 @@ def initial_step(csr, p, m0: Optional[np.ndarray] = None):
 
 def select(C, sched: int, theta_scale: float = 1.0, r: int = 1, abs_theta: float = 0.0,
            top_frac: float = 0.01, mask=None, row_ptr=None, move: int = 0, rr_blocks: int = 8,
-           pc_frac: float = 0.05, seed: int = 0):
+           pc_frac: float = 0.05, seed: int = 0, cstat=None):
     """Green set of the schedule for cash C: returns (green uint8[n], theta).
     row_ptr (the CSR offsets) is needed by LINK_THRESHOLD only; move (t,
-    counted from step 0), rr_blocks, pc_frac and seed by BLOCK_RR and PC."""
+    counted from step 0), rr_blocks, pc_frac and seed by BLOCK_RR and PC.
+    cstat: the cash whose statistics set theta and the PC constant (default
+    C itself; the stale threshold passes the previous move's cash)."""
     L = _load()
     C = _f64(C)
+    cs = None if cstat is None else _f64(cstat)
     green = np.empty(C.shape[0], dtype=np.uint8)
     mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     rp = None if row_ptr is None else np.ascontiguousarray(row_ptr, dtype=np.int64)
     if sched == LINK_THRESHOLD and rp is None:
         raise ValueError("LINK_THRESHOLD needs row_ptr")
     th = L.oracle_select(C.shape[0], _p(rp), _p(C), sched, theta_scale, r, abs_theta, top_frac,
-                         _p(mk), move, rr_blocks, pc_frac, seed, _p(green))
+                         _p(mk), move, rr_blocks, pc_frac, seed, _p(cs), _p(green))
     return green, th
 
 
@@ -156,10 +159,13 @@ def invariant_residual(csr, p, C, H, c0=None) -> float:
 def solve(csr, p, C, H, sched: int = THRESHOLD, theta_scale: float = 1.0, r: int = 1,
           abs_theta: float = 0.0, top_frac: float = 0.01, masks=None, safety_every: int = 0,
           tol: float = 1e-12, max_steps: int = 100000, check_every: int = 0, move0: int = 0,
-          rr_blocks: int = 8, pc_frac: float = 0.05, seed: int = 0):
+          rr_blocks: int = 8, pc_frac: float = 0.05, seed: int = 0, theta_lag: int = 0):
     """Algorithm 1 from state (C, H) (modified in place). Returns a dict with
     status, moves, resid (||C||_1/|H 1|), pushes, hsum and the worst
-    per-step invariant values when check_every >= 0."""
+    per-step invariant values when check_every >= 0. theta_lag = 1: every
+    move after the first takes its threshold from the cash before the
+    previous move and is made before its stop test takes effect (the stale
+    threshold of Sec. 6; see oracle_solve)."""
     L = _load()
     assert C.dtype == np.float64 and H.dtype == np.float64
     mk, period = None, 1
@@ -171,7 +177,7 @@ def solve(csr, p, C, H, sched: int = THRESHOLD, theta_scale: float = 1.0, r: int
     st = L.oracle_solve(csr.n, _p(csr.row_ptr), _p(csr.col), _p(p), sched, theta_scale, r,
                         abs_theta, top_frac, _p(mk), period, safety_every, tol, max_steps,
                         _p(C), _p(H), check_every, _p(chk), _p(out), move0, rr_blocks,
-                        pc_frac, seed)
+                        pc_frac, seed, theta_lag)
     res = dict(status=STATUS.get(st, st), moves=int(out[0]), resid=float(out[1]),
                pushes=float(out[2]), hsum=float(out[3]))
     if chk is not None:

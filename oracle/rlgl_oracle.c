@@ -173,8 +173,10 @@ double oracle_pc_uniform(uint64_t seed, int64_t t, int64_t i) {
  *               about k nodes drawn at once, independently.
  * Zero-cash nodes are left out of the cash-dependent sets; moving zero cash
  * changes nothing. row_ptr is read only by LINK_THRESHOLD. `move` is t for
- * BLOCK_RR and PC. Writes green[] and returns theta (0 for the schedules
- * without a threshold).
+ * BLOCK_RR and PC. Cstat is the cash whose statistics set theta (THRESHOLD,
+ * LINK_THRESHOLD, TOPFRAC) and ||C||_1 (PC); NULL means C itself (the
+ * stale-threshold variant of oracle_solve passes the previous move's cash).
+ * Writes green[] and returns theta (0 for the schedules without a threshold).
  */
 static double select_value(int32_t sched, const int64_t* row_ptr, const double* C, int64_t i) {
     if (sched == SCHED_LINK_THRESHOLD) return fabs(C[i]) / (double)(row_ptr[i + 1] - row_ptr[i]);
@@ -184,8 +186,9 @@ static double select_value(int32_t sched, const int64_t* row_ptr, const double* 
 double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t sched,
                      double theta_scale, int32_t r, double abs_theta, double top_frac,
                      const uint8_t* mask, int64_t move, int64_t rr_blocks, double pc_frac,
-                     uint64_t seed, uint8_t* green) {
+                     uint64_t seed, const double* Cstat, uint8_t* green) {
     double theta = 0.0;
+    if (!Cstat) Cstat = C;
     if (sched == SCHED_BLOCK_RR) {
         int64_t K = rr_blocks < 1 ? 1 : (rr_blocks > n ? n : rr_blocks);
         int64_t b = (n + K - 1) / K;
@@ -196,7 +199,7 @@ double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t
     }
     if (sched == SCHED_PC) {
         double l1 = 0.0;
-        for (int64_t j = 0; j < n; ++j) l1 += fabs(C[j]);
+        for (int64_t j = 0; j < n; ++j) l1 += fabs(Cstat[j]);
         const double k = pc_frac * (double)n;
         for (int64_t i = 0; i < n; ++i) {
             green[i] = 0;
@@ -221,7 +224,7 @@ double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t
         } else {
             double s = 0.0;
             for (int64_t j = 0; j < n; ++j) {
-                double v = select_value(sched, row_ptr, C, j);
+                double v = select_value(sched, row_ptr, Cstat, j);
                 s += (r == 1) ? v : pow(v, (double)r);
             }
             theta = (r == 1) ? theta_scale * (s / (double)n)
@@ -232,7 +235,7 @@ double oracle_select(int64_t n, const int64_t* row_ptr, const double* C, int32_t
         if (k < 1) k = 1;
         if (k > n) k = n;
         double* a = (double*)malloc((size_t)n * sizeof(double));
-        for (int64_t j = 0; j < n; ++j) a[j] = fabs(C[j]);
+        for (int64_t j = 0; j < n; ++j) a[j] = fabs(Cstat[j]);
         qsort(a, (size_t)n, sizeof(double), cmp_desc);
         theta = a[k - 1];
         free(a);
@@ -293,14 +296,26 @@ double oracle_invariant_residual(int64_t n, const int64_t* row_ptr, const int32_
  * (sum over moves of sum_{i in G} deg_i), out[3] = H 1. move0 = moves made
  * since step 0 before this call (the t of BLOCK_RR and PC); rr_blocks,
  * pc_frac and seed: see oracle_select.
+ *
+ * theta_lag = 1: the stale threshold that Sec. 6 allows for RLGL_Theta (the
+ * threshold "updated less frequently"), one move stale. The first move of
+ * the call is as above. Every later move t takes its statistics (theta, and
+ * ||C||_1 for PC) from C_{t-1}, the cash before the previous move, and its
+ * stop test from C_t in the same pass as its selection, so that the move is
+ * made whatever the test says: the order of a later move is
+ *   degenerate test; max_steps test; choose G_t with C_{t-1}'s statistics;
+ *   move; stop with OR_OK if t >= 2 and ||C_t||_1 / |H_t 1| < tol,
+ * and out[1] is then ||C_t||_1 / |H_{t+1} 1|.
  */
 int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* p,
                  int32_t sched, double theta_scale, int32_t r, double abs_theta,
                  double top_frac, const uint8_t* mask, int64_t mask_period,
                  int64_t safety_every, double tol, int64_t max_steps, double* C, double* H,
                  int64_t check_every, double* check, double* out, int64_t move0,
-                 int64_t rr_blocks, double pc_frac, uint64_t seed) {
+                 int64_t rr_blocks, double pc_frac, uint64_t seed, int32_t theta_lag) {
     uint8_t* green = (uint8_t*)malloc((size_t)n);
+    double* Cprev = theta_lag ? (double*)malloc((size_t)n * sizeof(double)) : NULL;
+    int have_prev = 0;
     int64_t moves = 0;
     double pushes = 0.0;
     int status = OR_ENOCONV;
@@ -309,13 +324,19 @@ int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const do
         double l1 = oracle_l1(n, C), hs = oracle_sum(n, H), habs = oracle_l1(n, H);
         if (out) { out[1] = (hs != 0.0) ? l1 / fabs(hs) : INFINITY; out[3] = hs; }
         if (fabs(hs) <= 1e-12 * habs || habs == 0.0) { status = OR_EDEGENERATE; break; }
-        if (t >= 2 && l1 / fabs(hs) < tol) { status = OR_OK; break; }
+        const int lagged = theta_lag && have_prev;
+        const int conv = t >= 2 && l1 / fabs(hs) < tol;
+        if (conv && !lagged) { status = OR_OK; break; }
         if (moves >= max_steps) { status = OR_ENOCONV; break; }
         int32_t s = sched;
         if (safety_every > 0 && (moves + 1) % safety_every == 0) s = SCHED_ALL_GREEN;
         const uint8_t* mk = (s == SCHED_MASK) ? mask + (size_t)((moves % mask_period) * n) : NULL;
         oracle_select(n, row_ptr, C, s, theta_scale, r, abs_theta, top_frac, mk, move0 + moves,
-                      rr_blocks, pc_frac, seed, green);
+                      rr_blocks, pc_frac, seed, lagged ? Cprev : NULL, green);
+        if (theta_lag) {
+            memcpy(Cprev, C, (size_t)n * sizeof(double));
+            have_prev = 1;
+        }
         double st[3];
         oracle_move(n, row_ptr, col, p, green, C, H, st);
         ++moves;
@@ -332,8 +353,15 @@ int oracle_solve(int64_t n, const int64_t* row_ptr, const int32_t* col, const do
                 if (ir > check[2]) check[2] = ir;
             }
         }
+        if (lagged && conv) {
+            status = OR_OK;
+            hs = oracle_sum(n, H);
+            if (out) { out[1] = (hs != 0.0) ? l1 / fabs(hs) : INFINITY; out[3] = hs; }
+            break;
+        }
     }
     if (out) { out[0] = (double)moves; out[2] = pushes; }
+    free(Cprev);
     free(green);
     return status;
 }

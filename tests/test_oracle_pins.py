@@ -553,3 +553,82 @@ def test_degree_law_is_the_stationary_law_of_an_undirected_walk():
     p = oracle.transition_probs(csr)
     ref = oracle.gth(oracle.dense_P(csr, p))
     assert np.abs(oracle.degree_law(csr) - ref).sum() < 1e-12
+
+
+# ---------------------------------------- stale threshold (Sec. 6, theta_lag)
+
+@pytest.mark.parametrize("sched,theta", [(oracle.THRESHOLD, 1e-10), (oracle.ALL_GREEN, 0.0)])
+def test_stale_threshold_with_fixed_theta_is_one_more_move(sched, theta):
+    """With a fixed threshold (or none) the stale-threshold variant differs
+    from Alg. 1 only in its stop: the move whose test succeeds is still made.
+    So it ends exactly one move of the plain rule later, and reports the
+    tested ||C_t||_1 over the H 1 after that move."""
+    csr = synth.tiny_chain(300, seed=4)
+    p = oracle.transition_probs(csr)
+    C0, H0 = oracle.initial_step(csr, p)
+    C, H = C0.copy(), H0.copy()
+    plain = oracle.solve(csr, p, C, H, sched=sched, abs_theta=theta, tol=1e-6, max_steps=100000)
+    assert plain["status"] == "OK" and plain["moves"] >= 3
+    l1_tested = np.abs(C).sum()
+    g, _ = oracle.select(C, sched, abs_theta=theta)
+    oracle.move(csr, p, g, C, H)
+    C2, H2 = C0.copy(), H0.copy()
+    lag = oracle.solve(csr, p, C2, H2, sched=sched, abs_theta=theta, tol=1e-6, max_steps=100000,
+                       theta_lag=1)
+    assert lag["status"] == "OK"
+    assert lag["moves"] == plain["moves"] + 1
+    assert np.array_equal(C2, C) and np.array_equal(H2, H)
+    assert lag["resid"] == pytest.approx(l1_tested / abs(H.sum()), rel=1e-13)
+
+
+@pytest.mark.parametrize("sched", [oracle.THRESHOLD, oracle.LINK_THRESHOLD, oracle.PC])
+def test_stale_threshold_moves_use_the_previous_cash(sched):
+    """Moves 1 and 2 of the variant both take their statistics from C_1 (the
+    cash before move 1), move 3 from C_2: rebuilt from single selections
+    whose statistics cash is given explicitly."""
+    csr = synth.tiny_chain(400, seed=5)
+    p = oracle.transition_probs(csr)
+    C0, H0 = oracle.initial_step(csr, p)
+    kw = dict(theta_scale=0.5, row_ptr=csr.row_ptr, pc_frac=0.05, seed=7)
+    C, H = C0.copy(), H0.copy()
+    prev = C.copy()
+    g, th1 = oracle.select(C, sched, move=0, **kw)
+    oracle.move(csr, p, g, C, H)
+    g2, th2 = oracle.select(C, sched, move=1, cstat=prev, **kw)
+    assert th2 == th1
+    prev = C.copy()
+    oracle.move(csr, p, g2, C, H)
+    g3, _ = oracle.select(C, sched, move=2, cstat=prev, **kw)
+    oracle.move(csr, p, g3, C, H)
+    C2, H2 = C0.copy(), H0.copy()
+    info = oracle.solve(csr, p, C2, H2, sched=sched, theta_scale=0.5, pc_frac=0.05, seed=7,
+                        tol=0.0, max_steps=3, theta_lag=1)
+    assert info["status"] == "ENOCONV" and info["moves"] == 3
+    assert np.array_equal(C2, C) and np.array_equal(H2, H)
+
+
+@pytest.mark.parametrize("sched", [oracle.THRESHOLD, oracle.LINK_THRESHOLD, oracle.PC])
+def test_stale_threshold_converges_to_gth(sched):
+    csr = synth.tiny_chain(1000, seed=1)
+    p = oracle.transition_probs(csr)
+    ref = oracle.gth(oracle.dense_P(csr, p))
+    pi, C, H, info = oracle.run(csr, sched=sched, theta_scale=0.5, tol=1e-12, max_steps=200000,
+                                theta_lag=1, check_every=50)
+    assert info["status"] == "OK"
+    assert np.abs(pi - ref).sum() <= 1e-11
+    assert info["invariant"] < 1e-13 and info["l1_growth"] < 1e-15
+
+
+def test_select_statistics_cash_sets_theta_and_pc_constant():
+    """The statistics cash alone sets theta (THRESHOLD: theta scales with it)
+    and the PC normaliser (doubling it halves every p_i, so the green set
+    can only shrink for the same uniforms)."""
+    rng = np.random.default_rng(3)
+    C = rng.standard_normal(5000)
+    g1, th1 = oracle.select(C, oracle.THRESHOLD, theta_scale=1.0)
+    g2, th2 = oracle.select(C, oracle.THRESHOLD, theta_scale=1.0, cstat=3.0 * C)
+    assert th2 == pytest.approx(3.0 * th1, rel=1e-14)
+    assert np.array_equal(g2, (np.abs(C) >= th2).astype(np.uint8))
+    p1, _ = oracle.select(C, oracle.PC, pc_frac=0.2, move=4, seed=11)
+    p2, _ = oracle.select(C, oracle.PC, pc_frac=0.2, move=4, seed=11, cstat=2.0 * C)
+    assert np.all(p2 <= p1) and p2.sum() < 0.7 * p1.sum()
