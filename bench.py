@@ -314,19 +314,26 @@ class GpuRun:
         per-class (ms, launches) and the algorithmic bytes of those launches
         (from the device-side move log)."""
         ch = self.chain
+        ch.reset(self.m0)
+        ch.profile(2)
+        kt = ch.profile_moves(sched, theta, tstar)
+        log = ch.move_log(tstar)
+        return kt, self.alg_bytes(sched, log)
+
+    def alg_bytes(self, sched, log, sweep=False):
+        """Algorithmic bytes per kernel class of the logged moves (every
+        access counted once from memory). On the sweep, a move of the stale
+        threshold has no statistics pass (its log entry has no stats time)."""
         csr = self.csr
         n, nnz = csr.n, csr.nnz
         cash = 4 if self.wl["precision"] == "mixed" else 8
         wb = 4 if csr.w is not None else 0
         link = 4 if sched == "link_threshold" else 0
-        ch.reset(self.m0)
-        ch.profile(2)
-        kt = ch.profile_moves(sched, theta, tstar)
-        log = ch.move_log(tstar)
         alg = {k: 0.0 for k in KERNEL_CLASSES}
         for rec in log:
             E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
-            alg["stats"] += n * (cash + link)
+            if not (sweep and rec["phase_us"][0] == 0.0 and rec["phase_us"][1] == 0.0):
+                alg["stats"] += n * (cash + link)
             if sched == "all_green":
                 alg["select"] += n * (3 * cash + 16 + 8)
             else:
@@ -337,19 +344,19 @@ class GpuRun:
                 alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash)
             if sched == "topfrac":
                 alg["topk"] += (3 if cash == 4 else 6) * n * cash
-        return kt, alg
+        return alg
 
-    def sweep_profile(self, sched, theta, tstar, alg):
+    def sweep_profile(self, sched, theta, tstar):
         """T* moves of the persistent sweep launched eagerly, each launch
         timed with CUDA events on the context's stream; the algorithmic
-        bytes of those moves are the sum over the phases (the same moves as
-        the per-phase profile, so the same bytes)."""
+        bytes of those moves from the sweep's own move log."""
         ch = self.chain
         ch.reset(self.m0)
         ch.profile(2)
         kt = ch.profile_sweep(sched, theta, tstar)
         ch.profile(2)
         log = ch.move_log(tstar)
+        alg = self.alg_bytes(sched, log, sweep=True)
         names = ("stats", "stats_wait", "select", "select_wait", "move", "move_wait")
         ph = np.array([r["phase_us"] for r in log], dtype=np.float64)
         phases = {k: float(v) for k, v in zip(names, ph.mean(axis=0))} if len(ph) else {}
@@ -358,7 +365,7 @@ class GpuRun:
         push_rate = (sum(e for e, _ in push) / (sum(t for _, t in push) * 1e-6) / 1e9) if push else None
         return kt["sweep"], sum(alg[k] for k in ("stats", "select", "push", "pull")), phases, push_rate
 
-    def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0, r=1):
+    def e2e(self, sched, theta, tstar, steps, warmup, theta_scale=1.0, r=1, theta_lag=0):
         """Through the public API with host buffers: every step uploads the
         chain from pinned host memory (create), solves, and reads pi back."""
         torch = self.torch
@@ -378,7 +385,7 @@ class GpuRun:
             torch.cuda.synchronize(self.device)
             t0 = time.perf_counter()
             with Chain(pinned, m0=m0, precision=self.wl["precision"], stream=self.stream) as ch:
-                ch.set_params(theta_scale=theta_scale, r=r)
+                ch.set_params(theta_scale=theta_scale, r=r, theta_lag=theta_lag)
                 info = ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
                 ch.estimate(pi_host)
             t1 = time.perf_counter()
@@ -458,35 +465,40 @@ def run_gpu(args):
     head = args.sched
     order = [head] + ([] if args.skip_compare else [k for k in plan if k != head])
     r_of = {name: 1 for name in plan}
+    lag_of = {name: 0 for name in plan}
 
     def use(name):
         sched, theta, scale, cap = plan[name]
-        g.chain.set_params(theta_scale=scale, r=r_of[name])
+        g.chain.set_params(theta_scale=scale, r=r_of[name], theta_lag=lag_of[name])
         return sched, theta, cap
 
     nvtx = torch.cuda.nvtx
-    # autotuned threshold: the scale and exponent r of theta_t(r) with the
-    # least time to the error target (untimed search; the timed run below
-    # uses the winner)
+    # autotuned threshold: the scale and exponent r of theta_t(r), and on the
+    # persistent sweep the stale threshold (theta from the previous move's
+    # cash), with the least time to the error target (untimed search; the
+    # timed run below uses the winner)
     tuning = None
     if args.tune and head in ("link_threshold", "threshold"):
         nvtx.range_push("tune")
         tuning = []
         sched, theta, _, cap = plan[head]
-        for r in (1, 2):
-            for scale in (0.25, 0.35, 0.5, 0.7, 1.0):
-                g.chain.set_params(theta_scale=scale, r=r)
-                ts_, e_, _ = g.calibrate(sched, theta, ref_dev, max_moves=cap)
-                if ts_ is None:
-                    tuning.append(dict(theta_scale=scale, r=r, tstar=None))
-                    continue
-                tt, _ = g.timed_solves(sched, theta, ts_, 3, 1)
-                tuning.append(dict(theta_scale=scale, r=r, tstar=ts_, ms=float(np.median(tt))))
+        for lag in ((0, 1) if args.persistent == 1 else (0,)):
+            for r in (1, 2):
+                for scale in (0.25, 0.35, 0.5, 0.7, 1.0):
+                    g.chain.set_params(theta_scale=scale, r=r, theta_lag=lag)
+                    ts_, e_, _ = g.calibrate(sched, theta, ref_dev, max_moves=cap)
+                    if ts_ is None:
+                        tuning.append(dict(theta_scale=scale, r=r, theta_lag=lag, tstar=None))
+                        continue
+                    tt, _ = g.timed_solves(sched, theta, ts_, 3, 1)
+                    tuning.append(dict(theta_scale=scale, r=r, theta_lag=lag, tstar=ts_,
+                                       ms=float(np.median(tt))))
         done = [t for t in tuning if t.get("ms")]
         if done:
             best = min(done, key=lambda t: t["ms"])
             plan[head] = (sched, theta, best["theta_scale"], cap)
             r_of[head] = best["r"]
+            lag_of[head] = best["theta_lag"]
         nvtx.range_pop()
     cal = {}
     nvtx.range_push("calibrate")
@@ -505,24 +517,25 @@ def run_gpu(args):
     # stream): per phase on the one-kernel-per-phase path, then the
     # persistent sweep that the timed solves run
     sched_h, theta_h, _ = use(head)
-    g.chain.set_params(persistent=0)
+    # (the one-kernel-per-phase path has no stale threshold)
+    g.chain.set_params(persistent=0, theta_lag=0)
     nvtx.range_push("profile")
     kt, alg = g.kernel_profile(sched_h, theta_h, tstar)
     nvtx.range_pop()
-    g.chain.set_params(persistent=args.persistent)
+    g.chain.set_params(persistent=args.persistent, theta_lag=lag_of[head])
     sweep_on = args.persistent == 1 and head != "topfrac"
     push_rate = None
     if sweep_on:
         nvtx.range_push("profile_sweep")
-        (ms_sw, n_sw), bytes_sw, sweep_phases, push_rate = g.sweep_profile(sched_h, theta_h, tstar, alg)
+        (ms_sw, n_sw), bytes_sw, sweep_phases, push_rate = g.sweep_profile(sched_h, theta_h, tstar)
         nvtx.range_pop()
     # the headline schedule on the one-kernel-per-phase path, for comparison
     phase_ms = None
     if sweep_on and not args.skip_compare:
-        g.chain.set_params(persistent=0)
+        g.chain.set_params(persistent=0, theta_lag=0)
         ts, _ = g.timed_solves(sched_h, theta_h, tstar, max(3, args.steps // 2), 3)
         phase_ms = float(np.median(ts))
-        g.chain.set_params(persistent=1)
+        g.chain.set_params(persistent=1, theta_lag=lag_of[head])
 
     # comparison schedules, timed the same way
     compare = {}
@@ -565,7 +578,8 @@ def run_gpu(args):
     if args.no_e2e:
         et, ep, h2d, d2h = [float("nan")], [0], 0, 0
     else:
-        et, ep, h2d, d2h = g.e2e(sched_h, theta_h, tstar, max(3, args.steps // 2), 1, plan[head][2], r_of[head])
+        et, ep, h2d, d2h = g.e2e(sched_h, theta_h, tstar, max(3, args.steps // 2), 1, plan[head][2], r_of[head],
+                                 lag_of[head])
     e2e_t = max_over_ranks(dist, float(np.sum(et)), device)
     e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
 
@@ -598,6 +612,7 @@ def run_gpu(args):
         "data": "synthetic (seeded R-MAT; stands in for the paper's web graphs)",
         "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
                    "schedule": head, "theta_scale": plan[head][2], "r": r_of[head],
+                   "theta_lag": lag_of[head],
                    "autotuned": tuning is not None, "precision": wl["precision"],
                    "tstar_moves": tstar,
                    "l2": "flushed between timed steps (512 MB write)",
@@ -611,7 +626,7 @@ def run_gpu(args):
         "persistent_sweep": sweep_on,
         "tuning": tuning,
         "sweep_phase_us_per_move": sweep_phases if sweep_on else None,
-        "time_to_err_ms_phase_kernels": phase_ms,
+        "time_to_err_ms_phase_kernels": phase_ms,  # same moves, fresh threshold
         "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
         "final_l1_err": final_err,
         "reference": ref_info,

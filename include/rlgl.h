@@ -123,6 +123,16 @@ typedef struct {
     int32_t stall_moves;    /* MIXED only: re-derive the cash also when ||C||_1 has not fallen
                                below its value of this many moves ago (FP32 rounding floor, e.g.
                                in a node with a million in-links); 0 = off (default 32) */
+    int32_t theta_lag;      /* 1: stale threshold, one move old (Sec. 6 lets RLGL_Theta's
+                               threshold be updated less often). The first move of a solve call
+                               is as with 0; every later move takes theta (and ||C||_1 for PC)
+                               from the cash before the previous move, computes its own cash's
+                               statistics while it selects, and is made whatever its stop test
+                               says (the call stops after it; solve_info.resid is then
+                               ||C_t||_1 / |H_{t+1} 1|). Saves the statistics pass and one grid
+                               barrier per move. Persistent sweep only: rlgl_solve returns
+                               RLGL_EINVAL for TOPFRAC, batches and persistent = 0; rlgl_step
+                               and rlgl_profile_moves ignore it. Default 0 */
 } rlgl_params;
 
 typedef struct {

@@ -531,6 +531,7 @@ static void fill_control(rlgl_ctx* ctx, Control* c, int sched, double theta, dou
     c->barrier_limit_ns = (unsigned long long)(ctx->params.barrier_limit_s * 1e9);
     c->test_skip_barrier = ctx->params.test_skip_barrier;
     c->stall_moves = ctx->params.stall_moves;
+    c->theta_lag = solving ? ctx->params.theta_lag : 0;
     c->sched = sched;
     c->r = ctx->params.r;
     c->safety_every = solving ? ctx->params.safety_every : 0;
@@ -812,6 +813,7 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->barrier_limit_s = 2.0;
     p->test_skip_barrier = 0;
     p->stall_moves = 32;
+    p->theta_lag = 0;
     return RLGL_OK;
 }
 
@@ -1206,6 +1208,8 @@ static rlgl_status solve_launch(rlgl_ctx* ctx, rlgl_schedule sched, double theta
         sweep = false;
         cudaGetLastError();
     }
+    if (!sweep && ctx->params.theta_lag)
+        return fail(ctx, RLGL_EINVAL, "theta_lag needs the persistent sweep (not TOPFRAC, batches or persistent = 0)");
     if (!sweep && !ctx->graph[sched]) TRY(build_graph(ctx, sched));
     TRY(begin(ctx, sched, theta, batch_tols ? 0.0 : tol, max_steps, 1, batch_tols ? -1.0 : tol));
     if (sweep) CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
@@ -1373,7 +1377,8 @@ rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
         !(p->pull_crossover >= 0.0) || p->safety_every < 0 || !(p->refresh_factor >= 0.0 && p->refresh_factor < 1.0) ||
         !(p->time_limit_s > 0.0) || (p->persistent != 0 && p->persistent != 1) || p->rr_blocks < 1 ||
         !(p->pc_frac > 0.0 && p->pc_frac <= 1e30) || !(p->barrier_limit_s > 0.0 && p->barrier_limit_s <= 60.0) ||
-        (p->test_skip_barrier != 0 && p->test_skip_barrier != 1) || p->stall_moves < 0)
+        (p->test_skip_barrier != 0 && p->test_skip_barrier != 1) || p->stall_moves < 0 ||
+        (p->theta_lag != 0 && p->theta_lag != 1))
         return fail(ctx, RLGL_EINVAL, "parameter out of range");
     ctx->params = *p;
     return RLGL_OK;

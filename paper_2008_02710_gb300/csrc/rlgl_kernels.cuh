@@ -101,7 +101,8 @@ struct Control {
     int solving;             // 1: solve (stop tests active), 0: single step
     int mixed;               // MIXED precision path
     int n_masks;
-    int pad[2];
+    int theta_lag;           // persistent sweep: theta from the previous move's cash
+    int pad[1];
 };
 
 struct DevState {
@@ -176,6 +177,28 @@ __device__ __forceinline__ T block_sum(T v, T* scratch) {
         s = warp_sum(s);
     }
     return s;
+}
+
+// K block sums at once (two barriers in all); thread 0 receives the totals
+// in v. scratch holds K * 32 values.
+template <typename T, int K>
+__device__ __forceinline__ void block_sum_n(T (&v)[K], T* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[k * 32 + wid] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T x = (lane < (int)(blockDim.x >> 5)) ? scratch[k * 32 + lane] : T(0);
+            v[k] = warp_sum(x);
+        }
+    }
 }
 
 // Block-wide exclusive scan of 64-bit values (blockDim = kThreads). Returns

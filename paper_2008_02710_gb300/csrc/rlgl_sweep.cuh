@@ -163,13 +163,25 @@ struct SelSmem {
 // memory) the frontier slots follow node order within each warp, so a
 // warp's frontier writes are contiguous; beyond, each thread's green nodes
 // take consecutive slots. Returns the block's sums of m_i and |m_i| in
-// thread 0.
+// thread 0. With acc_stats (the stale threshold), also the block's sums of
+// the statistics of the cash before the move, from the same loads:
+// ba = sum |C_i| and bpr = sum v_i^r as the statistics pass forms them
+// (v_i = |C_i| / d_i when link, else |C_i|; bpr stays 0 for r = 1 without
+// link, whose sum is ba).
+// x^r for the rare exponents r > 2, out of line so that the select loop
+// does not carry pow's registers.
+template <typename T>
+__device__ __noinline__ T pow_r(T x, int r) {
+    return pow(x, (T)r);
+}
+
 template <typename T>
 __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T th,
                                              const unsigned char* mask, const SchedAux& ax,
-                                             SweepSlot* sl, SelSmem<T>& cs, double& bmsum,
-                                             double& bmabs) {
-    __shared__ T tscratch[32];
+                                             SweepSlot* sl, SelSmem<T>& cs, bool acc_stats,
+                                             bool link, int r, double& bmsum, double& bmabs,
+                                             double& ba, double& bpr) {
+    __shared__ T tscratch[4 * 32];
     __shared__ unsigned long long base_sh, cached_sh;
     // rows with many push chunks: their chunk starts are written by the
     // whole block after the second pass instead of by one thread
@@ -179,7 +191,24 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
     __shared__ long long s_long[kLongRows][3];  // frontier row, first chunk, end chunk
     const int n = A.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T msum = T(0), mabs = T(0);
+    T msum = T(0), mabs = T(0), sa = T(0), spr = T(0);
+    // the statistics pass's terms (stats_slice)
+    auto stat = [&](T v, T idg) {
+        const T av = fabs(v);
+        sa += av;
+        const T tv = link ? av * idg : av;
+        if (link && r == 1) spr += tv;
+        else if (r == 2) spr += tv * tv;
+        else if (r > 2) spr += pow_r(tv, r);
+    };
+    auto finish = [&]() {
+        T v4[4] = {msum, mabs, sa, spr};
+        block_sum_n<T, 4>(v4, tscratch);
+        bmsum = (double)v4[0];
+        bmabs = (double)v4[1];
+        ba = (double)v4[2];
+        bpr = (double)v4[3];
+    };
     if (sched == SCHED_ALL_GREEN) {
         // every node moves; the pull needs no frontier
         for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
@@ -189,6 +218,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 const long long i = it0 + q * kThreads + threadIdx.x;
                 if (i >= n) continue;
                 const T v = __ldcg(A.c + i);
+                if (acc_stats) stat(v, link ? __ldg(A.ideg + i) : T(0));
                 A.c[i] = T(0);
                 red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
@@ -196,8 +226,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 A.mt[i] = moved_per_weight(v, A.s, A.sf, i);
             }
         }
-        bmsum = (double)block_sum(msum, tscratch);
-        bmabs = (double)block_sum(mabs, tscratch);
+        finish();
         return;
     }
     if ((long long)n > (long long)gridDim.x * kSelCached) {
@@ -224,6 +253,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 const long long i = it0 + q * kThreads + threadIdx.x;
                 g[q] = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
                 if (g[q]) mine += ((unsigned long long)rdeg[q] << kCountBits) + 1ull;
+                if (acc_stats && i < n) stat(val[q], idg[q]);
             }
             unsigned long long total;
             const unsigned long long pre = block_exscan(mine, &total);
@@ -258,8 +288,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             }
             __syncthreads();  // base_sh is rewritten by the next iteration
         }
-        bmsum = (double)block_sum(msum, tscratch);
-        bmabs = (double)block_sum(mabs, tscratch);
+        finish();
         return;
     }
     // pass 1: count (per warp and group for the cached nodes, per thread beyond)
@@ -283,6 +312,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         for (int q = 0; q < kNodesPerThread; ++q) {
             const long long i = it0 + q * kThreads + threadIdx.x;
             const bool g = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
+            if (acc_stats && i < n) stat(val[q], idg[q]);
             const unsigned long long pk = g ? ((unsigned long long)rdeg[q] << kCountBits) + 1ull : 0ull;
             if (j < kSelCachedIters) {
                 const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
@@ -402,11 +432,10 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
     }
     __syncthreads();
     const int nlong = s_nlong < kLongRows ? s_nlong : kLongRows;
-    for (int r = 0; r < nlong; ++r)
-        for (long long b = s_long[r][1] + threadIdx.x; b < s_long[r][2]; b += blockDim.x)
-            A.chunk_row[b] = (int)s_long[r][0];
-    bmsum = (double)block_sum(msum, tscratch);
-    bmabs = (double)block_sum(mabs, tscratch);
+    for (int q = 0; q < nlong; ++q)
+        for (long long b = s_long[q][1] + threadIdx.x; b < s_long[q][2]; b += blockDim.x)
+            A.chunk_row[b] = (int)s_long[q][0];
+    finish();
 }
 
 template <typename T>
@@ -437,7 +466,42 @@ struct SweepCtl {
     unsigned long long ts[7];  // block 0: move start, then arrival / release at each barrier
     SchedAux ax;       // this move's block-round-robin range and PC constants
     long long mask_off;  // MASK: offset of this move's mask
+    // stale threshold: the statistics of the cash before the last move
+    double lag_l1, lag_sumr;
+    unsigned long long lag_now;  // block 0's timer when they were taken
+    int have_lag;      // a move of this launch has set them
+    int stop_after;    // status to stop with after this move (-1: none)
 };
+
+// This move's schedule, threshold and schedule constants from the
+// statistics l1 = ||C||_1 and sumr = sum v^r (thread 0; the same in every
+// block).
+__device__ __forceinline__ void sweep_theta(SweepCtl& sc, const Control& ctl, int n, double l1, double sumr) {
+    const int r = ctl.r;
+    int sched = ctl.sched;
+    if (ctl.safety_every > 0 && ((sc.solve_moves + 1) % ctl.safety_every) == 0) sched = SCHED_ALL_GREEN;
+    double theta = 0.0;
+    if (sched == SCHED_THRESHOLD || sched == SCHED_LINK) {
+        const double mean = sumr / (double)n;
+        theta = ctl.theta_arg > 0.0 ? ctl.theta_arg
+                                    : (r == 1 ? ctl.theta_scale * mean : ctl.theta_scale * pow(mean, 1.0 / r));
+    }
+    sc.sched = sched;
+    sc.theta = theta;
+    sc.ax = sched_aux(ctl, n, sc.moves, l1, sched);
+    sc.mask_off = (sched == SCHED_MASK) ? (sc.mask_cursor % ctl.n_masks) * (long long)n : 0;
+    sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+}
+
+__device__ __forceinline__ void clear_slot(SweepSlot* o) {
+    o->a = 0.0;
+    o->s = 0.0;
+    o->pr = 0.0;
+    o->msum = 0.0;
+    o->mabs = 0.0;
+    o->reserve = 0ull;
+    o->chunk_next = 0ull;
+}
 
 template <typename T, bool kHasW>
 __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T> A) {
@@ -484,6 +548,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         const unsigned long long arr = ld_acquire_u64(&sw->bar.arrived);
         sc.target = arr - arr % gridDim.x;
         sc.p = (int)(sw->bar.parity & 1u);
+        sc.have_lag = 0;
+        sc.stop_after = -1;
     }
     __syncthreads();
     // Test of the bounded wait: the last block leaves without arriving, so
@@ -493,6 +559,12 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
     for (;;) {
         SweepSlot* sl = &sw->slot[sc.p];
         if (lead) sc.ts[0] = globaltimer();
+        // A move of the stale threshold (after the first of the launch)
+        // skips the statistics pass and its barrier: its select takes the
+        // statistics of the cash before the previous move and gathers its
+        // own cash's for the stop test.
+        const bool lagged = ctl.theta_lag && sc.have_lag;
+        if (!lagged) {
         // ---------------------------------------------------------- stats
         {
             const bool link = ctl.sched == SCHED_LINK;
@@ -514,16 +586,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
 
         // -------------------------------------------------------- control
         if (threadIdx.x == 0) {
-            if (blockIdx.x == 0) {
-                SweepSlot* o = &sw->slot[sc.p ^ 1];
-                o->a = 0.0;
-                o->s = 0.0;
-                o->pr = 0.0;
-                o->msum = 0.0;
-                o->mabs = 0.0;
-                o->reserve = 0ull;
-                o->chunk_next = 0ull;
-            }
+            if (blockIdx.x == 0) clear_slot(&sw->slot[sc.p ^ 1]);
             const int r = ctl.r;
             const bool link = ctl.sched == SCHED_LINK;
             const double l1 = __ldcg(&sl->a), sum = __ldcg(&sl->s);
@@ -556,21 +619,11 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 want_refresh = true;  // after this move
             sc.leave = (stop >= 0 || skip) ? 1 : 0;
             sc.want_refresh = want_refresh ? 1 : 0;
-            int sched = ctl.sched;
-            if (ctl.safety_every > 0 && ((sc.solve_moves + 1) % ctl.safety_every) == 0)
-                sched = SCHED_ALL_GREEN;
-            double theta = 0.0;
-            if (sched == SCHED_THRESHOLD || sched == SCHED_LINK) {
-                const double mean = sumr / (double)n;
-                theta = ctl.theta_arg > 0.0 ? ctl.theta_arg
-                                            : (r == 1 ? ctl.theta_scale * mean
-                                                      : ctl.theta_scale * pow(mean, 1.0 / r));
-            }
-            sc.sched = sched;
-            sc.theta = theta;
-            sc.ax = sched_aux(ctl, n, sc.moves, l1, sched);
-            sc.mask_off = (sched == SCHED_MASK) ? (sc.mask_cursor % ctl.n_masks) * (long long)n : 0;
-            sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+            sweep_theta(sc, ctl, n, l1, sumr);
+            // the next move of the stale threshold takes these statistics
+            sc.lag_l1 = l1;
+            sc.lag_sumr = sumr;
+            sc.lag_now = now;
             if (blockIdx.x == 0) {
                 st->l1 = l1;
                 st->sum = sum;
@@ -598,6 +651,38 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         }
         __syncthreads();
         if (sc.leave) return;
+        } else {
+        // ------------------------------------- control (stale threshold)
+        // the tests that need no new statistics, the threshold from the
+        // previous move's
+        if (lead) sc.ts[1] = sc.ts[2] = sc.ts[0];
+        if (threadIdx.x == 0) {
+            sc.iters++;
+            int stop = -1;
+            const bool degenerate = !(fabs(sc.hsum) > 1e-12 * sc.habs) || sc.habs == 0.0;
+            if (degenerate) stop = ST_DEGENERATE;
+            else if (sc.solve_moves >= ctl.max_steps) stop = ST_NOCONV;
+            else if ((double)(sc.lag_now - sc.t_start) > ctl.time_limit_ns || sc.iters > ctl.max_iters)
+                stop = ST_TIMEOUT;
+            sc.leave = stop >= 0 ? 1 : 0;
+            sc.want_refresh = 0;
+            sweep_theta(sc, ctl, n, sc.lag_l1, sc.lag_sumr);
+            if (blockIdx.x == 0 && stop >= 0) {
+                // this move's slot is still clear: the next launch may take it
+                st->iters = sc.iters;
+                st->mode = MODE_NONE;
+                sw->bar.parity = (unsigned int)sc.p;
+                st->done = 1;
+                st->status = stop;
+                if (A.use_cond) {
+                    cudaGraphSetConditional(A.cond_loop, 0u);
+                    if (ctl.mixed) cudaGraphSetConditional(A.cond_refresh, 0u);
+                }
+            }
+        }
+        __syncthreads();
+        if (sc.leave) return;
+        }
 
         // --------------------------------------------------------- select
         {
@@ -605,11 +690,17 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             const T th = kF32 ? (T)sc.theta_f : (T)sc.theta;
             const unsigned char* mask = (sched == SCHED_MASK) ? A.masks + sc.mask_off : nullptr;
             const SchedAux& ax = sc.ax;
-            double bmsum, bmabs;
-            sweep_select<T>(A, sched, th, mask, ax, sl, sm.sel, bmsum, bmabs);
+            double bmsum, bmabs, ba, bpr;
+            const bool link = ctl.sched == SCHED_LINK;
+            sweep_select<T>(A, sched, th, mask, ax, sl, sm.sel, lagged, link, ctl.r, bmsum, bmabs, ba, bpr);
             if (threadIdx.x == 0) {
                 if (bmsum != 0.0) atomicAdd(&sl->msum, bmsum);
                 if (bmabs != 0.0) atomicAdd(&sl->mabs, bmabs);
+                if (lagged) {
+                    if (ba != 0.0) atomicAdd(&sl->a, ba);
+                    if (bpr != 0.0) atomicAdd(&sl->pr, bpr);
+                    if (blockIdx.x == 0) sl->tstamp = globaltimer();
+                }
             }
         }
         if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr)) break;
@@ -625,6 +716,41 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 edges = ctl.nnz;
             }
             const double ms = __ldcg(&sl->msum), ma = __ldcg(&sl->mabs);
+            if (lagged) {
+                // stop test and re-derivation triggers on this move's cash
+                // C_t (gathered by the select), against H_t 1; the move is
+                // made whatever they say
+                const int r = ctl.r;
+                const bool link = ctl.sched == SCHED_LINK;
+                const double l1 = __ldcg(&sl->a);
+                const double sumr = (r == 1 && !link) ? l1 : __ldcg(&sl->pr);
+                const unsigned long long now = __ldcg(&sl->tstamp);
+                const bool converged = sc.moves >= 1 && l1 / fabs(sc.hsum) < ctl.tol;
+                bool want_refresh = false;
+                if (converged) {
+                    if (ctl.mixed && !sc.fresh) want_refresh = true;  // re-derive, then test again
+                    else sc.stop_after = ST_OK;
+                } else if (ctl.mixed &&
+                           ((ctl.refresh_factor > 0.0 && l1 < ctl.refresh_factor * s_l1_refresh) ||
+                            cash_stalled(l1, sc.stall_mark, sc.stall_count, ctl.stall_moves))) {
+                    want_refresh = true;
+                }
+                sc.want_refresh = want_refresh ? 1 : 0;
+                sc.l1 = l1;
+                sc.lag_l1 = l1;
+                sc.lag_sumr = sumr;
+                sc.lag_now = now;
+                if (blockIdx.x == 0) {
+                    st->l1 = l1;
+                    st->sumr = sumr;
+                    st->iters = sc.iters;
+                    st->stall_mark = sc.stall_mark;
+                    st->stall_count = sc.stall_count;
+                    // every block is done with the other slot (the last move's)
+                    clear_slot(&sw->slot[sc.p ^ 1]);
+                }
+            }
+            if (ctl.theta_lag) sc.have_lag = 1;
             sc.hsum += ms;
             sc.habs += ma;
             sc.moves++;
@@ -691,6 +817,19 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
             rec->phase_us[4] = (float)(sc.ts[5] - sc.ts[4]) * 1e-3f;
             rec->phase_us[5] = (float)(sc.ts[6] - sc.ts[5]) * 1e-3f;
+        }
+        if (sc.stop_after >= 0) {
+            if (lead) {
+                st->done = 1;
+                st->status = sc.stop_after;
+                st->mode = MODE_NONE;
+                sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                if (A.use_cond) {
+                    cudaGraphSetConditional(A.cond_loop, 0u);
+                    if (ctl.mixed) cudaGraphSetConditional(A.cond_refresh, 0u);
+                }
+            }
+            return;
         }
         if (sc.want_refresh) {
             if (lead) {

@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
                 ("time_limit_s", ctypes.c_double), ("rr_blocks", ctypes.c_int64),
                 ("pc_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("persistent", ctypes.c_int32), ("barrier_limit_s", ctypes.c_double),
-                ("test_skip_barrier", ctypes.c_int32), ("stall_moves", ctypes.c_int32)]
+                ("test_skip_barrier", ctypes.c_int32), ("stall_moves", ctypes.c_int32),
+                ("theta_lag", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):

@@ -61,3 +61,24 @@ def test_torch_tensor_with_numpy_dtype_is_converted():
     p, sp, keep = rlgl._ptr(t, np.float64)
     assert sp == rlgl.HOST and keep.dtype == torch.float64 and p == keep.data_ptr()
     assert keep.tolist() == [0.0, 1.0, 2.0, 3.0]
+
+
+def _struct_fields(name):
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return re.findall(r"\b(int32_t|int64_t|uint64_t|double|float)\s+(\w+)(\[\d+\])?\s*;", body)
+
+
+def test_params_struct_matches_header():
+    """The binding's rlgl_params has the header's fields in the header's
+    order and types (the struct crosses the ABI by value)."""
+    import ctypes
+    from paper_2008_02710_gb300 import rlgl
+    ctype = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+             "double": ctypes.c_double, "float": ctypes.c_float}
+    want = [(n, ctype[t]) for t, n, _ in _struct_fields("rlgl_params")]
+    got = [(n, t) for n, t in rlgl.Params._fields_]
+    assert got == want
+    p = rlgl.default_params()
+    assert p.theta_lag == 0 and p.stall_moves == 32 and p.persistent == 1
