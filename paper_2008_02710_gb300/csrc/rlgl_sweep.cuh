@@ -32,19 +32,29 @@ constexpr int ST_BARRIER = 9;
 // Per-move accumulators, zero at rest. Two slots alternate: the slot of
 // move t is cleared by block 0 during move t + 1, after the first barrier,
 // when every block has finished reading it.
-struct SweepSlot {
-    double a, s, pr;             // ||C||_1, sum C, sum v^r of the cash
+// Each slot and the barrier sit on their own 128-byte lines (the blocks'
+// atomics on one do not queue behind the polls of the other), and the
+// fields read together after a barrier are pairs in 16 bytes: one request
+// per pair.
+struct alignas(128) SweepSlot {
+    double a, pr;                // ||C||_1, sum v^r of the cash
     double msum, mabs;           // sum m_i, sum |m_i| of the moved cash
     unsigned long long reserve;  // packed frontier reservation
-    unsigned long long tstamp;   // block 0's timer at the end of its stats
+    unsigned long long tstamp;   // block 0's timer at the end of its stats (or select)
+    double s;                    // sum C
     unsigned long long chunk_next;  // next push chunk to hand out
 };
 
-struct GridBar {
+struct alignas(128) GridBar {
     unsigned long long arrived;  // arrivals since the solve began (grid size per barrier)
     unsigned int abort;          // a wait gave up: every block leaves
     unsigned int parity;         // slot of the next move (kept across launches)
 };
+
+// The two 8-byte fields at p (16-byte aligned), read from L2 in one request.
+__device__ __forceinline__ double2 ldcg_pair(const void* p) {
+    return __ldcg(reinterpret_cast<const double2*>(p));
+}
 
 struct SweepState {
     GridBar bar;
@@ -70,6 +80,56 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // limit_ns. Returns false (in every thread of the block) when the sweep must
 // stop. When ts is given, thread 0 stores its arrival and release times in
 // ts[0], ts[1].
+// Thread 0: the arrival half of grid_barrier.
+__device__ __forceinline__ void bar_arrive(GridBar* bar, unsigned long long& target) {
+    target += gridDim.x;
+    __threadfence();
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(&bar->arrived) : "memory");
+}
+
+// Thread 0: the waiting half of grid_barrier; returns 0 when the sweep
+// must stop.
+__device__ __forceinline__ int bar_wait(GridBar* bar, unsigned long long target,
+                                        unsigned long long limit_ns) {
+    int ok = 1;
+    const unsigned long long t0 = globaltimer();
+    unsigned int spins = 0;
+    while (ld_acquire_u64(&bar->arrived) < target) {
+        if ((++spins & 15u) == 0u) {
+            if (ld_acquire_u32(&bar->abort)) {
+                ok = 0;
+                break;
+            }
+            if (globaltimer() - t0 > limit_ns) {
+                atomicExch(&bar->abort, 1u);
+                ok = 0;
+                break;
+            }
+        }
+        __nanosleep(32);
+    }
+    return ok;
+}
+
+// As grid_barrier, with `work` run by thread 0 between its arrival and its
+// wait (off the critical path unless this block arrives last).
+template <typename F>
+__device__ __forceinline__ bool grid_barrier_with(GridBar* bar, unsigned long long& target,
+                                                  unsigned long long limit_ns, unsigned long long* ts,
+                                                  F&& work) {
+    __shared__ int s_ok2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ts) ts[0] = globaltimer();
+        bar_arrive(bar, target);
+        work();
+        s_ok2 = bar_wait(bar, target, limit_ns);
+        if (ts) ts[1] = globaltimer();
+    }
+    __syncthreads();
+    return s_ok2 != 0;
+}
+
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned long long& target,
                                              unsigned long long limit_ns,
                                              unsigned long long* ts = nullptr) {
@@ -471,6 +531,8 @@ struct SweepCtl {
     unsigned long long lag_now;  // block 0's timer when they were taken
     int have_lag;      // a move of this launch has set them
     int stop_after;    // status to stop with after this move (-1: none)
+    int lag_stop;      // stale threshold: the next move's stop before it selects (-1: none)
+    int pre_done;      // the next move's decisions are taken (sweep_lag_control)
 };
 
 // This move's schedule, threshold and schedule constants from the
@@ -491,6 +553,26 @@ __device__ __forceinline__ void sweep_theta(SweepCtl& sc, const Control& ctl, in
     sc.ax = sched_aux(ctl, n, sc.moves, l1, sched);
     sc.mask_off = (sched == SCHED_MASK) ? (sc.mask_cursor % ctl.n_masks) * (long long)n : 0;
     sc.theta_f = (sched == SCHED_LINK) ? __double2float_rn(theta) : __double2float_ru(theta);
+}
+
+// The decisions of a move of the stale threshold that need no new
+// statistics (thread 0): degenerate history, max_steps, time; the threshold
+// from the statistics of the cash before the previous move. Every input is
+// known once the previous move has read its totals, so this runs while the
+// block waits at that move's last barrier.
+__device__ __forceinline__ void sweep_lag_control(SweepCtl& sc, const Control& ctl, int n) {
+    sc.iters++;
+    int stop = -1;
+    const bool degenerate = !(fabs(sc.hsum) > 1e-12 * sc.habs) || sc.habs == 0.0;
+    if (degenerate) stop = ST_DEGENERATE;
+    else if (sc.solve_moves >= ctl.max_steps) stop = ST_NOCONV;
+    else if ((double)(sc.lag_now - sc.t_start) > ctl.time_limit_ns || sc.iters > ctl.max_iters)
+        stop = ST_TIMEOUT;
+    sc.lag_stop = stop;
+    sc.leave = stop >= 0 ? 1 : 0;
+    sc.want_refresh = 0;
+    sweep_theta(sc, ctl, n, sc.lag_l1, sc.lag_sumr);
+    sc.pre_done = 1;
 }
 
 __device__ __forceinline__ void clear_slot(SweepSlot* o) {
@@ -550,6 +632,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         sc.p = (int)(sw->bar.parity & 1u);
         sc.have_lag = 0;
         sc.stop_after = -1;
+        sc.pre_done = 0;
     }
     __syncthreads();
     // Test of the bounded wait: the last block leaves without arriving, so
@@ -589,10 +672,13 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             if (blockIdx.x == 0) clear_slot(&sw->slot[sc.p ^ 1]);
             const int r = ctl.r;
             const bool link = ctl.sched == SCHED_LINK;
-            const double l1 = __ldcg(&sl->a), sum = __ldcg(&sl->s);
-            const double sumr = (r == 1 && !link) ? l1 : __ldcg(&sl->pr);
+            const double2 apr = ldcg_pair(&sl->a);
+            const double2 rts = ldcg_pair(&sl->reserve);
+            const double sum = __ldcg(&sl->s);
+            const double l1 = apr.x;
+            const double sumr = (r == 1 && !link) ? l1 : apr.y;
             sc.l1 = l1;
-            const unsigned long long now = __ldcg(&sl->tstamp);
+            const unsigned long long now = (unsigned long long)__double_as_longlong(rts.y);
             if (sc.iters == 0) sc.t_start = now;
             sc.iters++;
             int stop = -1;
@@ -657,16 +743,9 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         // previous move's
         if (lead) sc.ts[1] = sc.ts[2] = sc.ts[0];
         if (threadIdx.x == 0) {
-            sc.iters++;
-            int stop = -1;
-            const bool degenerate = !(fabs(sc.hsum) > 1e-12 * sc.habs) || sc.habs == 0.0;
-            if (degenerate) stop = ST_DEGENERATE;
-            else if (sc.solve_moves >= ctl.max_steps) stop = ST_NOCONV;
-            else if ((double)(sc.lag_now - sc.t_start) > ctl.time_limit_ns || sc.iters > ctl.max_iters)
-                stop = ST_TIMEOUT;
-            sc.leave = stop >= 0 ? 1 : 0;
-            sc.want_refresh = 0;
-            sweep_theta(sc, ctl, n, sc.lag_l1, sc.lag_sumr);
+            if (!sc.pre_done) sweep_lag_control(sc, ctl, n);
+            sc.pre_done = 0;
+            const int stop = sc.lag_stop;
             if (blockIdx.x == 0 && stop >= 0) {
                 // this move's slot is still clear: the next launch may take it
                 st->iters = sc.iters;
@@ -708,23 +787,27 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         // ---------------------------------------------------- choose move
         if (threadIdx.x == 0) {
             const int sched = sc.sched;
-            const unsigned long long rsv = __ldcg(&sl->reserve);
+            // every total of the move in one round of paired loads
+            const double2 mm = ldcg_pair(&sl->msum);
+            const double2 rts = ldcg_pair(&sl->reserve);
+            const double2 apr = ldcg_pair(&sl->a);
+            const unsigned long long rsv = (unsigned long long)__double_as_longlong(rts.x);
             long long green = (long long)(rsv & ((1ull << kCountBits) - 1ull));
             long long edges = (long long)(rsv >> kCountBits);
             if (sched == SCHED_ALL_GREEN) {
                 green = n;
                 edges = ctl.nnz;
             }
-            const double ms = __ldcg(&sl->msum), ma = __ldcg(&sl->mabs);
+            const double ms = mm.x, ma = mm.y;
             if (lagged) {
                 // stop test and re-derivation triggers on this move's cash
                 // C_t (gathered by the select), against H_t 1; the move is
                 // made whatever they say
                 const int r = ctl.r;
                 const bool link = ctl.sched == SCHED_LINK;
-                const double l1 = __ldcg(&sl->a);
-                const double sumr = (r == 1 && !link) ? l1 : __ldcg(&sl->pr);
-                const unsigned long long now = __ldcg(&sl->tstamp);
+                const double l1 = apr.x;
+                const double sumr = (r == 1 && !link) ? l1 : apr.y;
+                const unsigned long long now = (unsigned long long)__double_as_longlong(rts.y);
                 const bool converged = sc.moves >= 1 && l1 / fabs(sc.hsum) < ctl.tol;
                 bool want_refresh = false;
                 if (converged) {
@@ -812,7 +895,13 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull);
-        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr)) break;
+        // the stale threshold's next move: its decisions while this block waits
+        if (!grid_barrier_with(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr,
+                               [&]() {
+                                   if (ctl.theta_lag && sc.stop_after < 0 && !sc.want_refresh)
+                                       sweep_lag_control(sc, ctl, n);
+                               }))
+            break;
         if (lead) {
             MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
             rec->phase_us[4] = (float)(sc.ts[5] - sc.ts[4]) * 1e-3f;
