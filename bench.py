@@ -466,6 +466,8 @@ def run_gpu(args):
     order = [head] + ([] if args.skip_compare else [k for k in plan if k != head])
     r_of = {name: 1 for name in plan}
     lag_of = {name: 0 for name in plan}
+    if args.persistent == 1 and head in ("link_threshold", "threshold"):
+        lag_of[head] = args.theta_lag
 
     def use(name):
         sched, theta, scale, cap = plan[name]
@@ -902,6 +904,9 @@ def main(argv=None):
     ap.add_argument("--max-moves", type=int, default=20000)
     ap.add_argument("--persistent", type=int, choices=[0, 1], default=1,
                     help="1: solves run as the persistent sweep; 0: one kernel per phase")
+    ap.add_argument("--theta-lag", type=int, choices=(0, 1), default=0,
+                    help="stale threshold (theta from the previous move's cash) for the headline "
+                         "threshold schedule when it is not autotuned")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="keep --theta-scale and r = 1 instead of autotuning the threshold")
     ap.add_argument("--autotune", action="store_true",

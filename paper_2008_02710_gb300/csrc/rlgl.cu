@@ -718,9 +718,11 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     TRY(dalloc(ctx, &ctx->log, (size_t)kLogCap));
     TRY(dalloc(ctx, &ctx->st, 1));
     TRY(dalloc(ctx, &ctx->sw, 1));
-    // the sweep reads slot fields in 16-byte pairs (pool allocations are
-    // aligned far beyond that)
-    if (((uintptr_t)ctx->sw & 15u) != 0) return fail(ctx, RLGL_ENOMEM, "sweep state not 16-byte aligned");
+    // the sweep reads slot fields in 16-byte pairs and stages the cash, 1/d
+    // and row offsets with 16-byte copies (pool allocations are aligned far
+    // beyond that)
+    if ((((uintptr_t)ctx->sw | (uintptr_t)ctx->c | (uintptr_t)ctx->ideg | (uintptr_t)ctx->row_ptr) & 15u) != 0)
+        return fail(ctx, RLGL_ENOMEM, "device buffers not 16-byte aligned");
     ctx->host_st = static_cast<DevState*>(pin_get());
     if (!ctx->host_st) return fail(ctx, RLGL_ENOMEM, "pinned host allocation failed");
     ctx->host_ctl = reinterpret_cast<Control*>(reinterpret_cast<char*>(ctx->host_st) + sizeof(DevState));

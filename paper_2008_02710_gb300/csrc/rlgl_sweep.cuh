@@ -32,16 +32,17 @@ constexpr int ST_BARRIER = 9;
 // Per-move accumulators, zero at rest. Two slots alternate: the slot of
 // move t is cleared by block 0 during move t + 1, after the first barrier,
 // when every block has finished reading it.
-// Each slot and the barrier sit on their own 128-byte lines (the blocks'
-// atomics on one do not queue behind the polls of the other), and the
-// fields read together after a barrier are pairs in 16 bytes: one request
-// per pair.
-struct alignas(128) SweepSlot {
-    double a, pr;                // ||C||_1, sum v^r of the cash
-    double msum, mabs;           // sum m_i, sum |m_i| of the moved cash
-    unsigned long long reserve;  // packed frontier reservation
+// Every group of fields that all blocks update or read at one time sits on
+// its own 128-byte line, and so does the barrier: the blocks' atomics on one
+// line do not queue behind those on another or behind the barrier's polls,
+// and the fields read together after a barrier are pairs in 16 bytes (one
+// request per pair, the pairs in parallel).
+struct SweepSlot {
+    alignas(128) double a, pr;   // ||C||_1, sum v^r of the cash
+    alignas(128) double msum, mabs;  // sum m_i, sum |m_i| of the moved cash
+    alignas(128) unsigned long long reserve;  // packed frontier reservation
     unsigned long long tstamp;   // block 0's timer at the end of its stats (or select)
-    double s;                    // sum C
+    alignas(128) double s;       // sum C
     unsigned long long chunk_next;  // next push chunk to hand out
 };
 
@@ -198,21 +199,50 @@ struct SweepArgs {
     int n_hot;
 };
 
-// Shared cache of the select phase: the first kSelCached nodes of a block
-// (two block-iterations) keep their cash, row offset, degree and test
-// result between the counting pass and the writing pass, and every warp's
-// green count and edge sum for each of its node groups there.
-constexpr int kSelCachedIters = 2;
-constexpr int kSelCached = kSelCachedIters * kNodesPerIter;
-constexpr int kSelGroups = kSelCachedIters * kNodesPerThread * (kThreads / 32);
+// Shared cache of the select phase when the chain has at most kIters
+// block-iterations (2 for FP32 cash, 1 for FP64, so that a block's static
+// shared memory stays within 48 KB): the block's node ranges (contiguous,
+// kNodesPerIter nodes each) keep their cash, 1/d, row offsets and test
+// results between the counting pass and the writing pass, and every warp's
+// green count and edge sum for each of its node groups sits there. The
+// arrays are filled by asynchronous 16-byte copies.
+constexpr int kSelRp = kNodesPerIter + 2;  // row offsets of a range (+1, padded to 16 bytes)
 template <typename T>
 struct SelSmem {
-    T val[kSelCached];
-    long long rb[kSelCached];
-    int rdeg[kSelCached];
-    unsigned char g[kSelCached];
-    unsigned long long wsum[kSelGroups];  // packed (edges << kCountBits) | count
+    static constexpr int kIters = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int kNodes = kIters * kNodesPerIter;
+    alignas(16) T val[kNodes];
+    alignas(16) T idg[kNodes];
+    alignas(16) long long rp[kIters][kSelRp];
+    unsigned char g[kNodes];
+    unsigned long long wsum[kIters * kNodesPerThread * (kThreads / 32)];  // packed (edges << kCountBits) | count
 };
+
+// Asynchronous copy of `bytes` (1..16) from global to shared memory, the
+// rest of the 16 destination bytes zero-filled; both addresses 16-byte
+// aligned. Completed by cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Copies elements [e0, e0 + count) of src (count elements of type E in
+// 16-byte pieces; the array holds `avail` elements from index 0) into dst,
+// zero past the array's end. Every thread of the block takes pieces.
+template <typename E>
+__device__ __forceinline__ void stage_range(E* dst, const E* src, long long e0, int count, long long avail) {
+    constexpr int kPer = 16 / (int)sizeof(E);
+    const int pieces = (count + kPer - 1) / kPer;
+    for (int u = threadIdx.x; u < pieces; u += blockDim.x) {
+        const long long e = e0 + (long long)u * kPer;
+        const long long left = (avail - e) * (long long)sizeof(E);
+        E* d = dst + u * kPer;
+        if (left >= 16) cp_async16(d, src + e, 16);
+        else if (left > 0) cp_async16(d, src + e, (int)left);
+        else *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
 
 // Select on this block's node slices (the single-chain form of k_select):
 // green nodes give their cash (m_i = C_i, C_i <- 0, H_i += m_i) and get
@@ -242,7 +272,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                                              bool link, int r, double& bmsum, double& bmabs,
                                              double& ba, double& bpr) {
     __shared__ T tscratch[4 * 32];
-    __shared__ unsigned long long base_sh, cached_sh;
+    __shared__ unsigned long long base_sh;
     // rows with many push chunks: their chunk starts are written by the
     // whole block after the second pass instead of by one thread
     constexpr int kLongRows = 16;
@@ -289,7 +319,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         finish();
         return;
     }
-    if ((long long)n > (long long)gridDim.x * kSelCached) {
+    if ((long long)n > (long long)gridDim.x * SelSmem<T>::kNodes) {
         // Large chains (more block-iterations than the cache holds): one pass
         // with one reservation per block-iteration, so that the nodes are
         // read once (a second pass would read them again from memory).
@@ -351,45 +381,44 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         finish();
         return;
     }
-    // pass 1: count (per warp and group for the cached nodes, per thread beyond)
-    unsigned long long mine = 0ull;
-    int j = 0;
-    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
-         it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
-        long long rb[kNodesPerThread];
-        int rdeg[kNodesPerThread];
-        T val[kNodesPerThread], idg[kNodesPerThread];
-        // every load of the group issued before any is used
+    // Cached path (n <= grid x kNodes): at most kIters ranges.
+    // Pass 1 stages every range's cash, 1/d and row offsets in shared
+    // memory at once (one round trip, no registers held), then tests and
+    // counts from there, per warp and node group.
+    const bool with_idg = sched == SCHED_LINK;
+    int nj = 0;
+    for (int j = 0; j < SelSmem<T>::kIters; ++j) {
+        const long long it0 = ((long long)blockIdx.x + (long long)j * gridDim.x) * kNodesPerIter;
+        if (it0 >= n) break;
+        ++nj;
+        stage_range<T>(cs.val + j * kNodesPerIter, A.c, it0, kNodesPerIter, n);
+        if (with_idg) stage_range<T>(cs.idg + j * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
+        stage_range<long long>(cs.rp[j], A.row_ptr, it0, kSelRp, (long long)n + 1);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int j = 0; j < nj; ++j) {
+        const long long it0 = ((long long)blockIdx.x + (long long)j * gridDim.x) * kNodesPerIter;
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
-            const long long i = it0 + q * kThreads + threadIdx.x;
-            rb[q] = (i < n) ? __ldg(A.row_ptr + i) : 0;
-            rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
-            val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
-            idg[q] = (i < n && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
-        }
-#pragma unroll
-        for (int q = 0; q < kNodesPerThread; ++q) {
-            const long long i = it0 + q * kThreads + threadIdx.x;
-            const bool g = (i < n) && green_test_v<T>(sched, val[q], idg[q], i, th, mask, ax);
-            if (acc_stats && i < n) stat(val[q], idg[q]);
-            const unsigned long long pk = g ? ((unsigned long long)rdeg[q] << kCountBits) + 1ull : 0ull;
-            if (j < kSelCachedIters) {
-                const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
-                cs.val[slot] = val[q];
-                cs.rb[slot] = rb[q];
-                cs.rdeg[slot] = rdeg[q];
-                cs.g[slot] = g ? 1 : 0;
-                const unsigned long long w = warp_sum(pk);
-                if (lane == 0) cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid] = w;
-            } else {
-                mine += pk;
-            }
+            const int loc = q * kThreads + threadIdx.x;
+            const int slot = j * kNodesPerIter + loc;
+            const long long i = it0 + loc;
+            const T v = cs.val[slot];
+            const T idg = with_idg ? cs.idg[slot] : T(0);
+            const int rdeg = (int)(cs.rp[j][loc + 1] - cs.rp[j][loc]);
+            const bool g = (i < n) && green_test_v<T>(sched, v, idg, i, th, mask, ax);
+            if (acc_stats && i < n) stat(v, idg);
+            const unsigned long long pk = g ? ((unsigned long long)rdeg << kCountBits) + 1ull : 0ull;
+            cs.g[slot] = g ? 1 : 0;
+            const unsigned long long w = warp_sum(pk);
+            if (lane == 0) cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid] = w;
         }
     }
-    const int ncached = (j < kSelCachedIters ? j : kSelCachedIters) * kNodesPerThread * (kThreads / 32);
+    const int ncached = nj * kNodesPerThread * (kThreads / 32);
     __syncthreads();
-    // exclusive prefix of the cached groups' counts, in group order (warp 0)
+    // exclusive prefix of the groups' counts in group order, and one
+    // reservation for the whole block (warp 0)
     if (wid == 0) {
         unsigned long long run = 0ull;
         for (int g0 = 0; g0 < ncached; g0 += 32) {
@@ -404,63 +433,35 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             if (gi < ncached) cs.wsum[gi] = run + x - v;
             run += __shfl_sync(0xffffffffu, x, 31);
         }
-        if (lane == 0) cached_sh = run;
+        if (lane == 0) {
+            base_sh = run ? atomicAdd(&sl->reserve, run) : 0ull;
+            s_nlong = 0;
+        }
     }
-    // one reservation for the whole block
-    unsigned long long total;
-    const unsigned long long pre = block_exscan(mine, &total);  // synchronises
-    if (threadIdx.x == 0) {
-        const unsigned long long all = total + cached_sh;
-        base_sh = all ? atomicAdd(&sl->reserve, all) : 0ull;
-    }
-    if (threadIdx.x == 0) s_nlong = 0;
     __syncthreads();
     const unsigned long long base = base_sh;
-    // pass 2: write
-    long long k = (long long)((base + cached_sh + pre) & ((1ull << kCountBits) - 1ull));
-    long long e = (long long)((base + cached_sh + pre) >> kCountBits);
-    j = 0;
-    for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
-         it0 += (long long)gridDim.x * kNodesPerIter, ++j) {
-        const bool cached = j < kSelCachedIters;
+    // pass 2: write (frontier slots in node order within each warp)
+    for (int j = 0; j < nj; ++j) {
+        const long long it0 = ((long long)blockIdx.x + (long long)j * gridDim.x) * kNodesPerIter;
 #pragma unroll
         for (int q = 0; q < kNodesPerThread; ++q) {
-            const long long i = it0 + q * kThreads + threadIdx.x;
-            T v = T(0);
-            long long rb = 0;
-            int rdeg = 0;
-            bool g = false;
-            long long kk = 0, ee = 0;
-            if (cached) {
-                const int slot = j * kNodesPerIter + q * kThreads + threadIdx.x;
-                v = cs.val[slot];
-                rb = cs.rb[slot];
-                rdeg = cs.rdeg[slot];
-                g = cs.g[slot] != 0;
-                // slots in node order within the warp
-                const unsigned int bal = __ballot_sync(0xffffffffu, g);
-                long long x = g ? (long long)rdeg : 0ll;
+            const int loc = q * kThreads + threadIdx.x;
+            const int slot = j * kNodesPerIter + loc;
+            const long long i = it0 + loc;
+            const T v = cs.val[slot];
+            const long long rb = cs.rp[j][loc];
+            const int rdeg = (int)(cs.rp[j][loc + 1] - rb);
+            const bool g = cs.g[slot] != 0;
+            const unsigned int bal = __ballot_sync(0xffffffffu, g);
+            long long x = g ? (long long)rdeg : 0ll;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const long long y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                const unsigned long long wb =
-                    base + cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid];
-                kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
-                ee = (long long)(wb >> kCountBits) + x - (g ? (long long)rdeg : 0ll);
-            } else if (i < n) {
-                rb = __ldg(A.row_ptr + i);
-                rdeg = (int)(__ldg(A.row_ptr + i + 1) - rb);
-                v = __ldcg(A.c + i);
-                g = green_test<T>(sched, v, i, th, mask, A.ideg, ax);
-                kk = k;
-                ee = e;
-                if (g) {
-                    ++k;
-                    e += rdeg;
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
+            const unsigned long long wb = base + cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid];
+            const long long kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
+            const long long ee = (long long)(wb >> kCountBits) + x - (g ? (long long)rdeg : 0ll);
             if (i >= n) continue;
             if (g) {
                 const T mtil = moved_per_weight(v, A.s, A.sf, i);
@@ -474,16 +475,16 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 A.f_m[kk] = mtil;
                 const long long b0 = (ee + kPushChunk - 1) / kPushChunk;
                 const long long b1 = (ee + rdeg + kPushChunk - 1) / kPushChunk;
-                int slot = -1;
+                int ls = -1;
                 if (b1 - b0 > kLongChunks) {
-                    slot = atomicAdd(&s_nlong, 1);
-                    if (slot < kLongRows) {
-                        s_long[slot][0] = kk;
-                        s_long[slot][1] = b0;
-                        s_long[slot][2] = b1;
+                    ls = atomicAdd(&s_nlong, 1);
+                    if (ls < kLongRows) {
+                        s_long[ls][0] = kk;
+                        s_long[ls][1] = b0;
+                        s_long[ls][2] = b1;
                     }
                 }
-                if (slot < 0 || slot >= kLongRows)
+                if (ls < 0 || ls >= kLongRows)
                     for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)kk;
             } else {
                 A.mt[i] = T(0);

@@ -154,7 +154,7 @@ def test_barrier_wait_is_bounded_and_context_survives(weighted):
 
 
 def test_sweep_large_chain_single_pass_select():
-    """More nodes than the sweep's select cache covers (n > blocks x 2048):
+    """More nodes than the sweep's select cache covers (n > blocks x 1024 for FP64 cash):
     the one-pass select. 25 FP64 moves agree with the oracle's 25 moves and
     with the one-kernel-per-phase path."""
     import oracle
