@@ -22,6 +22,8 @@
 // a wait that gives up raises an abort flag on which every block leaves,
 // and the solve ends with the status ST_BARRIER.
 #pragma once
+#include <cstddef>
+
 #include "rlgl_kernels.cuh"
 
 namespace rlgl {
@@ -37,14 +39,25 @@ constexpr int ST_BARRIER = 9;
 // line do not queue behind those on another or behind the barrier's polls,
 // and the fields read together after a barrier are pairs in 16 bytes (one
 // request per pair, the pairs in parallel).
+// (An alignment specifier applies to every declarator of its declaration:
+// one field per declaration here.)
 struct SweepSlot {
-    alignas(128) double a, pr;   // ||C||_1, sum v^r of the cash
-    alignas(128) double msum, mabs;  // sum m_i, sum |m_i| of the moved cash
+    alignas(128) double a;       // ||C||_1 of the cash
+    double pr;                   // sum v^r of the cash
+    alignas(128) double msum;    // sum m_i of the moved cash
+    double mabs;                 // sum |m_i|
     alignas(128) unsigned long long reserve;  // packed frontier reservation
     unsigned long long tstamp;   // block 0's timer at the end of its stats (or select)
     alignas(128) double s;       // sum C
     unsigned long long chunk_next;  // next push chunk to hand out
 };
+static_assert(offsetof(SweepSlot, pr) == offsetof(SweepSlot, a) + 8 && offsetof(SweepSlot, a) % 16 == 0,
+              "a, pr: one 16-byte pair");
+static_assert(offsetof(SweepSlot, mabs) == offsetof(SweepSlot, msum) + 8 && offsetof(SweepSlot, msum) % 16 == 0,
+              "msum, mabs: one 16-byte pair");
+static_assert(offsetof(SweepSlot, tstamp) == offsetof(SweepSlot, reserve) + 8 &&
+                  offsetof(SweepSlot, reserve) % 16 == 0,
+              "reserve, tstamp: one 16-byte pair");
 
 struct alignas(128) GridBar {
     unsigned long long arrived;  // arrivals since the solve began (grid size per barrier)
