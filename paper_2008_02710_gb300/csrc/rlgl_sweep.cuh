@@ -226,6 +226,7 @@ struct SelSmem {
     static constexpr int kNodes = kIters * kNodesPerIter;
     alignas(16) T val[kNodes];
     alignas(16) T idg[kNodes];
+    alignas(16) T sv[kNodes];  // s_i in the cash type (1 / row weight)
     alignas(16) long long rp[kIters][kSelRp];
     unsigned char g[kNodes];
     unsigned long long wsum[kIters * kNodesPerThread * (kThreads / 32)];  // packed (edges << kCountBits) | count
@@ -239,6 +240,45 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int byt
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most the most recent committed group is in flight.
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// s_i in the cash type: FP32 on the MIXED path, FP64 on the FP64 path.
+__device__ __forceinline__ const float* row_scale(const float* sf, const double*, float) { return sf; }
+__device__ __forceinline__ const double* row_scale(const float*, const double* s, double) { return s; }
+
+// Warp sum of the packed (edges << kCountBits) | count of the green lanes:
+// the count from the ballot, the edges from two 32-bit warp reductions of
+// the degree's 16-bit halves (no overflow for any int32 degrees).
+__device__ __forceinline__ unsigned long long warp_pack_sum(bool g, int rdeg) {
+    const unsigned int cnt = __popc(__ballot_sync(0xffffffffu, g));
+    const unsigned int lo = __reduce_add_sync(0xffffffffu, g ? ((unsigned int)rdeg & 0xffffu) : 0u);
+    const unsigned int hi = __reduce_add_sync(0xffffffffu, g ? ((unsigned int)rdeg >> 16) : 0u);
+    return ((((unsigned long long)hi << 16) + lo) << kCountBits) + cnt;
+}
+
+// Exclusive prefix over the warp's lanes of x >= 0 (x < 2^31).
+__device__ __forceinline__ long long warp_exscan_deg(int x) {
+    const int lane = threadIdx.x & 31;
+    if (__all_sync(0xffffffffu, x < (1 << 26))) {
+        // 32 x 2^26 = 2^31: the sums fit 32 bits
+        int y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        return (long long)(y - x);
+    }
+    long long y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long z = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += z;
+    }
+    return y - x;
+}
 
 // Copies elements [e0, e0 + count) of src (count elements of type E in
 // 16-byte pieces; the array holds `avail` elements from index 0) into dst,
@@ -332,8 +372,121 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         finish();
         return;
     }
+    if ((long long)n > (long long)gridDim.x * SelSmem<T>::kNodes && SelSmem<T>::kIters >= 2) {
+        // Large chains, FP32 cash: the block's node ranges one after another
+        // through the two stages of the shared cache, the next range's
+        // asynchronous copies in flight while this one is tested, reserved
+        // and written. One reservation per range: a count pass over all of
+        // them first would read the nodes from memory twice.
+        const bool with_idg = sched == SCHED_LINK;
+        const long long G = gridDim.x;
+        // n > G x kNodes: every block has at least two ranges
+        const int J = (int)((n - 1 - (long long)blockIdx.x * kNodesPerIter) / (G * kNodesPerIter)) + 1;
+        auto stage = [&](int j) {
+            const int buf = j & 1;
+            const long long it0 = ((long long)blockIdx.x + (long long)j * G) * kNodesPerIter;
+            stage_range<T>(cs.val + buf * kNodesPerIter, A.c, it0, kNodesPerIter, n);
+            if (with_idg) stage_range<T>(cs.idg + buf * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
+            stage_range<T>(cs.sv + buf * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
+            stage_range<long long>(cs.rp[buf], A.row_ptr, it0, kSelRp, (long long)n + 1);
+            cp_async_commit();
+        };
+        stage(0);
+        stage(1);
+        for (int j = 0; j < J; ++j) {
+            const int buf = j & 1;
+            const long long it0 = ((long long)blockIdx.x + (long long)j * G) * kNodesPerIter;
+            if (j + 1 < J) cp_async_wait_prev();
+            else cp_async_wait_all();
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const int loc = q * kThreads + threadIdx.x;
+                const int slot = buf * kNodesPerIter + loc;
+                const long long i = it0 + loc;
+                const T v = cs.val[slot];
+                const T idg = with_idg ? cs.idg[slot] : T(0);
+                const int rdeg = (int)(cs.rp[buf][loc + 1] - cs.rp[buf][loc]);
+                const bool g = (i < n) && green_test_v<T>(sched, v, idg, i, th, mask, ax);
+                if (acc_stats && i < n) stat(v, idg);
+                cs.g[slot] = g ? 1 : 0;
+                const unsigned long long w = warp_pack_sum(g, rdeg);
+                if (lane == 0) cs.wsum[q * (kThreads / 32) + wid] = w;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                // kNodesPerThread x warps = 32 groups: one warp-wide scan
+                const unsigned long long v = cs.wsum[lane];
+                unsigned long long x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                cs.wsum[lane] = x - v;
+                const unsigned long long run = __shfl_sync(0xffffffffu, x, 31);
+                if (lane == 0) {
+                    base_sh = run ? atomicAdd(&sl->reserve, run) : 0ull;
+                    s_nlong = 0;
+                }
+            }
+            __syncthreads();
+            const unsigned long long base = base_sh;
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const int loc = q * kThreads + threadIdx.x;
+                const int slot = buf * kNodesPerIter + loc;
+                const long long i = it0 + loc;
+                const T v = cs.val[slot];
+                const long long rb = cs.rp[buf][loc];
+                const int rdeg = (int)(cs.rp[buf][loc + 1] - rb);
+                const bool g = cs.g[slot] != 0;
+                const unsigned int bal = __ballot_sync(0xffffffffu, g);
+                const long long xe = warp_exscan_deg(g ? rdeg : 0);
+                const unsigned long long wb = base + cs.wsum[q * (kThreads / 32) + wid];
+                const long long kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
+                const long long ee = (long long)(wb >> kCountBits) + xe;
+                if (i >= n) continue;
+                if (g) {
+                    const T mtil = v * cs.sv[slot];
+                    A.c[i] = T(0);
+                    red_add(A.H + i, (double)v);  // no load: the L2 adds
+                    msum += v;
+                    mabs += fabs(v);
+                    A.mt[i] = mtil;
+                    A.f_eoff[kk] = ee;
+                    A.f_base[kk] = rb - ee;
+                    A.f_m[kk] = mtil;
+                    const long long b0 = (ee + kPushChunk - 1) / kPushChunk;
+                    const long long b1 = (ee + rdeg + kPushChunk - 1) / kPushChunk;
+                    int ls = -1;
+                    if (b1 - b0 > kLongChunks) {
+                        ls = atomicAdd(&s_nlong, 1);
+                        if (ls < kLongRows) {
+                            s_long[ls][0] = kk;
+                            s_long[ls][1] = b0;
+                            s_long[ls][2] = b1;
+                        }
+                    }
+                    if (ls < 0 || ls >= kLongRows)
+                        for (long long b = b0; b < b1; ++b) A.chunk_row[b] = (int)kk;
+                } else {
+                    A.mt[i] = T(0);
+                }
+            }
+            __syncthreads();
+            // this stage is free: the range after next goes into it
+            if (j + 2 < J) stage(j + 2);
+            const int nlong = s_nlong < kLongRows ? s_nlong : kLongRows;
+            for (int q = 0; q < nlong; ++q)
+                for (long long b = s_long[q][1] + threadIdx.x; b < s_long[q][2]; b += blockDim.x)
+                    A.chunk_row[b] = (int)s_long[q][0];
+        }
+        finish();
+        return;
+    }
     if ((long long)n > (long long)gridDim.x * SelSmem<T>::kNodes) {
-        // Large chains (more block-iterations than the cache holds): one pass
+        // Large chains, FP64 cash (more block-iterations than the cache holds): one pass
         // with one reservation per block-iteration, so that the nodes are
         // read once (a second pass would read them again from memory).
         for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
@@ -406,6 +559,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         ++nj;
         stage_range<T>(cs.val + j * kNodesPerIter, A.c, it0, kNodesPerIter, n);
         if (with_idg) stage_range<T>(cs.idg + j * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
+        stage_range<T>(cs.sv + j * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
         stage_range<long long>(cs.rp[j], A.row_ptr, it0, kSelRp, (long long)n + 1);
     }
     cp_async_wait_all();
@@ -422,9 +576,8 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             const int rdeg = (int)(cs.rp[j][loc + 1] - cs.rp[j][loc]);
             const bool g = (i < n) && green_test_v<T>(sched, v, idg, i, th, mask, ax);
             if (acc_stats && i < n) stat(v, idg);
-            const unsigned long long pk = g ? ((unsigned long long)rdeg << kCountBits) + 1ull : 0ull;
             cs.g[slot] = g ? 1 : 0;
-            const unsigned long long w = warp_sum(pk);
+            const unsigned long long w = warp_pack_sum(g, rdeg);
             if (lane == 0) cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid] = w;
         }
     }
@@ -466,18 +619,13 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             const int rdeg = (int)(cs.rp[j][loc + 1] - rb);
             const bool g = cs.g[slot] != 0;
             const unsigned int bal = __ballot_sync(0xffffffffu, g);
-            long long x = g ? (long long)rdeg : 0ll;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
+            const long long xe = warp_exscan_deg(g ? rdeg : 0);
             const unsigned long long wb = base + cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid];
             const long long kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
-            const long long ee = (long long)(wb >> kCountBits) + x - (g ? (long long)rdeg : 0ll);
+            const long long ee = (long long)(wb >> kCountBits) + xe;
             if (i >= n) continue;
             if (g) {
-                const T mtil = moved_per_weight(v, A.s, A.sf, i);
+                const T mtil = v * cs.sv[slot];
                 A.c[i] = T(0);
                 red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
