@@ -50,6 +50,7 @@ struct SweepSlot {
     unsigned long long tstamp;   // block 0's timer at the end of its stats (or select)
     alignas(128) double s;       // sum C
     unsigned long long chunk_next;  // next push chunk to hand out
+    unsigned long long range_next;  // select of large chains: next node range to hand out
 };
 static_assert(offsetof(SweepSlot, pr) == offsetof(SweepSlot, a) + 8 && offsetof(SweepSlot, a) % 16 == 0,
               "a, pr: one 16-byte pair");
@@ -373,30 +374,37 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         return;
     }
     if ((long long)n > (long long)gridDim.x * SelSmem<T>::kNodes && SelSmem<T>::kIters >= 2) {
-        // Large chains, FP32 cash: the block's node ranges one after another
-        // through the two stages of the shared cache, the next range's
-        // asynchronous copies in flight while this one is tested, reserved
-        // and written. One reservation per range: a count pass over all of
-        // them first would read the nodes from memory twice.
+        // Large chains, FP32 cash: node ranges of kNodesPerIter one after
+        // another through the two stages of the shared cache, the next
+        // range's asynchronous copies in flight while this one is tested,
+        // reserved and written. One reservation per range: a count pass over
+        // all of them first would read the nodes from memory twice. Block b
+        // takes ranges b and b + G, then grabs the next free range from a
+        // counter (the grab issued a range ahead), so that blocks end within
+        // a fraction of a range of one another.
         const bool with_idg = sched == SCHED_LINK;
         const long long G = gridDim.x;
-        // n > G x kNodes: every block has at least two ranges
-        const int J = (int)((n - 1 - (long long)blockIdx.x * kNodesPerIter) / (G * kNodesPerIter)) + 1;
-        auto stage = [&](int j) {
-            const int buf = j & 1;
-            const long long it0 = ((long long)blockIdx.x + (long long)j * G) * kNodesPerIter;
+        const long long nranges = ((long long)n + kNodesPerIter - 1) / kNodesPerIter;
+        __shared__ long long s_grab[2];
+        auto stage = [&](int buf, long long r) {
+            const long long it0 = r * kNodesPerIter;
             stage_range<T>(cs.val + buf * kNodesPerIter, A.c, it0, kNodesPerIter, n);
             if (with_idg) stage_range<T>(cs.idg + buf * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
             stage_range<T>(cs.sv + buf * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
             stage_range<long long>(cs.rp[buf], A.row_ptr, it0, kSelRp, (long long)n + 1);
             cp_async_commit();
         };
-        stage(0);
-        stage(1);
-        for (int j = 0; j < J; ++j) {
+        // n > G x kNodes: ranges b and b + G exist for every block
+        long long cur = blockIdx.x, nxt = blockIdx.x + G;
+        stage(0, cur);
+        stage(1, nxt);
+        for (int j = 0;; ++j) {
             const int buf = j & 1;
-            const long long it0 = ((long long)blockIdx.x + (long long)j * G) * kNodesPerIter;
-            if (j + 1 < J) cp_async_wait_prev();
+            const long long it0 = cur * kNodesPerIter;
+            // the range after next, staged at the end of this iteration
+            if (threadIdx.x == 0 && nxt >= 0)
+                s_grab[buf] = 2 * G + (long long)atomicAdd(&sl->range_next, 1ull);
+            if (nxt >= 0) cp_async_wait_prev();
             else cp_async_wait_all();
             __syncthreads();
 #pragma unroll
@@ -476,11 +484,16 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             }
             __syncthreads();
             // this stage is free: the range after next goes into it
-            if (j + 2 < J) stage(j + 2);
+            long long after = nxt >= 0 ? s_grab[buf] : -1;
+            if (after >= nranges) after = -1;
+            if (after >= 0) stage(buf, after);
             const int nlong = s_nlong < kLongRows ? s_nlong : kLongRows;
             for (int q = 0; q < nlong; ++q)
                 for (long long b = s_long[q][1] + threadIdx.x; b < s_long[q][2]; b += blockDim.x)
                     A.chunk_row[b] = (int)s_long[q][0];
+            cur = nxt;
+            nxt = after;
+            if (cur < 0) break;
         }
         finish();
         return;
@@ -745,6 +758,7 @@ __device__ __forceinline__ void clear_slot(SweepSlot* o) {
     o->mabs = 0.0;
     o->reserve = 0ull;
     o->chunk_next = 0ull;
+    o->range_next = 0ull;
 }
 
 template <typename T, bool kHasW>
