@@ -180,9 +180,12 @@ def test_sweep_large_chain_single_pass_select():
 def test_sweep_large_chain_mixed_pipelined_select(theta_lag):
     """MIXED cash on more nodes than the select cache covers (n > blocks x
     2048): node ranges stream through the two shared-memory stages, handed
-    out by a counter after the first two per block. 25 moves agree with the
-    oracle's 25 FP64 moves within the MIXED bound, with and without the
-    stale threshold."""
+    out by a counter after the first two per block. After 25 moves (no
+    re-derivation yet) the FP32 cash has drifted from the oracle's FP64
+    trajectory by rounding only (~1e-6 relative per node); a range skipped or
+    moved twice would leave ~2e-4 of the mass out. Without the stale
+    threshold the sweep also agrees with the one-kernel-per-phase path (both
+    FP32) move by move."""
     import oracle
     csr = synth.rmat_chain_n((1 << 21) + 54321, 3, seed=12)
     p = oracle.transition_probs(csr)
@@ -190,13 +193,19 @@ def test_sweep_large_chain_mixed_pipelined_select(theta_lag):
     info_or = oracle.solve(csr, p, C, H, sched=oracle.LINK_THRESHOLD, theta_scale=0.5, tol=0.0,
                            max_steps=25, theta_lag=theta_lag)
     pi_or = oracle.estimate(H)
-    with Chain(csr, precision="mixed") as ch:
-        ch.set_params(theta_scale=0.5, theta_lag=theta_lag)
-        info = ch.solve("link_threshold", tol=0.0, max_steps=25, raise_on_noconv=False)
-        assert info["moves"] == 25 and ch.get_params().persistent == 1
-        pi = ch.estimate()
-        log = ch.move_log(25)
-    assert np.abs(pi - pi_or).sum() <= 1e-6
+    res = []
+    for persistent in ((1, 0) if theta_lag == 0 else (1,)):
+        with Chain(csr, precision="mixed") as ch:
+            ch.set_params(theta_scale=0.5, theta_lag=theta_lag, persistent=persistent)
+            info = ch.solve("link_threshold", tol=0.0, max_steps=25, raise_on_noconv=False)
+            assert info["moves"] == 25 and ch.get_params().persistent == persistent
+            res.append((ch.estimate(), ch.move_log(25), info))
+    pi, log, info = res[0]
+    assert np.abs(pi - pi_or).sum() <= 1e-5
     assert abs(info["edges_pushed"] - info_or["pushes"]) <= 1e-3 * info_or["pushes"]
-    # every move found a frontier (the ranges were all visited)
     assert all(r["green"] > 0 for r in log)
+    if theta_lag == 0:
+        pib, logb, _ = res[1]
+        assert np.abs(pi - pib).sum() <= 1e-6
+        for ra, rb in zip(log[:10], logb[:10]):
+            assert abs(ra["green"] - rb["green"]) <= max(2, rb["green"] // 10000)
