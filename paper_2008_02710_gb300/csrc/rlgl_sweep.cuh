@@ -401,9 +401,11 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         for (int j = 0;; ++j) {
             const int buf = j & 1;
             const long long it0 = cur * kNodesPerIter;
-            // the range after next, staged at the end of this iteration
-            if (threadIdx.x == 0 && nxt >= 0)
-                s_grab[buf] = 2 * G + (long long)atomicAdd(&sl->range_next, 1ull);
+            // the range after next, staged at the end of this iteration: the
+            // grab's reply is first used there, so its round trip overlaps
+            // this range's work
+            unsigned long long grab = 0ull;
+            if (threadIdx.x == 0 && nxt >= 0) grab = atomicAdd(&sl->range_next, 1ull);
             if (nxt >= 0) cp_async_wait_prev();
             else cp_async_wait_all();
             __syncthreads();
@@ -482,6 +484,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                     A.mt[i] = T(0);
                 }
             }
+            if (threadIdx.x == 0 && nxt >= 0) s_grab[buf] = 2 * G + (long long)grab;
             __syncthreads();
             // this stage is free: the range after next goes into it
             long long after = nxt >= 0 ? s_grab[buf] : -1;
