@@ -383,6 +383,9 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         // counter (the grab issued a range ahead), so that blocks end within
         // a fraction of a range of one another.
         const bool with_idg = sched == SCHED_LINK;
+        // unweighted chains: s_i = 1/d_i, bit for bit the staged 1/d
+        const bool scale_is_idg = with_idg && A.w == nullptr;
+        const T* scale = scale_is_idg ? cs.idg : cs.sv;
         const long long G = gridDim.x;
         const long long nranges = ((long long)n + kNodesPerIter - 1) / kNodesPerIter;
         __shared__ long long s_grab[2];
@@ -390,7 +393,8 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             const long long it0 = r * kNodesPerIter;
             stage_range<T>(cs.val + buf * kNodesPerIter, A.c, it0, kNodesPerIter, n);
             if (with_idg) stage_range<T>(cs.idg + buf * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
-            stage_range<T>(cs.sv + buf * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
+            if (!scale_is_idg)
+                stage_range<T>(cs.sv + buf * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
             stage_range<long long>(cs.rp[buf], A.row_ptr, it0, kSelRp, (long long)n + 1);
             cp_async_commit();
         };
@@ -452,13 +456,17 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 const int rdeg = (int)(cs.rp[buf][loc + 1] - rb);
                 const bool g = cs.g[slot] != 0;
                 const unsigned int bal = __ballot_sync(0xffffffffu, g);
+                if (bal == 0u) {  // no green node in this warp's group
+                    if (i < n) A.mt[i] = T(0);
+                    continue;
+                }
                 const long long xe = warp_exscan_deg(g ? rdeg : 0);
                 const unsigned long long wb = base + cs.wsum[q * (kThreads / 32) + wid];
                 const long long kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
                 const long long ee = (long long)(wb >> kCountBits) + xe;
                 if (i >= n) continue;
                 if (g) {
-                    const T mtil = v * cs.sv[slot];
+                    const T mtil = v * scale[slot];
                     A.c[i] = T(0);
                     red_add(A.H + i, (double)v);  // no load: the L2 adds
                     msum += v;
@@ -568,6 +576,8 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
     // memory at once (one round trip, no registers held), then tests and
     // counts from there, per warp and node group.
     const bool with_idg = sched == SCHED_LINK;
+    const bool scale_is_idg = with_idg && A.w == nullptr;  // s_i = 1/d_i
+    const T* scale = scale_is_idg ? cs.idg : cs.sv;
     int nj = 0;
     for (int j = 0; j < SelSmem<T>::kIters; ++j) {
         const long long it0 = ((long long)blockIdx.x + (long long)j * gridDim.x) * kNodesPerIter;
@@ -575,7 +585,8 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         ++nj;
         stage_range<T>(cs.val + j * kNodesPerIter, A.c, it0, kNodesPerIter, n);
         if (with_idg) stage_range<T>(cs.idg + j * kNodesPerIter, A.ideg, it0, kNodesPerIter, n);
-        stage_range<T>(cs.sv + j * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
+        if (!scale_is_idg)
+            stage_range<T>(cs.sv + j * kNodesPerIter, row_scale(A.sf, A.s, T(0)), it0, kNodesPerIter, n);
         stage_range<long long>(cs.rp[j], A.row_ptr, it0, kSelRp, (long long)n + 1);
     }
     cp_async_wait_all();
@@ -635,13 +646,17 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
             const int rdeg = (int)(cs.rp[j][loc + 1] - rb);
             const bool g = cs.g[slot] != 0;
             const unsigned int bal = __ballot_sync(0xffffffffu, g);
+            if (bal == 0u) {  // no green node in this warp's group
+                if (i < n) A.mt[i] = T(0);
+                continue;
+            }
             const long long xe = warp_exscan_deg(g ? rdeg : 0);
             const unsigned long long wb = base + cs.wsum[(j * kNodesPerThread + q) * (kThreads / 32) + wid];
             const long long kk = (long long)(wb & ((1ull << kCountBits) - 1ull)) + __popc(bal & ((1u << lane) - 1u));
             const long long ee = (long long)(wb >> kCountBits) + xe;
             if (i >= n) continue;
             if (g) {
-                const T mtil = v * cs.sv[slot];
+                const T mtil = v * scale[slot];
                 A.c[i] = T(0);
                 red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
