@@ -32,6 +32,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -412,11 +413,19 @@ def traffic_from_profiles(kernel_cls, workload):
     return ent.get("dram_bytes_per_launch")
 
 
+def code_only(text):
+    """CUDA/C++ source without comments, trailing blanks and empty lines: a
+    change of comments alone leaves the kernels as they were."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh"):
-        with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

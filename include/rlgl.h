@@ -175,7 +175,7 @@ rlgl_status rlgl_default_params(rlgl_params* p);
 /*
  * Creates a context for the chain given by its out-links (CSR), uploads it,
  * builds the in-link (CSC) copy used by pull moves and residuals, and
- * performs step 0 (Eq. init; Alg. 1 lines (1)-(3)): H = H_1 = M_0 and
+ * performs step 0 (Eq. init; the initial step of Alg. 1): H = H_1 = M_0 and
  * C = C_1 = -M_0 (I - P), total zero.
  *   n, nnz   : nodes and edges; row i's out-edges are col[row_ptr[i] ..
  *              row_ptr[i+1]-1].
@@ -242,7 +242,7 @@ rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period,
                            rlgl_memspace src);
 
 /*
- * One synchronous move (Alg. 1 lines (6), (2), (3)): choose G_t from the
+ * One synchronous move (the move of Alg. 1): choose G_t from the
  * current cash by the schedule, then C <- C - M_t (I - P), H <- H + M_t with
  * M_t = C_t I(G_t). theta: see rlgl_schedule. info may be NULL (then the call
  * does not wait for the GPU); when given, the call synchronises and fills it.
@@ -250,7 +250,7 @@ rlgl_status rlgl_set_masks(rlgl_ctx* ctx, const uint8_t* masks, int64_t period,
 rlgl_status rlgl_step(rlgl_ctx* ctx, rlgl_schedule sched, double theta, rlgl_step_info* info);
 
 /*
- * Algorithm 1 until t >= 2 and ||C_t||_1 / |H_t 1| < tol (line (7)), or
+ * Algorithm 1 until t >= 2 and ||C_t||_1 / |H_t 1| < tol (its stop test), or
  * max_steps moves (RLGL_ENOCONV), or a degenerate history (RLGL_EDEGENERATE).
  * The whole loop runs on the device as one CUDA graph with a conditional
  * while-node: no host round trip per move. tol = 0 with max_steps = T makes

@@ -94,7 +94,7 @@ void oracle_move(int64_t n, const int64_t* row_ptr, const int32_t* col, const do
 }
 
 /*
- * Step 0 (Eq. init; Alg. 1 lines (1)-(3)): C_0 = 0, H_0 = 0, G_0 = [N] and
+ * Step 0 (Eq. init; the initial step of Alg. 1): C_0 = 0, H_0 = 0, G_0 = [N] and
  * the moved cash is the given distribution M_0 (uniform 1/N when m0 is
  * NULL), not C_0. Afterwards H = H_1 = M_0 and C = C_1 = -M_0 (I - P).
  */
@@ -282,7 +282,7 @@ double oracle_invariant_residual(int64_t n, const int64_t* row_ptr, const int32_
  * Loop, for t = 1, 2, ...:
  *   if |H_t 1| <= 1e-12 sum|H_t|            -> OR_EDEGENERATE (Sec. 2.1: the
  *                                              estimate is undefined);
- *   if t >= 2 and ||C_t||_1 / |H_t 1| < tol -> OR_OK   (Alg. 1 line (7));
+ *   if t >= 2 and ||C_t||_1 / |H_t 1| < tol -> OR_OK   (the stop test of Alg. 1);
  *   if max_steps moves were made           -> OR_ENOCONV;
  *   choose G_t from C_t; move.
  * safety_every > 0 makes every safety_every-th move all-green.

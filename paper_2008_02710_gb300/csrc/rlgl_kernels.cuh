@@ -1,8 +1,8 @@
 // Device kernels of the RLGL green-light sweep (sm_103a).
 //
 // One move of Alg. 1 (Eqs. recursion_M, recursion_H, recursion_C) runs as
-//   stats   : ||C||_1, sum C, sum |C|^r in FP64 (stopping rule, Alg. 1 line
-//             (7); threshold theta_t(r), Sec. 6) + solve control;
+//   stats   : ||C||_1, sum C, sum |C|^r in FP64 (the stop test of Alg. 1;
+//             threshold theta_t(r), Sec. 6) + solve control;
 //   [top-k] : exact k-th largest |C| by radix select (TOPFRAC);
 //   select  : G = {i : |C_i| >= theta, C_i != 0}; for i in G: m_i = C_i,
 //             C_i <- 0, H_i += m_i (FP64); frontier compaction with warp
@@ -416,7 +416,7 @@ __device__ __forceinline__ bool cash_stalled(double l1, double& mark, long long&
 }
 
 // Decides, after the cash statistics of C_t are known, whether the solve
-// stops (Alg. 1 line (7): t >= 2 and ||C_t||_1 / |H_t 1| < tol) and sets the
+// stops (the stop test of Alg. 1: t >= 2 and ||C_t||_1 / |H_t 1| < tol) and sets the
 // threshold for this move. Runs in one thread.
 __device__ void control_after_stats(DevState* st, unsigned long long cond_handle,
                                     unsigned long long cond_refresh, int use_cond, int n) {
@@ -516,7 +516,7 @@ __device__ __forceinline__ int rank_status(int r) {
 
 // The batch form of control_after_stats, run by every thread of the last
 // block: each chain takes its statistics from its accumulators, is tested
-// for its own stop (Alg. 1 line (7) with its own tolerance) and gets its own
+// for its own stop (the stop test of Alg. 1 with its own tolerance) and gets its own
 // threshold; the loop ends when no chain is left running.
 __device__ void batch_control(DevState* st, const BatchView& bv, unsigned long long cond_handle,
                               unsigned long long cond_refresh, int use_cond) {

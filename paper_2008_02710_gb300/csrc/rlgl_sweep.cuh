@@ -1,7 +1,7 @@
-// The persistent sweep: the moves of a single-chain solve (Alg. 1 lines
-// (2)-(7)) in one cooperative kernel, so that a move costs three grid
-// barriers instead of three to four kernel launches, their drain and their
-// serial last-block tails.
+// The persistent sweep: the moves of a single-chain solve (the loop of
+// Alg. 1 with its stop test) in one cooperative kernel, so that a move
+// costs three grid barriers (two with the stale threshold) instead of three
+// to four kernel launches, their drain and their serial last-block tails.
 //
 // Every block runs every phase of a move on its share of the work:
 //   stats   : its slice of the nodes; block sums go to one FP64 atomic per
