@@ -1119,21 +1119,12 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
         b = s_next;
         __syncthreads();
     }
-    // The first and last frontier rows of a chunk; those of the next chunk
-    // are loaded while this one is pushed, and the grab of the chunk after
-    // is answered meanwhile (its reply is first used at the second barrier
-    // of the iteration), so a chunk waits on neither round trip.
-    auto chunk_rows = [&](long long bb, long long& r0, long long& r1) {
-        r0 = ld_shared_data<kCg>(chunk_row + bb);
-        r1 = (bb + 1 < nchunks) ? (long long)ld_shared_data<kCg>(chunk_row + bb + 1) : K - 1;
-    };
-    long long k0 = 0, k1 = 0;
-    if (b < nchunks) chunk_rows(b, k0, k1);
     while (b < nchunks) {
-        unsigned long long grab = 0ull;
-        if (next && threadIdx.x == 0) grab = atomicAdd(next, 1ull);
+        if (next && threadIdx.x == 0) s_next = (long long)atomicAdd(next, 1ull);  // read below
         const long long e0 = b * kPushChunk;
         const int ne = (int)min((long long)kPushChunk, E - e0);
+        const long long k0 = ld_shared_data<kCg>(chunk_row + b);
+        const long long k1 = (b + 1 < nchunks) ? (long long)ld_shared_data<kCg>(chunk_row + b + 1) : K - 1;
         const int nr = (int)(k1 - k0 + 1);
 #pragma unroll
         for (int q = 0; q < kPer; ++q) sm.row[threadIdx.x * kPer + q] = 0;
@@ -1145,11 +1136,7 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             const long long off = eo - e0;  // row 0 starts at or before the chunk
             if (r > 0 && off < ne) sm.row[(int)off] = r;
         }
-        if (next && threadIdx.x == 0) s_next = (long long)grab;
         __syncthreads();
-        const long long bn = next ? s_next : b + step;
-        long long k0n = 0, k1n = 0;
-        if (bn < nchunks) chunk_rows(bn, k0n, k1n);
         // running maximum over the slots: slot -> row
         int v[kPer];
         int run = 0;
@@ -1207,9 +1194,12 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             }
         }
         __syncthreads();
-        b = bn;
-        k0 = k0n;
-        k1 = k1n;
+        if (next) {
+            b = s_next;
+            __syncthreads();  // everyone has read s_next before thread 0 rewrites it
+        } else {
+            b += step;
+        }
     }
     if (n_hot > 0) {
         __syncthreads();
