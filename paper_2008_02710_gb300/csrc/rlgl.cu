@@ -747,11 +747,20 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     if (err & 8u) return fail(ctx, RLGL_ENOTSTOCHASTIC, "a weight is not positive and finite");
 
     const int gn = grid_for(n, kThreads, ctx->sms * 16);
+    // long weighted rows go to a list (chunk_row and err serve as scratch
+    // until the CSC build below) and get a block each
+    CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(unsigned int), ctx->stream));
     k_row_scale<<<gn, kThreads, 0, ctx->stream>>>(
         ctx->row_ptr, ctx->w, n, ctx->s, ctx->sf,
         prec == RLGL_MIXED ? (float*)ctx->ideg : nullptr,
-        prec == RLGL_MIXED ? nullptr : (double*)ctx->ideg);
+        prec == RLGL_MIXED ? nullptr : (double*)ctx->ideg, ctx->chunk_row, ctx->err);
     CKL(ctx);
+    if (ctx->has_w) {
+        const long long max_long = nnz / kLongRowW + 1;  // rows longer than kLongRowW
+        k_row_scale_long<<<(unsigned int)max_long, kThreads, 0, ctx->stream>>>(
+            ctx->row_ptr, ctx->w, ctx->s, ctx->sf, ctx->chunk_row, ctx->err);
+        CKL(ctx);
+    }
     // In-link (CSC) copy: counts, scan, scatter.
     long long* cursor = nullptr;
     TRY(dalloc(ctx, &cursor, (size_t)n + 1));

@@ -1655,14 +1655,27 @@ __global__ void k_validate(const long long* __restrict__ row_ptr, const int* __r
 }
 
 // s_i = 1 / sum_k w_ik (FP64 sum in CSR order) or 1 / deg_i.
+// Rows with more weights than this have their weight sum taken by a whole
+// block (k_row_scale_long): one thread summing a million weights in a row
+// (the auxiliary node of a PageRank chain) took tens of milliseconds.
+constexpr long long kLongRowW = 65536;
+
 __global__ void k_row_scale(const long long* __restrict__ row_ptr, const float* __restrict__ w,
                             long long n, double* __restrict__ s, float* __restrict__ sf,
-                            float* __restrict__ idegf, double* __restrict__ idegd) {
+                            float* __restrict__ idegf, double* __restrict__ idegd,
+                            int* __restrict__ long_rows, unsigned int* __restrict__ n_long) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         long long a = row_ptr[i], b = row_ptr[i + 1];
+        const double id = 1.0 / (double)(b - a);
+        if (idegf) idegf[i] = (float)id;
+        if (idegd) idegd[i] = id;
         double sum;
         if (w) {
+            if (b - a > kLongRowW) {
+                long_rows[atomicAdd(n_long, 1u)] = (int)i;  // summed by k_row_scale_long
+                continue;
+            }
             sum = 0.0;
             for (long long k = a; k < b; ++k) sum += (double)w[k];
         } else {
@@ -1670,9 +1683,24 @@ __global__ void k_row_scale(const long long* __restrict__ row_ptr, const float* 
         }
         s[i] = 1.0 / sum;
         if (sf) sf[i] = (float)(1.0 / sum);
-        const double id = 1.0 / (double)(b - a);
-        if (idegf) idegf[i] = (float)id;
-        if (idegd) idegd[i] = id;
+    }
+}
+
+// s_i = 1 / sum_k w_ik for the long rows k_row_scale listed: block b sums
+// row long_rows[b] (FP64, a fixed order for a given block size).
+__global__ void __launch_bounds__(kThreads) k_row_scale_long(
+    const long long* __restrict__ row_ptr, const float* __restrict__ w, double* __restrict__ s,
+    float* __restrict__ sf, const int* __restrict__ long_rows, const unsigned int* __restrict__ n_long) {
+    __shared__ double scratch[32];
+    if (blockIdx.x >= *n_long) return;
+    const long long i = long_rows[blockIdx.x];
+    const long long a = row_ptr[i], b = row_ptr[i + 1];
+    double acc = 0.0;
+    for (long long k = a + threadIdx.x; k < b; k += blockDim.x) acc += (double)w[k];
+    const double sum = block_sum(acc, scratch);
+    if (threadIdx.x == 0) {
+        s[i] = 1.0 / sum;
+        if (sf) sf[i] = (float)(1.0 / sum);
     }
 }
 
