@@ -78,3 +78,36 @@ def test_reference_arm_other_ranks_exit_quietly():
                           "--workload", "rmat16", "--steps", "1", "--warmup", "3"],
                          capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_source_hash_ignores_comments_only():
+    """The committed DRAM traffic is keyed by a hash of the kernel code: a
+    comment change keeps it, a code change drops it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) { // add one\n  return x + 1; /* done */ }\n"
+    b = "// header\nint f(int x) {\n  return x + 1; }\n\n"
+    c = "int f(int x) { return x + 2; }\n"
+    norm = lambda t: "".join(bench.code_only(t).split())
+    assert norm(a) == norm(b)
+    assert norm(a) != norm(c)
+    assert len(bench.source_hash()) == 16
+
+
+def test_sweep_bytes_skip_the_statistics_pass_of_stale_moves():
+    """Algorithmic bytes of the sweep's moves: a move whose log entry has no
+    statistics time (the stale threshold) carries no statistics bytes."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2008_02710_gb300 import synth
+    g = bench.GpuRun.__new__(bench.GpuRun)
+    g.csr = synth.CSR(4, np.array([0, 1, 2, 3, 4], np.int64), np.array([1, 2, 3, 0], np.int32), None)
+    g.wl = {"precision": "mixed"}
+    rec = lambda st: {"edges_pushed": 2, "green": 2, "mode": 1, "phase_us": [st, st, 1.0, 1.0, 1.0, 1.0]}
+    fresh = g.alg_bytes("link_threshold", [rec(1.0), rec(1.0)], sweep=True)
+    stale = g.alg_bytes("link_threshold", [rec(1.0), rec(0.0)], sweep=True)
+    assert fresh["stats"] == 2 * 4 * (4 + 4) and stale["stats"] == 4 * (4 + 4)
+    assert fresh["select"] == stale["select"] and fresh["push"] == stale["push"]
+    phase = g.alg_bytes("link_threshold", [rec(0.0), rec(0.0)], sweep=False)
+    assert phase["stats"] == fresh["stats"]
