@@ -8,11 +8,17 @@
 //             statistic in the move's slot;
 //   barrier ; every block reads the totals and takes the same decisions
 //             (stop, re-derivation, theta) from the same numbers;
-//   select  : its slice of the nodes (the same compaction as k_select);
+//   select  : its node ranges, staged in shared memory by asynchronous
+//             copies (the same compaction as k_select);
 //   barrier ; every block reads the frontier size and picks push or pull;
 //   push    : its share of the frontier's edge chunks, or
 //   pull    : its share of the merge-path tiles;
 //   barrier.
+// With the stale threshold (Control::theta_lag) a move after the first of a
+// launch has no stats phase and no first barrier: its select gathers the
+// statistics of the cash it reads, and the next move's threshold and
+// decisions come from them, taken while the block waits at the last
+// barrier.
 // The kernel returns when the solve stops (it then ends the graph's loop) or
 // when the FP32 cash of the MIXED path must be re-derived in FP64 (the
 // graph's re-derivation runs and the loop launches the sweep again).
