@@ -33,13 +33,14 @@ def augmented(csr: CSR, c_num: int = 17, c_den: int = 20) -> CSR:
 
 def solve(csr: CSR, c_num: int = 17, c_den: int = 20, tol: float = 1e-9,
           schedule: str = "link_threshold", theta_scale: float = 0.5, precision: str = "mixed",
-          max_steps: int = 100000, stream=None):
-    """PageRank of the unit-weight graph csr: returns (pi*, solve info)."""
+          max_steps: int = 100000, stream=None, theta_lag: int = 0):
+    """PageRank of the unit-weight graph csr: returns (pi*, solve info).
+    theta_lag = 1 takes the stale threshold (see rlgl_params)."""
     aug = augmented(csr, c_num, c_den)
     m0 = np.zeros(aug.n)
     m0[0] = 1.0
     with rlgl.Chain(aug, m0=m0, precision=precision, stream=stream) as ch:
-        ch.set_params(theta_scale=theta_scale)
+        ch.set_params(theta_scale=theta_scale, theta_lag=theta_lag)
         info = ch.solve(schedule, tol=tol, max_steps=max_steps)
         pi = ch.estimate()
     y = pi[1:]
