@@ -166,7 +166,8 @@ typedef struct {
     double sum_hist;        /* H_{t+1} 1 after the move */
     float phase_us[6];      /* persistent sweep only (else 0), from block 0's clock: stats work,
                                wait at the barrier after it, select work (with the decisions),
-                               wait, push/pull work, wait; microseconds */
+                               wait, push/pull work, wait; microseconds. A move of the stale
+                               threshold has no statistics pass: its first two are 0 */
 } rlgl_move_record;
 
 /* Fills p with the defaults listed in rlgl_params. */
