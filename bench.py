@@ -11,20 +11,28 @@ seeded inputs stand in for the paper's web graphs.
 One bench step = one complete solve of that chain from step 0 to L1 error
 <= 1e-6 against the FP64 oracle's stationary law, with the headline
 schedule (RLGL threshold on the cash per out-link, |C_i|/d_i >= 0.5 x its
-mean; the literal |C_i| >= mean threshold, all-green power iteration and the
-top-1% schedule are timed the same way beside it): step 0, T* moves (T* found by
-an untimed calibration run), the estimate pi_hat = H / (H 1). The chain is
-resident in HBM; L2 (129 MB) is flushed between timed steps by writing a
-512 MB buffer. value = edge-pushes/s (links used by the moves, the paper's
-unit of work); ms_per_step = the time to L1 1e-6.
+mean, the threshold one move stale; the literal |C_i| >= mean threshold,
+all-green power iteration and the top-1% schedule are timed the same way
+beside it): step 0, T* moves (T* found by an untimed calibration run), the
+estimate pi_hat = H / (H 1). The chain is resident in HBM; L2 (129 MB) is
+flushed between timed steps by writing a 512 MB buffer. value =
+edge-pushes/s (links used by the moves, the paper's unit of work);
+ms_per_step = the time to L1 1e-6.
+
+The sub-record "beyond_l2" repeats the measurement (headline schedule and
+all-green, with the sweep's roofline) on a chain whose CSR and CSC are far
+beyond L2 (default: symmetrised R-MAT 24, 587 M links, reference law
+d_i / sum d).
 
 Oracle leg (host cores, untimed for the GPU numbers): the FP64 oracle's
 power iteration gives the reference stationary law that defines "L1 error";
-a bounded sample of oracle moves gives the CPU baseline.
+a bounded sample of oracle moves of the headline schedule gives the CPU
+baseline.
 
---impl reference times the FP64 CPU oracle on the same workload and metric.
-With torchrun (N > 1) every rank runs an independent replica on its own GPU
-(the solve of one chain is not sharded); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the same workload, schedule
+and metric. With torchrun (N > 1) every rank runs an independent replica on
+its own GPU (the solve of one chain is not sharded); rank 0 prints one JSON
+line.
 """
 from __future__ import annotations
 
@@ -207,24 +215,63 @@ def oracle_reference(csr, tol=1e-11, maxit=50000, undirected=False):
                     seconds=time.time() - t, cores=os.cpu_count())
 
 
-def oracle_cpu_sample(csr, budget_s=15.0, min_moves=2):
-    """Oracle leg: the FP64 oracle as it stands (one core), RLGL threshold
-    moves from step 0 for about budget_s seconds; edge-pushes/s."""
+ORACLE_SCHED = {"link_threshold": "LINK_THRESHOLD", "threshold": "THRESHOLD", "all_green": "ALL_GREEN",
+                "topfrac": "TOPFRAC"}
+
+
+def oracle_cpu_sample(csr, budget_s=15.0, min_moves=2, sched="link_threshold", theta_scale=0.5,
+                      theta_lag=1):
+    """Oracle leg: the FP64 oracle as it stands (one core) making moves of the
+    headline schedule from step 0 for about budget_s seconds; edge-pushes/s."""
     import oracle
     p = oracle.transition_probs(csr)
     C, H = oracle.initial_step(csr, p)
+    osched = getattr(oracle, ORACLE_SCHED[sched])
+    kw = dict(theta_scale=theta_scale, theta_lag=theta_lag) if sched in ("link_threshold", "threshold") else {}
     moves, pushes, t0 = 0, 0.0, time.time()
     while moves < min_moves or time.time() - t0 < budget_s:
-        info = oracle.solve(csr, p, C, H, sched=oracle.THRESHOLD, tol=0.0, max_steps=1,
-                            check_every=-1)
+        info = oracle.solve(csr, p, C, H, sched=osched, tol=0.0, max_steps=min_moves,
+                            check_every=-1, **kw)
         moves += info["moves"]
         pushes += info["pushes"]
         if info["moves"] == 0:
             break
     dt = time.time() - t0
     return dict(value=pushes / dt, unit=UNIT, cores=1, kind="oracle",
-                sample=f"first {moves} RLGL-threshold moves of the oracle from step 0 on this "
+                sample=f"first {moves} moves ({sched}, theta_scale {theta_scale}, stale threshold "
+                       f"{theta_lag}; {min_moves} per oracle call) of the oracle from step 0 on this "
                        f"workload ({pushes:.3e} edge-pushes in {dt:.1f} s, 1 thread)")
+
+
+def oracle_mt_time_to_err(csr, ref, nthreads):
+    """The oracle's power iteration (FP64, pull form, OpenMP over nthreads
+    host cores) from the uniform law: the least iteration count whose
+    iterate is within L1 1e-6 of the reference, and the wall time of that
+    run (its in-link build included)."""
+    import oracle
+    p = oracle.transition_probs(csr)
+
+    def err(k):
+        pi, _, _ = oracle.power_iteration(csr, p, tol=0.0, maxit=k, nthreads=nthreads)
+        return float(np.abs(pi - ref).sum())
+
+    lo, hi = 0, 8
+    while err(hi) > ERR_TARGET:
+        lo, hi = hi, 2 * hi
+        if hi > 4096:
+            return None
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if err(mid) <= ERR_TARGET:
+            hi = mid
+        else:
+            lo = mid
+    t0 = time.perf_counter()
+    pi, it, _ = oracle.power_iteration(csr, p, tol=0.0, maxit=hi, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"kind": "oracle power iteration (all-green), OpenMP", "cores": nthreads, "iterations": it,
+            "ms_to_err": 1e3 * dt, "err": float(np.abs(pi - ref).sum()),
+            "edge_pushes_per_s": it * csr.nnz / dt}
 
 
 # ------------------------------------------------------------------ GPU
@@ -253,11 +300,14 @@ class GpuRun:
             return float(e.item())
 
     def calibrate(self, sched, theta, ref_dev, max_moves=20000):
-        """Untimed: the least move count T* whose solve (the timed path: step
-        0, then T* moves as one device-loop solve with its re-derivations,
-        then the estimate) has L1 error <= 1e-6 against the reference. Doubles
-        T until the error is met, then bisects; returns (T*, error, the
-        (moves, error) pairs tried)."""
+        """Untimed: the least move count T* (exact up to 1/128 of it) whose
+        solve (the timed path: step 0, then T* moves as one device-loop solve
+        with its re-derivations, then the estimate) has L1 error <= 1e-6
+        against the reference. A scan first: one solve from step 0 continued
+        in pieces of about 1/16 of the moves made so far, the error read after
+        each piece, gives a first T; solves from step 0 then bracket T* and
+        bisect. Returns (T*, error, the (moves, error) pairs of the solves
+        from step 0)."""
         ch = self.chain
         traj = []
 
@@ -268,15 +318,40 @@ class GpuRun:
             traj.append((k, e))
             return e
 
-        lo, hi = 0, 8
-        e = err_at(hi)
+        ch.reset(self.m0)
+        done, e = 0, float("inf")
         while not e <= ERR_TARGET:  # NaN counts as not reached
-            if hi >= max_moves:
-                return None, e, sorted(traj)
-            lo, hi = hi, min(2 * hi, max_moves)
-            e = err_at(hi)
-        e_hi = e
-        while hi - lo > 1:
+            if done >= max_moves:
+                return None, e, sorted(traj + [(done, e)])
+            piece = min(max(8, done // 16), max_moves - done)
+            info = ch.solve(sched, theta, tol=0.0, max_steps=piece, raise_on_noconv=False)
+            done += piece
+            e = self.err(ref_dev)
+            if info["status"] not in ("RLGL_OK", "RLGL_ENOCONV"):
+                return None, e, sorted(traj + [(done, e)])
+        hi = done
+        e_hi = err_at(hi)
+        lo = 0
+        if e_hi <= ERR_TARGET:
+            # walk down until a move count misses the target
+            while True:
+                cand = hi - max(1, hi // 16)
+                if cand <= 0:
+                    break
+                e = err_at(cand)
+                if e <= ERR_TARGET:
+                    hi, e_hi = cand, e
+                else:
+                    lo = cand
+                    break
+        else:
+            # the continued solve reached it sooner than a solve from step 0
+            while not e_hi <= ERR_TARGET:
+                if hi >= max_moves:
+                    return None, e_hi, sorted(traj)
+                lo, hi = hi, min(max_moves, hi + max(1, hi // 16))
+                e_hi = err_at(hi)
+        while hi - lo > max(1, hi // 128):
             mid = (lo + hi) // 2
             e = err_at(mid)
             if e <= ERR_TARGET:
@@ -322,27 +397,40 @@ class GpuRun:
         return kt, self.alg_bytes(sched, log)
 
     def alg_bytes(self, sched, log, sweep=False):
-        """Algorithmic bytes per kernel class of the logged moves (every
-        access counted once from memory). On the sweep, a move of the stale
-        threshold has no statistics pass (its log entry has no stats time)."""
+        """Algorithmic bytes per kernel class of the logged moves: what the
+        method must move, every access counted once from memory (the paper's
+        cost is the links a move uses, Sec. 6):
+          every node and move: the selection scan reads the cash (the cash
+          type's size); a move with a statistics pass reads it once more;
+          every green node of a push move: row offset 8 B, row scale 8 B, the
+          cash read and written, the history read-modify-write 16 B, its
+          frontier entry written and read back 8 B;
+          every edge pushed: the column index 4 B, the weight 4 B (weighted
+          chains only) and one scattered add of the cash type;
+          a pull move (every all-green move) reads every in-link instead: the
+          source index 4 B, the weight 4 B (weighted), one gathered value of
+          the cash type, and per node the in-link offset 8 B, the cash read
+          and written and the history read-modify-write 16 B (all-green has
+          no selection scan: every node moves).
+        On the sweep, a move of the stale threshold has no statistics pass
+        (its log entry has no statistics time)."""
         csr = self.csr
         n, nnz = csr.n, csr.nnz
         cash = 4 if self.wl["precision"] == "mixed" else 8
         wb = 4 if csr.w is not None else 0
-        link = 4 if sched == "link_threshold" else 0
         alg = {k: 0.0 for k in KERNEL_CLASSES}
         for rec in log:
             E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
             if not (sweep and rec["phase_us"][0] == 0.0 and rec["phase_us"][1] == 0.0):
-                alg["stats"] += n * (cash + link)
-            if sched == "all_green":
-                alg["select"] += n * (3 * cash + 16 + 8)
-            else:
-                alg["select"] += n * (2 * cash + link) + G * (cash + 16 + 8 + 16 + 16 + cash)
-            if mode == 1:
-                alg["push"] += E * (4 + wb + cash) + G * (16 + cash)
-            elif mode == 2:
-                alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash)
+                alg["stats"] += n * cash
+            dense = sched == "all_green" or (mode == 2 and G == n)
+            if not dense:
+                alg["select"] += n * cash
+            if mode == 2:
+                alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash + 16)
+            elif mode == 1:
+                alg["select"] += G * (8 + 8 + 2 * cash + 16 + 4)
+                alg["push"] += E * (4 + wb + cash) + G * 4
             if sched == "topfrac":
                 alg["topk"] += (3 if cash == 4 else 6) * n * cash
         return alg
@@ -429,13 +517,33 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+PROBE_SRC = os.path.join(ROOT, "bench_l2_probe.cu")
+PROBE_LIB = os.path.join(ROOT, "libbench_l2_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """libbench_l2_probe.so (nvcc, sm_103a): the random-access rate probe of
+    the bench, built beside this file."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
+           "-Xcompiler", "-fPIC", "-o", tmp, PROBE_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed building libbench_l2_probe.so")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def random_access_peaks(n_words, m=1 << 22):
     """Scatter (red.global.add.f32) and gather rates, G ops/s, of m random
-    4-byte accesses into n_words words on this GPU (libl2probe.so): the
-    ceiling of the push and the pull when the chain sits in L2."""
+    4-byte accesses into n_words words on this GPU: the ceiling of the push
+    and the pull when the cash sits in L2."""
     import ctypes
-    from paper_2008_02710_gb300 import _build
-    lib = ctypes.CDLL(_build.build_probe())
+    lib = ctypes.CDLL(build_probe())
     lib.l2_probe_rate.restype = ctypes.c_double
     lib.l2_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
     grid = 8 * 152
@@ -453,6 +561,80 @@ def measured_peaks():
 
 # ----------------------------------------------------------------- main
 
+def roofline_of_sweep(g, sched, theta, tstar, workload, peak, peak_src):
+    """Roofline of the persistent sweep, the dominant kernel of a solve (every
+    move's work is in it): T* moves launched eagerly with a CUDA event pair
+    around each launch on the context's stream; achieved = algorithmic bytes
+    per launch / average launch time. The DRAM figures come from the
+    committed ncu capture of the same kernel code (null when the code has
+    changed since)."""
+    (ms_sw, n_sw), bytes_sw, phases, push_rate = g.sweep_profile(sched, theta, tstar)
+    n_sw = max(n_sw, 1)
+    avg_s = ms_sw / 1e3 / n_sw
+    alg = bytes_sw / n_sw
+    achieved = alg / avg_s / 1e9 if avg_s > 0 else None
+    traffic = traffic_from_profiles("sweep", workload)
+    rec = {"bound": "hbm", "kernel": "sweep", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": (achieved / peak) if achieved else None,
+           "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+           else "fallback 6.8 TB/s",
+           "traffic": traffic, "launches": n_sw, "avg_launch_us": avg_s * 1e6,
+           "alg_bytes_per_launch": alg,
+           "byte_model": "per node and move 1 cash read (+1 with a statistics pass); per green "
+                         "node 48 B (MIXED); per edge pushed 4 B index (+4 B weight) + 1 cash-size "
+                         "add; pull moves: per in-link 4 B (+4 B) + 1 cash-size gather, per node "
+                         "8 B + 2 cash + 16 B",
+           "dram_gbs": None, "dram_frac": None, "traffic_over_alg": None, "l2_resident": None}
+    if traffic and avg_s > 0:
+        rec["dram_gbs"] = traffic / avg_s / 1e9
+        rec["dram_frac"] = rec["dram_gbs"] / peak
+        rec["traffic_over_alg"] = traffic / alg
+        # most of what the moves touch was served from L2 (ncu: DRAM bytes
+        # well below the algorithmic bytes)
+        rec["l2_resident"] = bool(traffic < 0.5 * alg)
+    return rec, phases, push_rate
+
+
+def beyond_l2_record(args, device, peak, peak_src):
+    """The same measurement on a chain whose CSR and CSC are far beyond the
+    129 MB L2 (default: symmetrised R-MAT 24, reference law d_i / sum d):
+    time to L1 1e-6 of the headline schedule and of all-green, three timed
+    solves each (one warm-up, L2 flushed before each), and the sweep's
+    roofline."""
+    import torch
+    name = args.beyond_l2
+    t0 = time.time()
+    csr, wl = make_workload(name)
+    gen_s = time.time() - t0
+    ref, ref_info = oracle_reference(csr, undirected=wl.get("undirected", False))
+    ref_dev = torch.from_numpy(ref).to(device)
+    g = GpuRun(csr, wl, device)
+    out = {"workload": name, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz, "gen_s": gen_s,
+           "reference": ref_info, "timed": "3 solves after 1 warm-up, L2 flushed before each"}
+    try:
+        for label, sched, scale, lag in (("link_threshold", "link_threshold", args.theta_scale, args.theta_lag),
+                                         ("all_green", "all_green", 1.0, 0)):
+            g.chain.set_params(theta_scale=scale, r=1, theta_lag=lag, persistent=1)
+            tstar, e, _ = g.calibrate(sched, 0.0, ref_dev, max_moves=args.max_moves)
+            if tstar is None:
+                out[label] = {"tstar": None, "err_at_cap": e, "cap": args.max_moves}
+                continue
+            ts, inf = g.timed_solves(sched, 0.0, tstar, 3, 1)
+            ms = float(np.median(ts))
+            rf, phases, push_rate = roofline_of_sweep(g, sched, 0.0, tstar, name, peak, peak_src)
+            out[label] = {"tstar": tstar, "ms": ms, "err": e, "theta_scale": scale, "theta_lag": lag,
+                          "edge_pushes": inf[0]["edges_pushed"],
+                          "edge_pushes_per_s": inf[0]["edges_pushed"] / (ms / 1e3),
+                          "roofline": rf, "sweep_phase_us_per_move": phases}
+        if out.get("link_threshold", {}).get("ms") and out.get("all_green", {}).get("ms"):
+            out["speedup_vs_all_green"] = out["all_green"]["ms"] / out["link_threshold"]["ms"]
+    finally:
+        g.chain.close()
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -469,7 +651,7 @@ def run_gpu(args):
         "link_threshold": ("link_threshold", 0.0, args.theta_scale, args.max_moves),
         "threshold": ("threshold", 0.0, 1.0, args.max_moves),
         "all_green": ("all_green", 0.0, 1.0, args.max_moves),
-        "topfrac": ("topfrac", 0.01, 1.0, min(args.max_moves, 2000)),
+        "topfrac": ("topfrac", 0.01, 1.0, args.topfrac_max_moves),
     }
     head = args.sched
     order = [head] + ([] if args.skip_compare else [k for k in plan if k != head])
@@ -484,10 +666,9 @@ def run_gpu(args):
         return sched, theta, cap
 
     nvtx = torch.cuda.nvtx
-    # autotuned threshold: the scale and exponent r of theta_t(r), and on the
-    # persistent sweep the stale threshold (theta from the previous move's
-    # cash), with the least time to the error target (untimed search; the
-    # timed run below uses the winner)
+    # --tune: the threshold's scale and exponent r of theta_t(r), and on the
+    # persistent sweep the stale threshold, with the least time to the error
+    # target (untimed search; the timed run below uses the winner)
     tuning = None
     if args.tune and head in ("link_threshold", "threshold"):
         nvtx.range_push("tune")
@@ -523,6 +704,7 @@ def run_gpu(args):
         raise SystemExit(f"{head} did not reach L1 {ERR_TARGET} in {args.max_moves} moves; "
                          f"(move, L1) along the way: {tr[:4] + tr[4::max(1, len(tr) // 12)]}")
     tstar = cal[head]["tstar"]
+    peak, peak_src = measured_peaks()
 
     # kernel profile of the headline schedule (CUDA events on the context
     # stream): per phase on the one-kernel-per-phase path, then the
@@ -535,10 +717,11 @@ def run_gpu(args):
     nvtx.range_pop()
     g.chain.set_params(persistent=args.persistent, theta_lag=lag_of[head])
     sweep_on = args.persistent == 1 and head != "topfrac"
-    push_rate = None
+    push_rate = sweep_phases = roof = None
     if sweep_on:
         nvtx.range_push("profile_sweep")
-        (ms_sw, n_sw), bytes_sw, sweep_phases, push_rate = g.sweep_profile(sched_h, theta_h, tstar)
+        roof, sweep_phases, push_rate = roofline_of_sweep(g, sched_h, theta_h, tstar, args.workload,
+                                                          peak, peak_src)
         nvtx.range_pop()
     # the headline schedule on the one-kernel-per-phase path, for comparison
     phase_ms = None
@@ -557,6 +740,11 @@ def run_gpu(args):
             ts, inf = g.timed_solves(sched, theta, cal[name]["tstar"], max(3, args.steps // 2), 3)
             compare[name] = dict(tstar=cal[name]["tstar"], ms=float(np.median(ts)),
                                  edges=inf[0]["edges_pushed"], err=cal[name]["err"])
+            if name == "all_green" and args.persistent == 1:
+                rf, ph, _ = roofline_of_sweep(g, sched, theta, cal[name]["tstar"], args.workload + ":all_green",
+                                              peak, peak_src)
+                compare[name]["roofline"] = rf
+                compare[name]["sweep_phase_us_per_move"] = ph
         else:
             compare[name] = dict(tstar=None, ms=None, err_at_cap=cal[name]["err"],
                                  cap=plan[name][3])
@@ -595,17 +783,17 @@ def run_gpu(args):
     e2e_val = sum_over_ranks(dist, float(np.sum(ep)), device) / e2e_t
 
     # roofline of the dominant kernel: the persistent sweep when the timed
-    # solves run it (every move's work is in it), else the phase class with
-    # the most device time (classes whose launches returned at once carry no
-    # algorithmic bytes)
-    if sweep_on:
-        dom, ms_dom, n_dom, bytes_dom = "sweep", ms_sw, n_sw, bytes_sw
-    else:
+    # solves run it, else the phase class with the most device time
+    # (classes whose launches returned at once carry no algorithmic bytes)
+    if not sweep_on:
         dom = max((k for k in KERNEL_CLASSES if alg[k] > 0), key=lambda k: kt[k][0])
         ms_dom, n_dom = kt[dom]
-        bytes_dom = alg[dom]
-    peak, peak_src = measured_peaks()
-    achieved = bytes_dom / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
+        achieved = alg[dom] / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_src,
+                "traffic": traffic_from_profiles(dom, args.workload), "launches": n_dom,
+                "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
+                "alg_bytes_per_launch": alg[dom] / max(n_dom, 1)}
     scat_peak, gath_peak = random_access_peaks(csr.n)
     refreshes = infos[0]["refreshes"]
     if sweep_on:
@@ -615,38 +803,38 @@ def run_gpu(args):
     else:
         kernels_per_iter = (7 if head == "topfrac" else 4) + (3 if wl["precision"] == "mixed" else 0)
         launches = args.steps * (kernels_per_iter * iters + 1 + 5 + 2)
+    ag = compare.get("all_green", {})
+    ag_ceiling = None
+    if ag.get("ms") and gath_peak > 0:
+        # all-green moves pull every in-link: one random gather each
+        per_move_us = 1e3 * ag["ms"] / ag["tstar"]
+        floor_us = csr.nnz / (gath_peak * 1e9) * 1e6
+        ag_ceiling = {"us_per_move": per_move_us, "gather_floor_us": floor_us,
+                      "over_floor": per_move_us / floor_us}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 cash / f64 history" if wl["precision"] == "mixed" else "f64",
         "data": "synthetic (seeded R-MAT; stands in for the paper's web graphs)",
-        "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
-                   "schedule": head, "theta_scale": plan[head][2], "r": r_of[head],
-                   "theta_lag": lag_of[head],
-                   "autotuned": tuning is not None, "precision": wl["precision"],
-                   "tstar_moves": tstar,
-                   "l2": "flushed between timed steps (512 MB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "config": bench_config(args, wl, csr, ws, plan[head][2], r_of[head], lag_of[head], head),
+        "precision": wl["precision"], "tstar_moves": tstar, "autotuned": tuning is not None,
         "time_to_err_ms": {head: ms_per_step, **{k: v["ms"] for k, v in compare.items()}},
         "moves_to_err": {k: v["tstar"] for k, v in cal.items()},
         "edge_pushes_to_err": {head: infos[0]["edges_pushed"],
                                **{k: v.get("edges") for k, v in compare.items()}},
-        "speedup_vs_all_green": (compare["all_green"]["ms"] / ms_per_step)
-        if compare.get("all_green", {}).get("ms") else None,
+        "speedup_vs_all_green": (ag["ms"] / ms_per_step) if ag.get("ms") else None,
+        "all_green_vs_gather_floor": ag_ceiling,
         "persistent_sweep": sweep_on,
         "tuning": tuning,
         "sweep_phase_us_per_move": sweep_phases if sweep_on else None,
         "time_to_err_ms_phase_kernels": phase_ms,  # same moves, fresh threshold
         "not_reached": {k: v for k, v in compare.items() if v.get("tstar") is None},
+        "compare": {k: {kk: vv for kk, vv in v.items() if kk in ("roofline", "sweep_phase_us_per_move")}
+                    for k, v in compare.items() if "roofline" in v},
         "final_l1_err": final_err,
         "reference": ref_info,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                     "traffic": traffic_from_profiles(dom, args.workload),
-                     "launches": n_dom, "avg_launch_us": (ms_dom / max(n_dom, 1)) * 1e3,
-                     "alg_bytes_per_launch": bytes_dom / max(n_dom, 1)},
+        "roofline": roof,
         "random_access": {"scatter_peak_gops": scat_peak, "gather_peak_gops": gath_peak,
                           "probe": f"4M random 4-byte accesses into {csr.n} words, 1216 blocks",
                           "push_phase_gops": push_rate if sweep_on else None,
@@ -659,11 +847,30 @@ def run_gpu(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_cpu_sample(csr, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = oracle_cpu_sample(csr, budget_s=args.cpu_budget, theta_scale=plan[head][2],
+                                                theta_lag=lag_of[head] if head == "link_threshold" else 0,
+                                                sched=head)
+    # free this chain before the next one
+    g.chain.close()
+    del g
+    torch.cuda.empty_cache()
+    if ws == 1 and args.beyond_l2 != "none":
+        nvtx.range_push("beyond_l2")
+        out["beyond_l2"] = beyond_l2_record(args, device, peak, peak_src)
+        nvtx.range_pop()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_config(args, wl, csr, ws, theta_scale, r, theta_lag, sched):
+    """The workload as both arms name it (the GPU arm and the oracle arm
+    print the same dict)."""
+    return {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
+            "schedule": sched, "theta_scale": theta_scale, "r": r, "theta_lag": theta_lag,
+            "l2": "GPU arm: L2 flushed between timed steps (512 MB write)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single chain, one GPU"}
 
 
 def run_batch(args):
@@ -793,36 +1000,48 @@ def run_serving(args):
 
 
 def run_reference(args):
-    """The FP64 CPU oracle timed on the host cores on the same workload."""
+    """The FP64 CPU oracle timed on the host cores on the same workload,
+    schedule and metric as the GPU arm: every step continues the oracle's
+    solve from where the previous one stopped by args.ref_moves moves of the
+    headline schedule (per-link threshold, theta_scale, stale threshold);
+    edge-pushes/s. Beside it, the oracle's OpenMP power iteration to L1 1e-6
+    on every host core."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     import oracle
     csr, wl = make_workload(args.workload)
+    head = args.sched
+    lag = args.theta_lag if head in ("link_threshold", "threshold") else 0
+    scale = args.theta_scale if head == "link_threshold" else 1.0
     p = oracle.transition_probs(csr)
     C, H = oracle.initial_step(csr, p)
+    osched = getattr(oracle, ORACLE_SCHED[head])
+    kw = dict(theta_scale=scale, theta_lag=lag) if head in ("link_threshold", "threshold") else {}
     times, pushes = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        info = oracle.solve(csr, p, C, H, sched=oracle.THRESHOLD, tol=0.0,
-                            max_steps=args.ref_moves, check_every=-1)
+        info = oracle.solve(csr, p, C, H, sched=osched, tol=0.0, max_steps=args.ref_moves,
+                            check_every=-1, **kw)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
             pushes.append(info["pushes"])
     value = float(np.sum(pushes) / np.sum(times))
-    sample = (f"{args.ref_moves} RLGL-threshold moves of the FP64 oracle per step, continuing "
-              f"from step 0 on this workload, 1 thread")
+    sample = (f"{args.ref_moves} moves of the FP64 oracle per step ({head}, theta_scale {scale}, "
+              f"stale threshold {lag}), continuing from step 0 on this workload, 1 thread")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": args.workload, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz,
-                   "schedule": "threshold", "precision": "fp64"},
+        "config": bench_config(args, wl, csr, ws, scale, 1, lag, head),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if not args.no_oracle_mt:
+        ref, _ = oracle_reference(csr, undirected=wl.get("undirected", False))
+        out["oracle_mt"] = oracle_mt_time_to_err(csr, ref, os.cpu_count() or 1)
     print(json.dumps(out), flush=True)
 
 
@@ -911,13 +1130,21 @@ def main(argv=None):
     ap.add_argument("--theta-scale", type=float, default=0.5,
                     help="theta_scale of the per-link threshold schedule")
     ap.add_argument("--max-moves", type=int, default=20000)
+    ap.add_argument("--topfrac-max-moves", type=int, default=20000,
+                    help="move cap of the top-1%% schedule's calibration")
+    ap.add_argument("--beyond-l2", default="rmat24u",
+                    help="workload of the beyond-L2 sub-record ('none' to skip)")
+    ap.add_argument("--no-oracle-mt", action="store_true",
+                    help="reference arm: skip the OpenMP power iteration to 1e-6")
     ap.add_argument("--persistent", type=int, choices=[0, 1], default=1,
                     help="1: solves run as the persistent sweep; 0: one kernel per phase")
-    ap.add_argument("--theta-lag", type=int, choices=(0, 1), default=0,
+    ap.add_argument("--theta-lag", type=int, choices=(0, 1), default=1,
                     help="stale threshold (theta from the previous move's cash) for the headline "
                          "threshold schedule when it is not autotuned")
-    ap.add_argument("--no-tune", dest="tune", action="store_false",
-                    help="keep --theta-scale and r = 1 instead of autotuning the threshold")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the threshold's scale, r and staleness first (untimed) instead of "
+                         "--theta-scale, r = 1 and --theta-lag")
+    ap.add_argument("--no-tune", dest="tune", action="store_false", help=argparse.SUPPRESS)
     ap.add_argument("--autotune", action="store_true",
                     help="batch: pick theta scale, r and the push/pull crossover with the autotuner first")
     ap.add_argument("--skip-compare", action="store_true")

@@ -6,8 +6,8 @@
 // indices of an n-word array (indices from a xorshift sequence, all in
 // range), grid-stride, 256 threads per block.
 //
-// Separate library (libl2probe.so): measurement only, not part of the
-// RLGL path.
+// Built by bench.py into libbench_l2_probe.so beside it: measurement only,
+// not part of the RLGL library.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -279,6 +279,16 @@ rlgl_status rlgl_wait(rlgl_ctx* ctx, rlgl_solve_info* info);
  * [n]). RLGL_EDEGENERATE when |H 1| <= 1e-12 sum|H| (pi_out untouched). */
 rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst);
 
+/* The estimate restricted to the nodes [lo, hi) and normalised over them:
+ * pi_out[i - lo] = H_i / sum_{k in [lo, hi)} H_k (FP64; dst memspace, double
+ * [hi - lo]). With the auxiliary-node chain P^(0) of Sec. 2.3.2 (node 0 the
+ * auxiliary node) the range [1, N) gives the PageRank vector of the original
+ * nodes (Eq. pi_hat over the original nodes). RLGL_EINVAL unless
+ * 0 <= lo < hi <= n, and for a batch; RLGL_EDEGENERATE when |sum H| <=
+ * 1e-12 sum|H| over the range (pi_out untouched). */
+rlgl_status rlgl_estimate_range(rlgl_ctx* ctx, int64_t lo, int64_t hi, double* pi_out,
+                                rlgl_memspace dst);
+
 /* Current (C_t, H_t) as FP64 (dst memspace; either pointer may be NULL). */
 rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace dst);
 
@@ -334,14 +344,17 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
  *   c, h     : device double [n], the cash C_t and history H_t.
  *   c0       : device double [n] or NULL (C_0 = 0).
  *   l1_out   : device double [1]; receives the residual, or NaN when an
- *              index of the CSR is out of range or a row is empty.
+ *              index of the CSR is out of range, a row is empty, or a row's
+ *              weights do not sum to a positive number.
  *   stream   : cudaStream_t the work is queued on (NULL: legacy stream).
  * Asynchronous: returns after queueing three kernels; *l1_out is ready when
  * the stream reaches that point. Its scratch is one fixed array in device
  * memory (8 MiB of accumulators plus 8 KiB), held by every GPU that loads
  * the library until the process exits, so n is limited to 2^20 nodes:
  * RLGL_EINVAL beyond that, for NULL pointers, or for n or nnz < 1. RLGL_ECUDA
- * when a launch fails. The first call on each device looks up that array's
+ * when a launch fails, or, with nothing queued, when an error of earlier
+ * work is already pending on the calling thread (that error is left pending
+ * for its owner, not cleared). The first call on each device looks up that array's
  * device address (cudaGetSymbolAddress), so make it before any stream
  * capture. All calls on a device share the array and each one clears it
  * first, so calls whose work overlaps on the GPU (two streams, or two

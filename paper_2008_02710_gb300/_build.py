@@ -9,8 +9,6 @@ SRC = [os.path.join(HERE, "csrc", "rlgl.cu"), os.path.join(HERE, "csrc", "rlgl_n
 DEPS = SRC + [os.path.join(HERE, "csrc", "rlgl_kernels.cuh"), os.path.join(HERE, "csrc", "rlgl_sweep.cuh"),
                os.path.join(ROOT, "include", "rlgl.h")]
 LIB = os.path.join(HERE, "librlgl.so")
-PROBE_SRC = os.path.join(HERE, "csrc", "l2_probe.cu")
-PROBE_LIB = os.path.join(HERE, "libl2probe.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-shared", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
@@ -38,21 +36,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-def build_probe(force: bool = False) -> str:
-    """libl2probe.so: the random-access rate probe used by bench.py."""
-    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
-        return PROBE_LIB
-    tmp = PROBE_LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC", "-o", tmp, PROBE_SRC]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libl2probe.so")
-    os.replace(tmp, PROBE_LIB)
-    return PROBE_LIB
-
-
 if __name__ == "__main__":
     build(force=True, verbose=True)
-    build_probe(force=True)

@@ -1322,13 +1322,12 @@ static rlgl_status batch_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace d
     return RLGL_OK;
 }
 
-rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
-    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
-    if (!pi_out) return fail(ctx, RLGL_EINVAL, "pi_out is NULL");
-    NOT_PENDING(ctx);
-    if (ctx->nchains > 1) return batch_estimate(ctx, pi_out, dst);
-    const int n = (int)ctx->n;
-    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->st, ctx->part, 0);
+// pi_i = H_i / sum_{k in [lo, hi)} H_k for i in [lo, hi), into pi_out[i - lo].
+static rlgl_status estimate_range(rlgl_ctx* ctx, long long lo, long long hi, double* pi_out,
+                                  rlgl_memspace dst) {
+    const int m = (int)(hi - lo);
+    const double* H = ctx->H + lo;
+    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(H, m, ctx->st, ctx->part, 0);
     CKL(ctx);
     double sums[2];
     CK(ctx, cudaMemcpyAsync(sums, ctx->part + 2 * kMaxGrid, sizeof sums, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1337,12 +1336,33 @@ rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
         return fail(ctx, RLGL_EDEGENERATE, "degenerate history: H 1 = %g, sum|H| = %g", sums[0], sums[1]);
     double* out = pi_out;
     if (dst == RLGL_HOST) out = ctx->hsrc;  // staging (all scratch, rewritten before use)
-    k_scale<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, n, ctx->part + 2 * kMaxGrid, out);
+    k_scale<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(H, m, ctx->part + 2 * kMaxGrid, out);
     CKL(ctx);
     if (dst == RLGL_HOST)
-        CK(ctx, cudaMemcpyAsync(pi_out, out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(pi_out, out, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return RLGL_OK;
+}
+
+rlgl_status rlgl_estimate(rlgl_ctx* ctx, double* pi_out, rlgl_memspace dst) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (!pi_out) return fail(ctx, RLGL_EINVAL, "pi_out is NULL");
+    if (dst != RLGL_HOST && dst != RLGL_DEVICE) return fail(ctx, RLGL_EINVAL, "bad memspace");
+    NOT_PENDING(ctx);
+    if (ctx->nchains > 1) return batch_estimate(ctx, pi_out, dst);
+    return estimate_range(ctx, 0, ctx->n, pi_out, dst);
+}
+
+rlgl_status rlgl_estimate_range(rlgl_ctx* ctx, int64_t lo, int64_t hi, double* pi_out, rlgl_memspace dst) {
+    if (!ctx) return fail(nullptr, RLGL_EINVAL, "ctx is NULL");
+    if (!pi_out) return fail(ctx, RLGL_EINVAL, "pi_out is NULL");
+    if (dst != RLGL_HOST && dst != RLGL_DEVICE) return fail(ctx, RLGL_EINVAL, "bad memspace");
+    if (ctx->nchains > 1) return fail(ctx, RLGL_EINVAL, "rlgl_estimate_range serves single chains");
+    if (lo < 0 || hi > ctx->n || lo >= hi)
+        return fail(ctx, RLGL_EINVAL, "node range [%lld, %lld) not inside [0, %lld)", (long long)lo,
+                    (long long)hi, ctx->n);
+    NOT_PENDING(ctx);
+    return estimate_range(ctx, lo, hi, pi_out, dst);
 }
 
 rlgl_status rlgl_get_state(rlgl_ctx* ctx, double* c, double* h, rlgl_memspace dst) {

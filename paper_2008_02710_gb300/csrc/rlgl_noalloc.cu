@@ -64,7 +64,8 @@ __global__ void na_clear(unsigned char* base, long long n) {
 // y_j += H_i p_ij over every out-edge, one warp per row; p_ij = w_ij / sum_k
 // w_ik (or 1/deg_i without weights). Empty rows, row offsets outside
 // [0, nnz] and columns outside [0, n) are skipped and flagged instead of
-// being accessed.
+// being accessed; so is a row whose weights do not sum to a positive number
+// (zero, negative or NaN), which has no transition probabilities.
 __global__ void na_scatter(unsigned char* base, long long n, long long nnz,
                            const long long* __restrict__ row_ptr,
                            const int* __restrict__ col, const float* __restrict__ w,
@@ -87,6 +88,10 @@ __global__ void na_scatter(unsigned char* base, long long n, long long nnz,
         } else {
             rs = (double)(b - a);
         }
+        if (!(rs > 0.0)) {
+            if (lane == 0) atomicOr(s.bad, 1u);
+            continue;
+        }
         const double hi = h[i] / rs;
         for (long long k = a + lane; k < b; k += 32) {
             const int j = col[k];
@@ -100,7 +105,7 @@ __global__ void na_scatter(unsigned char* base, long long n, long long nnz,
 }
 
 // l1 = sum_j |c_j - c0_j - (y_j - h_j)|, combined by the last block to
-// finish; NaN when an index was out of range.
+// finish; NaN when na_scatter flagged a row.
 __global__ void na_reduce(unsigned char* base, long long n, const double* __restrict__ c,
                           const double* __restrict__ h, const double* __restrict__ c0,
                           double* l1_out) {
@@ -169,6 +174,12 @@ extern "C" rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz,
             g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
         }
         base = g_scratch_ptr[dev];
+    }
+    // An error left pending on this thread by earlier, unrelated work is
+    // reported (RLGL_ECUDA) and left in place for its owner: nothing is
+    // queued. Otherwise a launch error read below is this call's own.
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        return RLGL_ECUDA;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     na_clear<<<256, kNaThreads, 0, s>>>(base, n);

@@ -93,23 +93,19 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Grid-wide barrier of a cooperative launch. Thread 0 of each block makes
-// the block's writes visible (fence), adds one to the arrival count (no
-// value returned) and waits until the count reaches `target`, the number of
-// arrivals once every block has reached this barrier: the count only grows,
-// so no block has to reset or release anything. The wait is bounded by
-// limit_ns. Returns false (in every thread of the block) when the sweep must
-// stop. When ts is given, thread 0 stores its arrival and release times in
-// ts[0], ts[1].
-// Thread 0: the arrival half of grid_barrier.
+// Thread 0: the arrival half of a grid barrier. Makes the block's writes
+// visible (fence) and adds one to the arrival count (no value returned);
+// target grows by the grid size, the count once every block has arrived.
 __device__ __forceinline__ void bar_arrive(GridBar* bar, unsigned long long& target) {
     target += gridDim.x;
     __threadfence();
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(&bar->arrived) : "memory");
 }
 
-// Thread 0: the waiting half of grid_barrier; returns 0 when the sweep
-// must stop.
+// Thread 0: the waiting half of a grid barrier. Polls the arrival count
+// until it reaches target, at most limit_ns; a wait that runs out raises the
+// abort flag, and a raised flag ends every other wait. Returns 0 when the
+// sweep must stop.
 __device__ __forceinline__ int bar_wait(GridBar* bar, unsigned long long target,
                                         unsigned long long limit_ns) {
     int ok = 1;
@@ -132,58 +128,34 @@ __device__ __forceinline__ int bar_wait(GridBar* bar, unsigned long long target,
     return ok;
 }
 
-// As grid_barrier, with `work` run by thread 0 between its arrival and its
-// wait (off the critical path unless this block arrives last).
+// Grid-wide barrier of a cooperative launch: the count only grows, so no
+// block has to reset or release anything. `target` is the block's expected
+// arrival count (kept by thread 0). `work` runs in thread 0 between its
+// arrival and its wait (off the critical path unless this block arrives
+// last). The wait is bounded by limit_ns; returns false (in every thread of
+// the block) when the sweep must stop. When ts is given, thread 0 stores its
+// arrival and release times in ts[0], ts[1].
 template <typename F>
 __device__ __forceinline__ bool grid_barrier_with(GridBar* bar, unsigned long long& target,
                                                   unsigned long long limit_ns, unsigned long long* ts,
                                                   F&& work) {
-    __shared__ int s_ok2;
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         if (ts) ts[0] = globaltimer();
         bar_arrive(bar, target);
         work();
-        s_ok2 = bar_wait(bar, target, limit_ns);
+        s_ok = bar_wait(bar, target, limit_ns);
         if (ts) ts[1] = globaltimer();
     }
     __syncthreads();
-    return s_ok2 != 0;
+    return s_ok != 0;
 }
 
 __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned long long& target,
                                              unsigned long long limit_ns,
                                              unsigned long long* ts = nullptr) {
-    // target: the block's expected arrival count (shared memory; thread 0 keeps it)
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (ts) ts[0] = globaltimer();
-        int ok = 1;
-        target += gridDim.x;
-        __threadfence();
-        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(&bar->arrived) : "memory");
-        const unsigned long long t0 = globaltimer();
-        unsigned int spins = 0;
-        while (ld_acquire_u64(&bar->arrived) < target) {
-            if ((++spins & 15u) == 0u) {
-                if (ld_acquire_u32(&bar->abort)) {
-                    ok = 0;
-                    break;
-                }
-                if (globaltimer() - t0 > limit_ns) {
-                    atomicExch(&bar->abort, 1u);
-                    ok = 0;
-                    break;
-                }
-            }
-            __nanosleep(32);
-        }
-        s_ok = ok;
-        if (ts) ts[1] = globaltimer();
-    }
-    __syncthreads();
-    return s_ok != 0;
+    return grid_barrier_with(bar, target, limit_ns, ts, []() {});
 }
 
 template <typename T>

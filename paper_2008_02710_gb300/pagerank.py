@@ -42,6 +42,6 @@ def solve(csr: CSR, c_num: int = 17, c_den: int = 20, tol: float = 1e-9,
     with rlgl.Chain(aug, m0=m0, precision=precision, stream=stream) as ch:
         ch.set_params(theta_scale=theta_scale, theta_lag=theta_lag)
         info = ch.solve(schedule, tol=tol, max_steps=max_steps)
-        pi = ch.estimate()
-    y = pi[1:]
-    return y / y.sum(), info
+        # the original nodes' part of the estimate, normalised over them
+        pr = ch.estimate_range(1, aug.n)
+    return pr, info

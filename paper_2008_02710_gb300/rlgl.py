@@ -105,6 +105,7 @@ SIGNATURES = {
     "rlgl_query": (_ST, [_VP, ctypes.POINTER(_I32)]),
     "rlgl_wait": (_ST, [_VP, ctypes.POINTER(SolveInfo)]),
     "rlgl_estimate": (_ST, [_VP, _VP, _I32]),
+    "rlgl_estimate_range": (_ST, [_VP, _I64, _I64, _VP, _I32]),
     "rlgl_get_state": (_ST, [_VP, _VP, _VP, _I32]),
     "rlgl_invariant_residual": (_ST, [_VP, ctypes.POINTER(_D)]),
     "rlgl_refresh": (_ST, [_VP, ctypes.POINTER(_D)]),
@@ -307,6 +308,14 @@ class Chain:
             out = np.empty(self.n, dtype=np.float64)
         p, sp, keep = _ptr(out)
         self._c(self.lib.rlgl_estimate(self.ctx, p, sp))
+        return out
+
+    def estimate_range(self, lo: int, hi: int, out=None):
+        """pi_hat over the nodes [lo, hi), normalised over them."""
+        if out is None:
+            out = np.empty(hi - lo, dtype=np.float64)
+        p, sp, keep = _ptr(out)
+        self._c(self.lib.rlgl_estimate_range(self.ctx, lo, hi, p, sp))
         return out
 
     def set_chain_tol(self, tol):

@@ -107,7 +107,15 @@ def test_sweep_bytes_skip_the_statistics_pass_of_stale_moves():
     rec = lambda st: {"edges_pushed": 2, "green": 2, "mode": 1, "phase_us": [st, st, 1.0, 1.0, 1.0, 1.0]}
     fresh = g.alg_bytes("link_threshold", [rec(1.0), rec(1.0)], sweep=True)
     stale = g.alg_bytes("link_threshold", [rec(1.0), rec(0.0)], sweep=True)
-    assert fresh["stats"] == 2 * 4 * (4 + 4) and stale["stats"] == 4 * (4 + 4)
+    assert fresh["stats"] == 2 * 4 * 4 and stale["stats"] == 4 * 4
     assert fresh["select"] == stale["select"] and fresh["push"] == stale["push"]
+    # per move: a 4-byte scan of every node, 48 B per green node (44 in the
+    # select, the frontier read back by the push), 8 B per edge pushed
+    assert fresh["select"] == 2 * (4 * 4 + 2 * 44) and fresh["push"] == 2 * (2 * 8 + 2 * 4)
     phase = g.alg_bytes("link_threshold", [rec(0.0), rec(0.0)], sweep=False)
     assert phase["stats"] == fresh["stats"]
+    # all-green pulls every in-link: 8 B per link and 36 B per node with the
+    # statistics pass (MIXED)
+    pull = {"edges_pushed": 4, "green": 4, "mode": 2, "phase_us": [1.0] * 6}
+    ag = g.alg_bytes("all_green", [pull], sweep=True)
+    assert sum(ag.values()) == 4 * 8 + 4 * 36

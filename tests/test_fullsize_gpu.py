@@ -43,6 +43,33 @@ def test_rmat20_solve_reaches_1e6_against_oracle(rmat20, sched):
     assert inv <= 1e-6 * 2 ** -10  # re-derived before convergence was reported
 
 
+def test_rmat20_headline_path_against_oracle(rmat20):
+    """The path the bench times, at full size: R-MAT 20, MIXED precision, the
+    persistent sweep, the per-link threshold at scale 1/2 with the stale
+    threshold (theta_lag = 1). The solve of a fixed move count from step 0
+    (tol 0, as the bench runs it) and the solve to a residual both reach L1
+    1e-6 against the oracle's law; the sweep ran every move (the move log
+    carries its phase times) and its state keeps the cash balance."""
+    csr, p, ref = rmat20
+    with Chain(csr, precision="mixed") as ch:
+        ch.set_params(theta_scale=0.5, r=1, theta_lag=1)
+        assert ch.get_params().persistent == 1
+        info = ch.solve("link_threshold", 0.0, tol=0.0, max_steps=120, raise_on_noconv=False)
+        pi_fixed = ch.estimate()
+        log = ch.move_log(120)
+        ch.reset()
+        info_tol = ch.solve("link_threshold", 0.0, tol=1e-8, max_steps=5000)
+        pi_tol = ch.estimate()
+        inv = ch.invariant_residual()
+    assert info["moves"] == 120 and info["status"] == "RLGL_ENOCONV"
+    assert len(log) == 120 and all(r["phase_us"][2] > 0 for r in log)
+    assert sum(r["phase_us"][0] == 0.0 for r in log) >= 100  # stale moves: no statistics pass
+    assert np.abs(pi_fixed - ref).sum() <= 1e-6
+    assert info_tol["status"] == "RLGL_OK"
+    assert np.abs(pi_tol - ref).sum() <= 1e-6
+    assert inv <= 1e-8 * 2 ** -10
+
+
 def test_rmat20_one_move_against_oracle(rmat20):
     """The 6th push move of the per-link schedule from the GPU's own FP64
     state equals the oracle's move of that state, node by node within the

@@ -137,13 +137,13 @@ def test_mixed_converges_to_the_stationary_law(tiny, medium, sched):
     assert np.abs(pi - ref).sum() <= 1e-6
     assert resid <= 1e-6
     csr, p = medium
-    with Chain(csr, precision="mixed") as a, Chain(csr, precision="fp64") as b:
+    law, _, delta = oracle.power_iteration(csr, p, tol=1e-13, maxit=200000)
+    assert delta <= 1e-13
+    with Chain(csr, precision="mixed") as a:
         a.set_params(theta_lag=1, **KW)
-        b.set_params(**KW)
-        ia = a.solve(sched, tol=1e-9, max_steps=200000)
-        ib = b.solve(sched, tol=1e-12, max_steps=200000)
-        assert ia["status"] == ib["status"] == "RLGL_OK"
-        assert np.abs(a.estimate() - b.estimate()).sum() <= 2e-6
+        ia = a.solve(sched, tol=1e-10, max_steps=200000)
+        assert ia["status"] == "RLGL_OK"
+        assert np.abs(a.estimate() - law).sum() <= 1e-6
 
 
 def test_rejected_where_the_sweep_does_not_run(tiny):
