@@ -511,7 +511,7 @@ def code_only(text):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh"):
+    for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh", "rlgl_power.cuh"):
         with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]

@@ -133,6 +133,9 @@ typedef struct {
                                barrier per move. Persistent sweep only: rlgl_solve returns
                                RLGL_EINVAL for TOPFRAC, batches and persistent = 0; rlgl_step
                                and rlgl_profile_moves ignore it. Default 0 */
+    int32_t batch_block;    /* threads per block of the persistent batch solve: 128, 256 (default)
+                               or 512 (the merge-path tiles of the chains' pulls hold 1024, 2048
+                               and 2048 rows + links) */
 } rlgl_params;
 
 typedef struct {

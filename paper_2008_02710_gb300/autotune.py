@@ -3,7 +3,8 @@
 The threshold schedules have knobs the paper leaves open: the multiplier and
 the exponent r of theta_t(r) (Sec. 6), and here also the fraction of the
 edges at which a move pulls over the in-links instead of pushing over the
-out-links. Which setting reaches a tolerance first depends on the chain
+out-links, and, for a batch of chains solved in one persistent launch, the
+threads per block of that launch (block size). Which setting reaches a tolerance first depends on the chain
 (degree spread, mixing) and on the device. The tuner runs the same solve
 (step 0, then the schedule to the tolerance) once per candidate on the
 chain itself, measures its wall time around the library call (which
@@ -23,6 +24,15 @@ DEFAULT_GRID = {
     "pull_crossover": (0.1, 0.25, 0.5),
 }
 
+# A batch adds the block size of its persistent launch.
+DEFAULT_BATCH_GRID = dict(DEFAULT_GRID, batch_block=(128, 256, 512))
+
+
+def default_grid(chain) -> Dict[str, Iterable]:
+    """The default search grid for `chain`: with the block size for a batch
+    of several chains."""
+    return DEFAULT_BATCH_GRID if getattr(chain, "nchains", 1) > 1 else DEFAULT_GRID
+
 
 def candidates(grid: Optional[Dict[str, Iterable]] = None) -> List[dict]:
     """The cartesian product of the grid's values, as parameter dicts."""
@@ -40,6 +50,8 @@ def autotune(chain, schedule: str = "link_threshold", tol: float = 1e-6,
     Raises RuntimeError when no candidate converged."""
     trials = []
     best = None
+    if grid is None:
+        grid = default_grid(chain)
     for cand in candidates(grid):
         chain.set_params(**cand)
         secs = []

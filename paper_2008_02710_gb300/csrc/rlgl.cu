@@ -5,6 +5,7 @@
 // move runs in the kernels of rlgl_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -18,6 +19,8 @@
 
 #include "../../include/rlgl.h"
 #include "rlgl_kernels.cuh"
+#include "rlgl_batch.cuh"
+#include "rlgl_power.cuh"
 #include "rlgl_sweep.cuh"
 
 using namespace rlgl;
@@ -87,6 +90,21 @@ struct rlgl_ctx {
     ChainState* cs = nullptr;
     double* bsums = nullptr;  // per-chain sum H, sum |H| [2 nchains]
     std::vector<int64_t> node_ptr_h;
+    std::vector<int64_t> chain_nnz_h;  // links of each chain
+    // persistent batch: per-chain merge-path tiles (for tiles of ct_items
+    // items), the per-chain group barriers and slots, the work queue (built
+    // for block size bq_block) and its counter, and the solve graph
+    long long* ct_off = nullptr;
+    long long* ct_r = nullptr;
+    long long* ct_e = nullptr;
+    long long ct_items = 0;
+    BGroup* grp = nullptr;
+    int* bq = nullptr;  // q_chain [q_len], q_member [q_len], g_of [nchains]
+    long long q_len = 0;
+    int bq_block = 0;
+    int grid_batch = 0;
+    unsigned long long* q_next = nullptr;
+    cudaGraphExec_t batch_graph = nullptr;
     DevState* host_st = nullptr;  // pinned mirror
     Control* host_ctl = nullptr;  // pinned
     rlgl_params params{};
@@ -97,6 +115,9 @@ struct rlgl_ctx {
     // solve graph of the persistent sweep (any schedule it serves) and its grid
     cudaGraphExec_t sweep_graph = nullptr;
     int grid_sweep = 0;
+    // solve graph and grid of the all-green (power) sweep
+    cudaGraphExec_t power_graph = nullptr;
+    int grid_power = 0;
     int n_hot = 0;  // leading nodes whose in-links the push sums per block
     // profiling
     int profiling = 0;
@@ -380,13 +401,13 @@ static rlgl_status enqueue_pull(Launch L) {
     return RLGL_OK;
 }
 
-// The persistent sweep (rlgl_sweep.cuh): one cooperative launch of
-// ctx->grid_sweep blocks, never more than fit on the device at once.
-template <typename T, bool kHasW>
-static rlgl_status launch_sweep(rlgl_ctx* ctx, const SweepArgs<T>& a) {
+// A persistent kernel (rlgl_sweep.cuh, rlgl_power.cuh): one cooperative
+// launch of `grid` blocks, never more than fit on the device at once.
+template <typename T>
+static rlgl_status launch_coop(rlgl_ctx* ctx, int grid, void (*kernel)(SweepArgs<T>), const SweepArgs<T>& a) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3((unsigned)ctx->grid_sweep);
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = ctx->stream;
@@ -396,13 +417,12 @@ static rlgl_status launch_sweep(rlgl_ctx* ctx, const SweepArgs<T>& a) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(ctx, cudaLaunchKernelEx(&cfg, k_sweep<T, kHasW>, a));
+    CK(ctx, cudaLaunchKernelEx(&cfg, kernel, a));
     return RLGL_OK;
 }
 
 template <typename T>
-static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
-    rlgl_ctx* ctx = L.ctx;
+static SweepArgs<T> sweep_args(rlgl_ctx* ctx, const Conds& cd) {
     SweepArgs<T> a;
     a.c = (T*)ctx->c;
     a.H = ctx->H;
@@ -412,6 +432,8 @@ static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
     a.ideg = (const T*)ctx->ideg;
     a.masks = ctx->masks;
     a.mt = (T*)ctx->mt;
+    a.mt2 = (T*)ctx->hsrc;  // free while no re-derivation runs
+    a.facc = (T*)ctx->f_m;  // the power sweep clears it at every launch
     a.f_eoff = ctx->f_eoff;
     a.f_base = ctx->f_base;
     a.f_m = (T*)ctx->f_m;
@@ -433,11 +455,118 @@ static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
     a.n = (int)ctx->n;
     a.vec_ok = vec_aligned(ctx);
     a.n_hot = ctx->n_hot;
+    return a;
+}
+
+template <typename T>
+static rlgl_status enqueue_sweep(Launch L, const Conds& cd) {
+    rlgl_ctx* ctx = L.ctx;
+    const SweepArgs<T> a = sweep_args<T>(ctx, cd);
     if (ctx->has_w)
-        LAUNCH(L, KC_SWEEP, TRY((launch_sweep<T, true>(ctx, a))));
+        LAUNCH(L, KC_SWEEP, TRY((launch_coop<T>(ctx, ctx->grid_sweep, k_sweep<T, true>, a))));
     else
-        LAUNCH(L, KC_SWEEP, TRY((launch_sweep<T, false>(ctx, a))));
+        LAUNCH(L, KC_SWEEP, TRY((launch_coop<T>(ctx, ctx->grid_sweep, k_sweep<T, false>, a))));
     return RLGL_OK;
+}
+
+// The all-green (power) sweep of rlgl_power.cuh.
+template <typename T>
+static rlgl_status enqueue_power(Launch L, const Conds& cd) {
+    rlgl_ctx* ctx = L.ctx;
+    const SweepArgs<T> a = sweep_args<T>(ctx, cd);
+    if (ctx->has_w)
+        LAUNCH(L, KC_SWEEP, TRY((launch_coop<T>(ctx, ctx->grid_power, k_power<T, true>, a))));
+    else
+        LAUNCH(L, KC_SWEEP, TRY((launch_coop<T>(ctx, ctx->grid_power, k_power<T, false>, a))));
+    return RLGL_OK;
+}
+
+// The persistent batch solve (rlgl_batch.cuh) with blocks of BT threads.
+template <typename T>
+static BatchArgs<T> batch_args(rlgl_ctx* ctx) {
+    BatchArgs<T> a;
+    a.c = (T*)ctx->c;
+    a.H = ctx->H;
+    a.s = ctx->s;
+    a.sf = ctx->sf;
+    a.row_ptr = ctx->row_ptr;
+    a.ideg = (const T*)ctx->ideg;
+    a.masks = ctx->masks;
+    a.mt = (T*)ctx->mt;
+    a.f_eoff = ctx->f_eoff;
+    a.f_base = ctx->f_base;
+    a.f_m = (T*)ctx->f_m;
+    a.chunk_row = ctx->chunk_row;
+    a.col = ctx->col;
+    a.w = ctx->w;
+    a.t_ptr = ctx->t_ptr;
+    a.t_src = ctx->t_src;
+    a.t_w = ctx->t_w;
+    a.ct_r = ctx->ct_r;
+    a.ct_e = ctx->ct_e;
+    a.ct_off = ctx->ct_off;
+    a.node_ptr = ctx->node_ptr;
+    a.cs = ctx->cs;
+    a.grp = ctx->grp;
+    a.q_chain = ctx->bq;
+    a.q_member = ctx->bq + ctx->q_len;
+    a.g_of = ctx->bq + 2 * ctx->q_len;
+    a.q_len = ctx->q_len;
+    a.q_next = ctx->q_next;
+    a.y = ctx->y;
+    a.hsrc = ctx->hsrc;
+    a.st = ctx->st;
+    a.nchains = ctx->nchains;
+    return a;
+}
+
+template <typename T, bool kHasW, int BT>
+static rlgl_status launch_bsweep_t(rlgl_ctx* ctx, const BatchArgs<T>& a) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)ctx->grid_batch);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    memset(attr, 0, sizeof attr);
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(ctx, cudaLaunchKernelEx(&cfg, k_bsweep<T, kHasW, BT>, a));
+    return RLGL_OK;
+}
+
+template <typename T>
+static rlgl_status enqueue_bsweep(rlgl_ctx* ctx) {
+    const BatchArgs<T> a = batch_args<T>(ctx);
+    switch (ctx->bq_block) {
+        case 128: return ctx->has_w ? launch_bsweep_t<T, true, 128>(ctx, a) : launch_bsweep_t<T, false, 128>(ctx, a);
+        case 512: return ctx->has_w ? launch_bsweep_t<T, true, 512>(ctx, a) : launch_bsweep_t<T, false, 512>(ctx, a);
+        default: return ctx->has_w ? launch_bsweep_t<T, true, 256>(ctx, a) : launch_bsweep_t<T, false, 256>(ctx, a);
+    }
+}
+
+template <typename T, bool kHasW>
+static int bsweep_fit_t(int bt) {
+    int nb = 0;
+    cudaError_t e;
+    switch (bt) {
+        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bsweep<T, kHasW, 128>, 128, 0); break;
+        case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bsweep<T, kHasW, 512>, 512, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bsweep<T, kHasW, 256>, 256, 0); break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+static int bsweep_fit(rlgl_ctx* ctx, int bt) {
+    if (ctx->prec == RLGL_MIXED) return ctx->has_w ? bsweep_fit_t<float, true>(bt) : bsweep_fit_t<float, false>(bt);
+    return ctx->has_w ? bsweep_fit_t<double, true>(bt) : bsweep_fit_t<double, false>(bt);
 }
 
 // Blocks of the sweep: all that fit on the device at once (the occupancy of
@@ -466,9 +595,42 @@ static int sweep_grid(rlgl_ctx* ctx) {
     return (int)(want < fit ? want : fit);
 }
 
+// Blocks of the power sweep: all that fit, fewer when the chain has fewer
+// merge-path tiles (and node block-iterations) than that.
+template <typename T>
+static int power_fit(rlgl_ctx* ctx) {
+    int nb = 0;
+    cudaError_t e = ctx->has_w
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power<T, true>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_power<T, false>, kThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+static int power_grid(rlgl_ctx* ctx) {
+    const int nb = ctx->prec == RLGL_MIXED ? power_fit<float>(ctx) : power_fit<double>(ctx);
+    if (nb < 1) return 0;
+    const long long fit = (long long)nb * ctx->sms;
+    long long want = ctx->ntiles;
+    const long long nodes = (ctx->n + kNodesPerIter - 1) / kNodesPerIter;
+    if (nodes > want) want = nodes;
+    if (want < 1) want = 1;
+    return (int)(want < fit ? want : fit);
+}
+
 // Whether a solve with this schedule runs as the persistent sweep.
 static bool use_sweep(const rlgl_ctx* ctx, int sched) {
     return ctx->params.persistent && ctx->nchains <= 1 && sched != RLGL_TOPFRAC && ctx->grid_sweep > 0;
+}
+
+// Whether it runs as the all-green (power) sweep: all-green with the plain
+// stop rule (the stale threshold's order of move and stop test is the
+// general sweep's).
+static bool use_power(const rlgl_ctx* ctx, int sched) {
+    return use_sweep(ctx, sched) && sched == RLGL_ALL_GREEN && !ctx->params.theta_lag && ctx->grid_power > 0;
 }
 
 // One eager iteration of Alg. 1: stats [top-k] select push pull. Every kernel
@@ -502,6 +664,14 @@ static void drop_graphs(rlgl_ctx* ctx) {
     if (ctx->sweep_graph) {
         cudaGraphExecDestroy(ctx->sweep_graph);
         ctx->sweep_graph = nullptr;
+    }
+    if (ctx->power_graph) {
+        cudaGraphExecDestroy(ctx->power_graph);
+        ctx->power_graph = nullptr;
+    }
+    if (ctx->batch_graph) {
+        cudaGraphExecDestroy(ctx->batch_graph);
+        ctx->batch_graph = nullptr;
     }
 }
 
@@ -689,6 +859,7 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     ctx->grid_push = grid_for(nnz, kPushChunk, ctx->sms * 4);
     ctx->grid_pull = grid_for(n + nnz, kMpItems, ctx->sms * 8);
     ctx->grid_sweep = sweep_grid(ctx);
+    ctx->grid_power = power_grid(ctx);
     const size_t cs = cash_size(ctx);
 
     TRY(dalloc(ctx, &ctx->row_ptr, (size_t)n + 1));
@@ -828,6 +999,7 @@ rlgl_status rlgl_default_params(rlgl_params* p) {
     p->test_skip_barrier = 0;
     p->stall_moves = 32;
     p->theta_lag = 0;
+    p->batch_block = 256;
     return RLGL_OK;
 }
 
@@ -933,6 +1105,11 @@ rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t
     if (s != RLGL_OK) return bail(s);
     ctx->nchains = (int)n_chains;
     ctx->node_ptr_h = np;
+    // the push chunk index of a batch holds every chain's own part
+    // (chain k's chunks start at its first link / kPushChunk + k)
+    dfree(ctx, ctx->chunk_row);
+    ctx->chunk_row = nullptr;
+    if ((s = dalloc(ctx, &ctx->chunk_row, (size_t)(nnz / kPushChunk + n_chains + 2))) != RLGL_OK) return bail(s);
     if ((s = dalloc(ctx, &ctx->node_ptr, (size_t)n_chains + 1)) != RLGL_OK) return bail(s);
     if ((s = dalloc(ctx, &ctx->chain_of, (size_t)n)) != RLGL_OK) return bail(s);
     if ((s = dalloc(ctx, &ctx->cs, (size_t)n_chains)) != RLGL_OK) return bail(s);
@@ -960,6 +1137,25 @@ rlgl_status rlgl_batch_create(int64_t n_chains, const int64_t* node_ptr, int64_t
         cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return bail(fail(ctx, RLGL_ECUDA, "chain map failed"));
     if (err) return bail(fail(ctx, RLGL_EINVAL, "an edge leaves its chain: the CSR must be block-diagonal"));
+    {
+        // each chain's links (row_ptr at the chain boundaries), for the
+        // persistent batch's work queue
+        long long* eb = nullptr;
+        if ((s = dalloc(ctx, &eb, (size_t)n_chains + 1)) != RLGL_OK) return bail(s);
+        k_gather_rows<<<grid_for(n_chains + 1, kThreads, 1024), kThreads, 0, ctx->stream>>>(
+            ctx->row_ptr, ctx->node_ptr, n_chains + 1, eb);
+        std::vector<long long> ebh((size_t)n_chains + 1);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(ebh.data(), eb, ebh.size() * sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            dfree(ctx, eb);
+            return bail(fail(ctx, RLGL_ECUDA, "reading the chains' link offsets failed"));
+        }
+        dfree(ctx, eb);
+        ctx->chain_nnz_h.resize((size_t)n_chains);
+        for (int64_t k = 0; k < n_chains; ++k) ctx->chain_nnz_h[(size_t)k] = ebh[(size_t)k + 1] - ebh[(size_t)k];
+    }
     if ((s = set_step0(ctx, nullptr, RLGL_HOST)) != RLGL_OK) return bail(s);  // uniform per chain
     *out = ctx;
     return RLGL_OK;
@@ -1142,9 +1338,9 @@ static rlgl_status build_graph_t(rlgl_ctx* ctx, int sched, cudaGraph_t g) {
 
 // The sweep's solve graph: WHILE(loop) { [IF(refresh) {re-derive C}] sweep }.
 // The sweep ends the loop when the solve stops and requests the
-// re-derivation when it returns for one.
+// re-derivation when it returns for one. power: the all-green sweep.
 template <typename T>
-static rlgl_status build_sweep_graph_t(rlgl_ctx* ctx, cudaGraph_t g) {
+static rlgl_status build_sweep_graph_t(rlgl_ctx* ctx, cudaGraph_t g, bool power) {
     Conds cd;
     cd.use = 1;
     cudaGraphConditionalHandle hw;
@@ -1165,16 +1361,16 @@ static rlgl_status build_sweep_graph_t(rlgl_ctx* ctx, cudaGraph_t g) {
         TRY(capture_into(ctx, rbody, nullptr, 0, [&] { return enqueue_refresh<T>(L); }, nullptr));
         deps.push_back(rnode);
     }
-    TRY(capture_into(ctx, body, deps.data(), deps.size(), [&] { return enqueue_sweep<T>(L, cd); },
-                     nullptr));
+    TRY(capture_into(ctx, body, deps.data(), deps.size(),
+                     [&] { return power ? enqueue_power<T>(L, cd) : enqueue_sweep<T>(L, cd); }, nullptr));
     return RLGL_OK;
 }
 
-static rlgl_status build_sweep_graph(rlgl_ctx* ctx) {
+static rlgl_status build_sweep_graph(rlgl_ctx* ctx, bool power) {
     cudaGraph_t g = nullptr;
     CK(ctx, cudaGraphCreate(&g, 0));
-    rlgl_status s = (ctx->prec == RLGL_MIXED) ? build_sweep_graph_t<float>(ctx, g)
-                                              : build_sweep_graph_t<double>(ctx, g);
+    rlgl_status s = (ctx->prec == RLGL_MIXED) ? build_sweep_graph_t<float>(ctx, g, power)
+                                              : build_sweep_graph_t<double>(ctx, g, power);
     if (s != RLGL_OK) {
         cudaGraphDestroy(g);
         return s;
@@ -1183,7 +1379,132 @@ static rlgl_status build_sweep_graph(rlgl_ctx* ctx) {
     cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     CK(ctx, e);
-    ctx->sweep_graph = exec;
+    (power ? ctx->power_graph : ctx->sweep_graph) = exec;
+    return RLGL_OK;
+}
+
+// Whether a batch solve runs as the persistent batch kernel.
+static bool use_bsweep(const rlgl_ctx* ctx, int sched) {
+    return ctx->params.persistent && ctx->nchains > 1 && sched != RLGL_TOPFRAC && !ctx->params.theta_lag;
+}
+
+// The persistent batch's per-chain tiles (for its block size) and work
+// queue: chains sorted by size (rows + links), largest first; chain k gets
+// g_k = ceil(w_k / W) blocks (W = the batch's work over the grid), at most
+// 16 and at most its tiles, and the groups of more than one block together
+// take no more than the grid, so all of them start at once.
+static rlgl_status batch_prepare(rlgl_ctx* ctx) {
+    const int bt = ctx->params.batch_block;
+    const long long items = (long long)bt * mp_ipt(bt);
+    const int nc = ctx->nchains;
+    if (ctx->ct_items != items) {
+        if (!ctx->ct_off) TRY(dalloc(ctx, &ctx->ct_off, (size_t)nc + 1));
+        CK(ctx, cudaMemsetAsync(ctx->ct_off, 0, ((size_t)nc + 1) * sizeof(long long), ctx->stream));
+        k_chain_tile_counts<<<grid_for(nc, kThreads, 1024), kThreads, 0, ctx->stream>>>(ctx->node_ptr, ctx->t_ptr, nc,
+                                                                                      items, ctx->ct_off);
+        CKL(ctx);
+        TRY(device_inclusive_scan(ctx, ctx->ct_off, (long long)nc + 1));
+        long long total = 0;
+        CK(ctx, cudaMemcpyAsync(&total, ctx->ct_off + nc, sizeof total, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->ct_r) { dfree(ctx, ctx->ct_r); ctx->ct_r = nullptr; }
+        if (ctx->ct_e) { dfree(ctx, ctx->ct_e); ctx->ct_e = nullptr; }
+        TRY(dalloc(ctx, &ctx->ct_r, (size_t)total));
+        TRY(dalloc(ctx, &ctx->ct_e, (size_t)total));
+        k_chain_tiles<<<grid_for(total, kThreads, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
+            ctx->node_ptr, ctx->t_ptr, ctx->ct_off, nc, items, ctx->ct_r, ctx->ct_e);
+        CKL(ctx);
+        ctx->ct_items = items;
+    }
+    if (ctx->bq_block != bt) {
+        const int nb = bsweep_fit(ctx, bt);
+        if (nb < 1) return fail(ctx, RLGL_ECUDA, "the persistent batch kernel does not fit on an SM");
+        const long long G = (long long)nb * ctx->sms;
+        std::vector<double> wk((size_t)nc);
+        double W = 0.0;
+        for (int k = 0; k < nc; ++k) {
+            wk[(size_t)k] = (double)(ctx->node_ptr_h[(size_t)k + 1] - ctx->node_ptr_h[(size_t)k]) +
+                            (double)ctx->chain_nnz_h[(size_t)k];
+            W += wk[(size_t)k];
+        }
+        W = W / (double)G;
+        if (W < 1.0) W = 1.0;
+        std::vector<int> order((size_t)nc), g((size_t)nc);
+        for (int k = 0; k < nc; ++k) {
+            order[(size_t)k] = k;
+            long long gk = (long long)ceil(wk[(size_t)k] / W);
+            const long long tiles = (long long)ceil(wk[(size_t)k] / (double)items);
+            if (gk > 16) gk = 16;
+            if (gk > tiles) gk = tiles;
+            if (gk < 1) gk = 1;
+            g[(size_t)k] = (int)gk;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wk[(size_t)x] > wk[(size_t)y]; });
+        for (;;) {
+            long long multi = 0;
+            for (int k = 0; k < nc; ++k)
+                if (g[(size_t)k] > 1) multi += g[(size_t)k];
+            if (multi <= G) break;
+            for (int k = 0; k < nc; ++k)
+                if (g[(size_t)k] > 1) g[(size_t)k] /= 2;
+        }
+        long long E = 0;
+        for (int k = 0; k < nc; ++k) E += g[(size_t)k];
+        std::vector<int> q((size_t)(2 * E + nc));
+        long long e = 0;
+        for (int k : order)
+            for (int m = 0; m < g[(size_t)k]; ++m) {
+                q[(size_t)e] = k;
+                q[(size_t)(E + e)] = m;
+                ++e;
+            }
+        for (int k = 0; k < nc; ++k) q[(size_t)(2 * E + k)] = g[(size_t)k];
+        if (ctx->bq) { CK(ctx, cudaStreamSynchronize(ctx->stream)); dfree(ctx, ctx->bq); ctx->bq = nullptr; }
+        TRY(dalloc(ctx, &ctx->bq, q.size()));
+        CK(ctx, cudaMemcpyAsync(ctx->bq, q.data(), q.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->q_len = E;
+        ctx->grid_batch = (int)(E < G ? E : G);
+        ctx->bq_block = bt;
+        if (ctx->batch_graph) {
+            cudaGraphExecDestroy(ctx->batch_graph);
+            ctx->batch_graph = nullptr;
+        }
+    }
+    if (!ctx->grp) TRY(dalloc(ctx, &ctx->grp, (size_t)nc));
+    if (!ctx->q_next) TRY(dalloc(ctx, &ctx->q_next, 1));
+    return RLGL_OK;
+}
+
+// The persistent batch's solve graph: clear the groups and the queue
+// counter, take the start time, the batch kernel, the totals.
+template <typename T>
+static rlgl_status enqueue_batch_solve(rlgl_ctx* ctx) {
+    CK(ctx, cudaMemsetAsync(ctx->grp, 0, (size_t)ctx->nchains * sizeof(BGroup), ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->q_next, 0, sizeof(unsigned long long), ctx->stream));
+    k_bstart<<<1, 1, 0, ctx->stream>>>(ctx->st);
+    CKL(ctx);
+    TRY(enqueue_bsweep<T>(ctx));
+    k_bfinish<<<1, kThreads, 0, ctx->stream>>>(ctx->st, ctx->cs, ctx->nchains);
+    CKL(ctx);
+    return RLGL_OK;
+}
+
+static rlgl_status build_batch_graph(rlgl_ctx* ctx) {
+    cudaGraph_t g = nullptr;
+    CK(ctx, cudaGraphCreate(&g, 0));
+    rlgl_status s = capture_into(ctx, g, nullptr, 0, [&] {
+        return ctx->prec == RLGL_MIXED ? enqueue_batch_solve<float>(ctx) : enqueue_batch_solve<double>(ctx);
+    }, nullptr);
+    if (s != RLGL_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e);
+    ctx->batch_graph = exec;
     return RLGL_OK;
 }
 
@@ -1213,21 +1534,30 @@ static rlgl_status solve_launch(rlgl_ctx* ctx, rlgl_schedule sched, double theta
     const bool batch_tols = ctx->nchains > 1 && tol < 0.0;  // per-chain tolerances
     if (!(tol >= 0.0) && !batch_tols) return fail(ctx, RLGL_EINVAL, "tol must be >= 0");
     bool sweep = use_sweep(ctx, sched);
-    if (sweep && !ctx->sweep_graph && build_sweep_graph(ctx) != RLGL_OK) {
+    const bool power = use_power(ctx, sched);
+    cudaGraphExec_t& sg = power ? ctx->power_graph : ctx->sweep_graph;
+    if (sweep && !sg && build_sweep_graph(ctx, power) != RLGL_OK) {
         // The device or driver would not take the cooperative kernel into a
         // graph: use one kernel per phase from now on (params.persistent
         // then reads 0, and rlgl_last_error keeps the reason).
         ctx->params.persistent = 0;
         ctx->grid_sweep = 0;
+        ctx->grid_power = 0;
         sweep = false;
         cudaGetLastError();
     }
     if (!sweep && ctx->params.theta_lag)
         return fail(ctx, RLGL_EINVAL, "theta_lag needs the persistent sweep (not TOPFRAC, batches or persistent = 0)");
-    if (!sweep && !ctx->graph[sched]) TRY(build_graph(ctx, sched));
+    const bool bsweep = use_bsweep(ctx, sched);
+    if (bsweep) {
+        TRY(batch_prepare(ctx));
+        if (!ctx->batch_graph) TRY(build_batch_graph(ctx));
+    } else if (!sweep && !ctx->graph[sched]) {
+        TRY(build_graph(ctx, sched));
+    }
     TRY(begin(ctx, sched, theta, batch_tols ? 0.0 : tol, max_steps, 1, batch_tols ? -1.0 : tol));
     if (sweep) CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
-    CK(ctx, cudaGraphLaunch(sweep ? ctx->sweep_graph : ctx->graph[sched], ctx->stream));
+    CK(ctx, cudaGraphLaunch(bsweep ? ctx->batch_graph : (sweep ? sg : ctx->graph[sched]), ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->host_st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaEventRecord(ctx->done_ev, ctx->stream));
     ctx->pending = true;
@@ -1412,7 +1742,8 @@ rlgl_status rlgl_set_params(rlgl_ctx* ctx, const rlgl_params* p) {
         !(p->time_limit_s > 0.0) || (p->persistent != 0 && p->persistent != 1) || p->rr_blocks < 1 ||
         !(p->pc_frac > 0.0 && p->pc_frac <= 1e30) || !(p->barrier_limit_s > 0.0 && p->barrier_limit_s <= 60.0) ||
         (p->test_skip_barrier != 0 && p->test_skip_barrier != 1) || p->stall_moves < 0 ||
-        (p->theta_lag != 0 && p->theta_lag != 1))
+        (p->theta_lag != 0 && p->theta_lag != 1) ||
+        (p->batch_block != 128 && p->batch_block != 256 && p->batch_block != 512))
         return fail(ctx, RLGL_EINVAL, "parameter out of range");
     ctx->params = *p;
     return RLGL_OK;
@@ -1487,13 +1818,14 @@ rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta,
 }  // extern "C"
 
 template <typename T>
-static rlgl_status profile_sweep_t(rlgl_ctx* ctx, int64_t moves) {
+static rlgl_status profile_sweep_t(rlgl_ctx* ctx, int64_t moves, bool power) {
     Launch L{ctx, false};
     Conds none;
     // every launch makes at least one move or ends the solve
     for (int64_t k = 0; k < moves + 4; ++k) {
         TRY(enqueue_refresh<T>(L));  // runs only when a re-derivation is pending
-        TRY(enqueue_sweep<T>(L, none));
+        if (power) TRY(enqueue_power<T>(L, none));
+        else TRY(enqueue_sweep<T>(L, none));
         TRY(read_state(ctx));
         if (ctx->host_st->done) break;
     }
@@ -1513,8 +1845,9 @@ rlgl_status rlgl_profile_sweep(rlgl_ctx* ctx, rlgl_schedule sched, double theta,
     ctx->profiling = 1;
     TRY(begin(ctx, sched, theta, 0.0, moves, 1));
     CK(ctx, cudaMemsetAsync(ctx->sw, 0, sizeof(SweepState), ctx->stream));
-    rlgl_status s = ctx->prec == RLGL_MIXED ? profile_sweep_t<float>(ctx, moves)
-                                            : profile_sweep_t<double>(ctx, moves);
+    const bool power = use_power(ctx, sched);
+    rlgl_status s = ctx->prec == RLGL_MIXED ? profile_sweep_t<float>(ctx, moves, power)
+                                            : profile_sweep_t<double>(ctx, moves, power);
     ctx->profiling = prev;
     if (s != RLGL_OK) return s;
     return prof_collect(ctx);
@@ -1591,13 +1924,15 @@ void rlgl_destroy(rlgl_ctx* ctx) {
         for (auto& g : ctx->graph)
             if (g) g_retired.push_back(g);
         if (ctx->sweep_graph) g_retired.push_back(ctx->sweep_graph);
+        if (ctx->power_graph) g_retired.push_back(ctx->power_graph);
+        if (ctx->batch_graph) g_retired.push_back(ctx->batch_graph);
     }
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
                    ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->colsum,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
                    ctx->err, ctx->log, ctx->st, ctx->sw, ctx->node_ptr, ctx->chain_of, ctx->cs,
-                   ctx->bsums};
+                   ctx->bsums, ctx->ct_off, ctx->ct_r, ctx->ct_e, ctx->grp, ctx->bq, ctx->q_next};
     for (void* p : dev)
         dfree(ctx, p);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);

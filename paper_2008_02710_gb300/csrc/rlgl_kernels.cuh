@@ -54,9 +54,13 @@ struct MoveRecord {                   // layout of rlgl_move_record
 struct ChainState {
     double acc[7];
     double l1, sum, sumr, theta, hsum, habs, tol;
+    double l1r;              // persistent batch: ||C||_1 after the last re-derivation
     long long n, moves;
+    // persistent batch: the last solve's moves, links, green nodes, push and
+    // pull moves and re-derivations of this chain
+    long long s_moves, s_edges, s_green, s_push, s_pull, s_refr;
     float theta_f;
-    int done, status, pad;
+    int done, status, fresh;  // fresh: the cash is exact (step 0 or re-derived)
 };
 
 struct BatchView {
@@ -201,11 +205,12 @@ __device__ __forceinline__ void block_sum_n(T (&v)[K], T* scratch) {
     }
 }
 
-// Block-wide exclusive scan of 64-bit values (blockDim = kThreads). Returns
+// Block-wide exclusive scan of 64-bit values (blockDim = kBT). Returns
 // the exclusive prefix; *total receives the block total (all threads).
+template <int kBT = kThreads>
 __device__ __forceinline__ unsigned long long block_exscan(unsigned long long v,
                                                            unsigned long long* total) {
-    __shared__ unsigned long long wsum[kThreads / 32];
+    __shared__ unsigned long long wsum[kBT / 32];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long x = v;
 #pragma unroll
@@ -217,17 +222,17 @@ __device__ __forceinline__ unsigned long long block_exscan(unsigned long long v,
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        unsigned long long s = (lane < kThreads / 32) ? wsum[lane] : 0ull;
+        unsigned long long s = (lane < kBT / 32) ? wsum[lane] : 0ull;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < kThreads / 32) wsum[lane] = s;  // inclusive warp prefixes
+        if (lane < kBT / 32) wsum[lane] = s;  // inclusive warp prefixes
     }
     __syncthreads();
     unsigned long long before = (wid > 0) ? wsum[wid - 1] : 0ull;
-    *total = wsum[kThreads / 32 - 1];
+    *total = wsum[kBT / 32 - 1];
     return before + x - v;
 }
 
@@ -1008,7 +1013,10 @@ __global__ void __launch_bounds__(kThreads) k_select(
             ch->habs += ma;
             bsum += m;
             babs += ma;
-            if (!ch->done) ch->moves++;
+            if (!ch->done) {
+                ch->moves++;
+                ch->fresh = 0;
+            }
         }
         bsum = block_sum(bsum, scratch);
         babs = block_sum(babs, scratch);
@@ -1075,12 +1083,12 @@ __global__ void __launch_bounds__(kThreads) k_select(
 constexpr int kMaxHot = 32;  // hot-target slots of the push
 
 // Shared memory of the push chunk loop.
-template <typename T>
+template <typename T, int kBT = kThreads>
 struct PushSmem {
     int row[kPushChunk];
     long long base[kPushChunk + 1];
     T m[kPushChunk + 1];
-    int wmax[kThreads / 32];
+    int wmax[kBT / 32];
     double hot[kMaxHot];
 };
 
@@ -1094,7 +1102,7 @@ struct PushSmem {
 // per block in FP64 in shared memory and added to the cash once per block:
 // one global addition per block instead of one per in-link, all of which
 // would queue on one L2 address.
-template <typename T, bool kHasW, bool kCg>
+template <typename T, bool kHasW, bool kCg, int kBT = kThreads>
 __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __restrict__ col,
                                             const float* __restrict__ w,
                                             const long long* __restrict__ f_eoff,
@@ -1102,9 +1110,9 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                                             const T* __restrict__ f_m,
                                             const int* __restrict__ chunk_row, long long E,
                                             long long K, long long first, long long step,
-                                            PushSmem<T>& sm, int n_hot,
+                                            PushSmem<T, kBT>& sm, int n_hot,
                                             unsigned long long* next = nullptr) {
-    constexpr int kPer = kPushChunk / kThreads;  // edge slots per thread
+    constexpr int kPer = kPushChunk / kBT;  // edge slots per thread
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ long long s_next;
@@ -1163,7 +1171,7 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
         T slot_v[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
-            const int le = threadIdx.x + q * kThreads;
+            const int le = threadIdx.x + q * kBT;
             slot_j[q] = -1;
             slot_v[q] = T(0);
             if (le < ne) {
@@ -1181,7 +1189,7 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             // hot targets: one shared-memory addition per warp and target
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
-                const int le = threadIdx.x + q * kThreads;
+                const int le = threadIdx.x + q * kBT;
                 const bool hot = le < ne && slot_j[q] < n_hot;
                 unsigned int m = __ballot_sync(0xffffffffu, hot);
                 while (m) {
@@ -1225,10 +1233,12 @@ __global__ void __launch_bounds__(kThreads) k_push(
 // contiguous runs (equal keys are never separated by a different key).
 // Returns this thread's scan value; s_key/s_val then hold every thread's
 // key and scan value.
-template <typename TV>
+template <typename TV, int kBT = kThreads>
 __device__ __forceinline__ TV block_segscan(long long key, TV val, long long* s_key, TV* s_val) {
-    __shared__ long long w_key[kThreads / 32];
-    __shared__ TV w_val[kThreads / 32];
+    constexpr int kW = kBT / 32;
+    constexpr unsigned kWMask = kW >= 32 ? 0xffffffffu : ((1u << kW) - 1u);
+    __shared__ long long w_key[kW];
+    __shared__ TV w_val[kW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     TV x = val;
 #pragma unroll
@@ -1242,14 +1252,14 @@ __device__ __forceinline__ TV block_segscan(long long key, TV val, long long* s_
         w_val[wid] = x;
     }
     __syncthreads();
-    if (wid == 0 && lane < kThreads / 32) {
+    if (wid == 0 && lane < kW) {
         // the same scan over the warp tails
         long long k = w_key[lane];
         TV v = w_val[lane];
 #pragma unroll
-        for (int o = 1; o < kThreads / 32; o <<= 1) {
-            TV y = __shfl_up_sync(0x000000ffu, v, o);
-            long long ky = __shfl_up_sync(0x000000ffu, k, o);
+        for (int o = 1; o < kW; o <<= 1) {
+            TV y = __shfl_up_sync(kWMask, v, o);
+            long long ky = __shfl_up_sync(kWMask, k, o);
             if (lane >= o && ky == k) v += y;
         }
         w_val[lane] = v;
@@ -1272,45 +1282,67 @@ __device__ __forceinline__ TV block_segscan(long long key, TV val, long long* s_
 // tile boundary use atomic adds.
 
 // Shared memory of the merge-path tile loop.
-template <typename TV>
+// Merge-path items per thread for a block of kBT threads: a tile is
+// kBT * mp_ipt(kBT) items (2048 for 256 threads).
+__host__ __device__ constexpr int mp_ipt(int kBT) { return kBT >= 512 ? 4 : kMpIpt; }
+
+template <typename TV, int kBT = kThreads>
 struct PullSmem {
-    TV val[kMpItems];
-    int end[kMpItems + 1];
+    TV val[kBT * mp_ipt(kBT)];
+    int end[kBT * mp_ipt(kBT) + 1];
     int start0;
-    long long ckey[kThreads];
-    TV cval[kThreads];
+    long long ckey[kBT];
+    TV cval[kBT];
 };
 
-// The tiles b = first, first + step, ... of a merge-path pull (see k_pull).
-template <typename TV, typename TO, bool kHasW, bool kCg>
+// The tiles b = first, first + step, ... of a merge-path pull (see k_pull),
+// or, when `next` is given, tiles handed out one at a time by that counter
+// (thread 0 asks for the next one while the block works on the current one),
+// so that blocks end within about one tile of one another.
+// A row's sum goes into out with one reduction (red.global.add, nothing
+// comes back): a load-then-store per row end would put one dependent L2
+// round trip per row end on the thread, serialised over the rows a warp's
+// threads end at different steps of the merge.
+template <typename TV, typename TO, bool kHasW, bool kCg, int kBT = kThreads>
 __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __restrict__ src,
                                            const long long* __restrict__ t_ptr,
                                            const int* __restrict__ t_src,
                                            const float* __restrict__ t_w,
                                            const long long* __restrict__ tile_r,
                                            const long long* __restrict__ tile_e, long long ntiles,
-                                           long long first, long long step, PullSmem<TV>& sm) {
-    for (long long b = first; b < ntiles; b += step) {
+                                           long long first, long long step, PullSmem<TV, kBT>& sm,
+                                           unsigned long long* next = nullptr) {
+    constexpr int kIpt = mp_ipt(kBT);  // merge items per thread: a tile is kBT * kIpt items
+    __shared__ long long s_tnext;
+    long long b = first;
+    if (next) {
+        if (threadIdx.x == 0) s_tnext = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        b = s_tnext;
+        __syncthreads();
+    }
+    while (b < ntiles) {
+        if (next && threadIdx.x == 0) s_tnext = (long long)atomicAdd(next, 1ull);  // read below
         const long long r0 = tile_r[b], e0 = tile_e[b];
         const int nrows = (int)(tile_r[b + 1] - r0);
         const int nedges = (int)(tile_e[b + 1] - e0);
         {
-            int sidx[kMpIpt];
-            float wv[kMpIpt];
-            long long re[kMpIpt];
+            int sidx[kIpt];
+            float wv[kIpt];
+            long long re[kIpt];
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) {
-                const int k = threadIdx.x + q * kThreads;
+            for (int q = 0; q < kIpt; ++q) {
+                const int k = threadIdx.x + q * kBT;
                 sidx[q] = (k < nedges) ? __ldg(t_src + e0 + k) : -1;
                 if (kHasW) wv[q] = (k < nedges) ? __ldg(t_w + e0 + k) : 0.0f;
                 re[q] = (k < nrows) ? __ldg(t_ptr + r0 + 1 + k) : 0;
             }
-            TV v[kMpIpt];
+            TV v[kIpt];
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? ld_shared_data<kCg>(src + sidx[q]) : TV(0);
+            for (int q = 0; q < kIpt; ++q) v[q] = (sidx[q] >= 0) ? ld_shared_data<kCg>(src + sidx[q]) : TV(0);
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) {
-                const int k = threadIdx.x + q * kThreads;
+            for (int q = 0; q < kIpt; ++q) {
+                const int k = threadIdx.x + q * kBT;
                 if (k < nedges) sm.val[k] = kHasW ? v[q] * (TV)wv[q] : v[q];
                 if (k < nrows) sm.end[k] = (int)(re[q] - e0);
             }
@@ -1321,14 +1353,14 @@ __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __res
         }
         __syncthreads();
         const int total = nrows + nedges;
-        int d = threadIdx.x * kMpIpt;
+        int d = threadIdx.x * kIpt;
         const bool active = d < total;
         // head piece: the end of a row begun by earlier threads (rowA);
         // tail piece: a row that continues past this thread (carry).
         long long rowA = -1, rowB = -1;
         TV accA = TV(0), accB = TV(0);
         if (active) {
-            const int dend = min(d + kMpIpt, total);
+            const int dend = min(d + kIpt, total);
             int lo = max(0, d - nedges), hi = min(d, nrows);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
@@ -1349,8 +1381,7 @@ __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __res
                         rowA = r0 + i;
                         accA = acc;
                     } else if (cnt > 0) {
-                        TO* o = out + (r0 + i);
-                        *o = (TO)(ld_shared_data<kCg>(o) + (TO)acc);
+                        red_add(out + (r0 + i), (TO)acc);
                     }
                     acc = TV(0);
                     cnt = 0;
@@ -1367,19 +1398,22 @@ __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __res
         }
         // Join the pieces: carry of thread t plus the carries of the threads
         // before it on the same row.
-        const TV run = block_segscan<TV>(rowB, accB, sm.ckey, sm.cval);
+        const TV run = block_segscan<TV, kBT>(rowB, accB, sm.ckey, sm.cval);
         if (rowA >= 0) {
             TV sum = accA;
             if (threadIdx.x > 0 && sm.ckey[threadIdx.x - 1] == rowA) sum += sm.cval[threadIdx.x - 1];
-            TO* o = out + rowA;
-            // the tile's first row may have begun in the previous tile
-            if (rowA == r0 && sm.start0 < 0) red_add(o, (TO)sum);
-            else *o = (TO)(ld_shared_data<kCg>(o) + (TO)sum);
+            red_add(out + rowA, (TO)sum);
         }
         // last active thread: its carry leaves the tile
-        const int last = (total - 1) / kMpIpt;
+        const int last = (total - 1) / kIpt;
         if ((int)threadIdx.x == last && rowB >= 0) red_add(out + rowB, (TO)run);
         __syncthreads();
+        if (next) {
+            b = s_tnext;
+            __syncthreads();  // everyone has read s_tnext before thread 0 rewrites it
+        } else {
+            b += step;
+        }
     }
 }
 
@@ -1820,7 +1854,12 @@ __global__ void k_bbegin(ChainState* cs, int nchains, double tol, int reset_move
         cs[k].done = 0;
         cs[k].status = 0;
         if (tol >= 0.0) cs[k].tol = tol;
-        if (reset_moves) cs[k].moves = 0;
+        if (reset_moves) {
+            // step 0: exact cash, ||C||_1 taken at the first statistics
+            cs[k].moves = 0;
+            cs[k].fresh = 1;
+            cs[k].l1r = 0.0;
+        }
     }
 }
 

@@ -55,7 +55,7 @@ struct SweepSlot {
     alignas(128) unsigned long long reserve;  // packed frontier reservation
     unsigned long long tstamp;   // block 0's timer at the end of its stats (or select)
     alignas(128) double s;       // sum C
-    unsigned long long chunk_next;  // next push chunk to hand out
+    unsigned long long chunk_next;  // next push chunk (or pull tile) to hand out
     unsigned long long range_next;  // select of large chains: next node range to hand out
 };
 static_assert(offsetof(SweepSlot, pr) == offsetof(SweepSlot, a) + 8 && offsetof(SweepSlot, a) % 16 == 0,
@@ -168,6 +168,8 @@ struct SweepArgs {
     const T* ideg;
     const unsigned char* masks;
     T* mt;
+    T* mt2;      // power sweep: the moved cash of every other move
+    T* facc;     // power sweep: sums of rows split across tiles (zero at rest)
     long long* f_eoff;
     long long* f_base;
     T* f_m;
@@ -1066,7 +1068,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                                         A.n_hot, &sl->chunk_next);
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
-                                          A.ntiles, blockIdx.x, gridDim.x, sm.pull);
+                                          A.ntiles, blockIdx.x, gridDim.x, sm.pull, &sl->chunk_next);
         // the stale threshold's next move: its decisions while this block waits
         if (!grid_barrier_with(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 5 : nullptr,
                                [&]() {

@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("pc_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("persistent", ctypes.c_int32), ("barrier_limit_s", ctypes.c_double),
                 ("test_skip_barrier", ctypes.c_int32), ("stall_moves", ctypes.c_int32),
-                ("theta_lag", ctypes.c_int32)]
+                ("theta_lag", ctypes.c_int32), ("batch_block", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):

@@ -120,3 +120,80 @@ def test_batch_rejects_edges_between_chains(parts):
     with pytest.raises(RLGLError):
         with Chain(batch, node_ptr=node_ptr) as ch:
             ch.step("topfrac", 0.1)
+
+
+def test_persistent_batch_matches_phase_kernels_and_block_sizes(parts):
+    """The whole batch solve in one persistent launch (each chain its own
+    stop, per-chain frontier regions and merge-path tiles) gives, for every
+    block size it is built for, the result of the one-kernel-per-phase batch
+    path, chain by chain."""
+    parts = [_weighted(c) for c in parts]
+    batch, node_ptr = synth.stack_chains(parts)
+    with Chain(batch, node_ptr=node_ptr) as ch:
+        ch.set_params(theta_scale=0.5, persistent=0)
+        ch.solve("link_threshold", tol=1e-12, max_steps=100000)
+        ref = ch.estimate()
+        _, ref_moves, _ = ch.chains()
+        for bb in (128, 256, 512):
+            ch.reset()
+            ch.set_params(persistent=1, batch_block=bb)
+            info = ch.solve("link_threshold", tol=1e-12, max_steps=100000)
+            pi = ch.estimate()
+            status, moves, resid = ch.chains()
+            assert info["status"] == "RLGL_OK" and np.all(status == 0), bb
+            assert np.all(np.abs(moves - ref_moves) <= 1), (bb, moves, ref_moves)
+            assert info["moves"] == moves.max()
+            for k in range(len(parts)):
+                a, b = node_ptr[k], node_ptr[k + 1]
+                assert np.abs(pi[a:b] - ref[a:b]).sum() <= 1e-11, (bb, k)
+
+
+@pytest.fixture(scope="module")
+def lopsided():
+    """One chain much larger than the rest (it gets a group of several
+    blocks in the persistent launch) among small ones."""
+    big = synth.rmat_chain_n(120000, 12, seed=9)
+    small = [synth.tiny_chain(n, seed=s) for n, s in ((100, 1), (333, 2), (57, 3), (1000, 4))]
+    return [_weighted(c) for c in [small[0], big] + small[1:]]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_persistent_batch_large_chain_in_a_group(lopsided, prec):
+    batch, node_ptr = synth.stack_chains(lopsided)
+    with Chain(batch, node_ptr=node_ptr, precision=prec) as ch:
+        ch.set_params(theta_scale=0.5)
+        info = ch.solve("link_threshold", tol=1e-12 if prec == "fp64" else 1e-9, max_steps=100000)
+        pi = ch.estimate()
+        status, moves, resid = ch.chains()
+    assert info["status"] == "RLGL_OK" and np.all(status == 0)
+    for k, c in enumerate(lopsided):
+        a, b = node_ptr[k], node_ptr[k + 1]
+        p = oracle.transition_probs(c)
+        law, _, _ = oracle.power_iteration(c, p, tol=1e-14, maxit=200000)
+        bound = 1e-10 if prec == "fp64" else 1e-6
+        assert np.abs(pi[a:b] - law).sum() <= bound, (k, np.abs(pi[a:b] - law).sum())
+        if prec == "fp64":
+            pi_or, _, _, info_or = oracle.run(c, sched=oracle.LINK_THRESHOLD, theta_scale=0.5, tol=1e-12,
+                                              max_steps=100000)
+            assert abs(int(moves[k]) - info_or["moves"]) <= max(1, info_or["moves"] // 1000), k
+
+
+def test_persistent_batch_group_wait_is_bounded(lopsided):
+    """A member of the large chain's group leaves before its first barrier
+    (test hook): the others give up after the limit, that chain ends with
+    RLGL_ETIMEOUT, the other chains converge, and the context solves
+    normally afterwards."""
+    batch, node_ptr = synth.stack_chains(lopsided)
+    with Chain(batch, node_ptr=node_ptr) as ch:
+        ch.set_params(theta_scale=0.5, barrier_limit_s=0.05, test_skip_barrier=1)
+        info = ch.solve("link_threshold", tol=1e-10, max_steps=100000, raise_on_noconv=False)
+        status, _, _ = ch.chains()
+        assert info["status"] == "RLGL_ETIMEOUT"
+        # the large chain's group lost a member; chains of one block are
+        # untouched (the 1000-node chain may get a small group too)
+        assert status[1] == 7 and np.all(status[[0, 2, 3]] == 0) and status[4] in (0, 7)
+        ch.set_params(test_skip_barrier=0, barrier_limit_s=2.0)
+        ch.reset()
+        info = ch.solve("link_threshold", tol=1e-10, max_steps=100000)
+        status, _, _ = ch.chains()
+        assert info["status"] == "RLGL_OK" and np.all(status == 0)

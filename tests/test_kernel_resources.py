@@ -1,8 +1,8 @@
-"""Resource budget of the persistent sweep, from the compiler's own report
+"""Resource budget of the persistent sweeps, from the compiler's own report
 (nvcc -Xptxas -v, no GPU): four 256-thread blocks must fit on an SM, so
-k_sweep may use at most 64 registers a thread and 48 KB of static shared
-memory a block, and the FP32 (MIXED) instantiations, those of the timed
-path, must not spill."""
+k_sweep and k_power (the all-green sweep) may use at most 64 registers a
+thread and 48 KB of static shared memory a block, and the FP32 (MIXED)
+instantiations, those of the timed path, must not spill."""
 import os
 import re
 import shutil
@@ -65,3 +65,14 @@ def test_mixed_sweep_does_not_spill(ptxas_report):
     assert len(ent) == 2
     for name, regs, spill, smem in ent:
         assert spill == 0, (name, spill)
+
+
+def test_power_sweep_fits_four_blocks_per_sm(ptxas_report):
+    ent = _entries(ptxas_report, "_ZN4rlgl7k_power")
+    assert len(ent) == 4
+    for name, regs, spill, smem in ent:
+        assert regs is not None and regs <= 64, (name, regs)
+        assert smem is not None and smem <= 48 * 1024, (name, smem)
+    for name, regs, spill, smem in ent:
+        if name.startswith("_ZN4rlgl7k_powerIf"):
+            assert spill == 0, (name, spill)

@@ -209,3 +209,53 @@ def test_sweep_large_chain_mixed_pipelined_select(theta_lag):
         assert np.abs(pi - pib).sum() <= 2e-6
         for ra, rb in zip(log[:10], logb[:10]):
             assert abs(ra["green"] - rb["green"]) <= max(2, rb["green"] // 10000)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_power_sweep_makes_the_oracle_moves(prec):
+    """The all-green sweep (one pass over the in-links a move; rows whose
+    in-links cross merge-path tiles are finished after a barrier) makes the
+    oracle's all-green moves: after 40 moves from step 0 the state is the
+    oracle's up to rounding, on a chain whose auxiliary node's in-links span
+    many tiles, and the move log shows the fused moves (no statistics or
+    select pass)."""
+    import oracle
+    csr = synth.pagerank_chain(synth.rmat_chain(14, 16, seed=7))  # node 0: 16385 in-links
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    c1 = np.abs(C).max()  # the cash the moves start from: the scale of their rounding
+    oracle.solve(csr, p, C, H, sched=oracle.ALL_GREEN, tol=0.0, max_steps=40, check_every=-1)
+    with Chain(csr, precision=prec) as ch:
+        info = ch.solve("all_green", tol=0.0, max_steps=40, raise_on_noconv=False)
+        c, h = ch.get_state()
+        log = ch.move_log(40)
+        assert ch.get_params().persistent == 1
+    assert info["moves"] == 40 and info["pull_moves"] == 40
+    assert info["edges_pushed"] == 40 * csr.nnz
+    assert all(r["phase_us"][0] == 0.0 and r["phase_us"][1] == 0.0 and r["phase_us"][4] > 0 for r in log)
+    assert [r["move"] for r in log] == list(range(40))
+    if prec == "fp64":
+        # FP64 rounding of 40 moves' in-link sums, in another order than the
+        # oracle's: a budget per node from its in-degree (16385 at node 0)
+        indeg = np.bincount(csr.col, minlength=csr.n)
+        budget = 40 * (indeg + 4) * 2.0 ** -53
+        assert np.all(np.abs(h - H) <= budget * np.abs(H).max())
+        # the cash after 40 moves is what is left of sums that cancel: its
+        # error scales with the cash the moves started from
+        assert np.all(np.abs(c - C) <= budget * c1)
+    else:
+        # FP32 cash: the history drifts by FP32 rounding of the moved cash
+        assert np.abs(h / h.sum() - H / H.sum()).sum() <= 1e-5
+
+
+def test_power_sweep_barrier_wait_is_bounded(weighted):
+    """The all-green sweep's grid barriers are bounded too (test hook: one
+    block leaves before its first barrier)."""
+    with Chain(weighted, precision="mixed") as ch:
+        ch.set_params(barrier_limit_s=0.05, test_skip_barrier=1)
+        info = ch.solve("all_green", tol=1e-9, raise_on_noconv=False)
+        assert info["status"] == "RLGL_ETIMEOUT"
+        ch.set_params(test_skip_barrier=0, barrier_limit_s=2.0)
+        ch.reset()
+        info = ch.solve("all_green", tol=1e-9)
+        assert info["status"] == "RLGL_OK"
