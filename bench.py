@@ -501,6 +501,44 @@ def traffic_from_profiles(kernel_cls, workload):
     return ent.get("dram_bytes_per_launch")
 
 
+def ingest_ncu(csv_path, key, command):
+    """Writes profiles/traffic.json[key]: the DRAM bytes (read + write) per
+    launch averaged over the launches of an ncu CSV (--metrics
+    dram__bytes_read.sum,dram__bytes_write.sum --csv), with the hash of the
+    kernel code they were measured on."""
+    import csv
+    per = {}
+    with open(csv_path, newline="") as fh:
+        lines = [l for l in fh if l.startswith('"')]
+    for row in csv.DictReader(lines):
+        name = row.get("Metric Name", "")
+        if name not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        unit = row.get("Metric Unit", "byte").lower()
+        scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}.get(unit, 1)
+        v = float(row["Metric Value"].replace(",", "")) * scale
+        per.setdefault(row["ID"], {}).update({name: v, "kernel": row.get("Kernel Name", "")})
+    # launches renamed by their NVTX range (ncu --print-nvtx-rename kernel)
+    # count for the range of this key only
+    # (a renamed launch reads "<range>/<kernel>")
+    rng = lambda d: d.get("kernel", "").split("/", 1)[0]
+    named = [d for d in per.values() if rng(d).startswith("roofline:")]
+    want = "roofline:" + key.rsplit(":sweep", 1)[0]
+    pick = [d for d in named if rng(d) == want] if named else list(per.values())
+    launches = [d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"] for d in pick
+                if "dram__bytes_read.sum" in d and "dram__bytes_write.sum" in d]
+    if not launches:
+        raise SystemExit(f"no DRAM byte counts in {csv_path}")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    data = json.load(open(path)) if os.path.exists(path) else {}
+    data[key] = {"dram_bytes_per_launch": float(np.mean(launches)), "launches_captured": len(launches),
+                 "per_launch": [float(x) for x in launches], "source_sha": source_hash(), "command": command}
+    with open(path, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print(json.dumps({key: data[key]}))
+
+
 def code_only(text):
     """CUDA/C++ source without comments, trailing blanks and empty lines: a
     change of comments alone leaves the kernels as they were."""
@@ -511,7 +549,7 @@ def code_only(text):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh", "rlgl_power.cuh"):
+    for f in ("rlgl.cu", "rlgl_kernels.cuh", "rlgl_sweep.cuh", "rlgl_power.cuh", "rlgl_batch.cuh"):
         with open(os.path.join(ROOT, "paper_2008_02710_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -568,7 +606,12 @@ def roofline_of_sweep(g, sched, theta, tstar, workload, peak, peak_src):
     per launch / average launch time. The DRAM figures come from the
     committed ncu capture of the same kernel code (null when the code has
     changed since)."""
+    import torch
+    # (an NVTX range per measurement: "roofline:<workload>" holds exactly the
+    # launches this record times, for an ncu capture of the same launches)
+    torch.cuda.nvtx.range_push(f"roofline:{workload}")
     (ms_sw, n_sw), bytes_sw, phases, push_rate = g.sweep_profile(sched, theta, tstar)
+    torch.cuda.nvtx.range_pop()
     n_sw = max(n_sw, 1)
     avg_s = ms_sw / 1e3 / n_sw
     alg = bytes_sw / n_sw
@@ -621,7 +664,8 @@ def beyond_l2_record(args, device, peak, peak_src):
                 continue
             ts, inf = g.timed_solves(sched, 0.0, tstar, 3, 1)
             ms = float(np.median(ts))
-            rf, phases, push_rate = roofline_of_sweep(g, sched, 0.0, tstar, name, peak, peak_src)
+            key = name if label == "link_threshold" else f"{name}:{label}"
+            rf, phases, push_rate = roofline_of_sweep(g, sched, 0.0, tstar, key, peak, peak_src)
             out[label] = {"tstar": tstar, "ms": ms, "err": e, "theta_scale": scale, "theta_lag": lag,
                           "edge_pushes": inf[0]["edges_pushed"],
                           "edge_pushes_per_s": inf[0]["edges_pushed"] / (ms / 1e3),
@@ -929,13 +973,14 @@ def run_batch(args):
                 from paper_2008_02710_gb300 import autotune
                 res = autotune.autotune(ch, sched, tol=tol, max_steps=20000,
                                         grid={"theta_scale": (0.25, 0.5, 1.0), "r": (1, 2),
-                                              "pull_crossover": (0.25, 0.9)})
+                                              "pull_crossover": (0.25, 0.9),
+                                              "batch_block": (128, 256, 512)})
                 tuned = res["best"]
                 ch.reset()
                 info = ch.solve(sched, 0.0, tol, 20000, raise_on_noconv=False)
                 emax = float(chain_errors(ch).max())
                 if emax > ERR_TARGET:  # the tuned setting must still meet the error
-                    ch.set_params(theta_scale=scale, r=1, pull_crossover=0.9)
+                    ch.set_params(theta_scale=scale, r=1, pull_crossover=0.9, batch_block=256)
                     tuned = None
             times = []
             for i in range(args.warmup + args.steps):
@@ -952,11 +997,22 @@ def run_batch(args):
                 if i >= args.warmup:
                     times.append(e0.elapsed_time(e1))
             ms = float(np.median(times))
+            _, mv, _ = ch.chains()
+            # algorithmic bytes of the solve (per node and move: the
+            # statistics and selection reads of the cash; per green node 48 B;
+            # per link used: index + one add or gather), MIXED
+            alg = float(np.sum(mv * np.diff(node_ptr))) * 8 + inf["green_total"] * 48 + inf["edges_pushed"] * 8
+            peak, peak_src = measured_peaks()
             out[sched] = {"tol": tol, "max_err": emax, "ms": ms, "chains_per_s": args.chains / (ms / 1e3),
-                          "autotuned": tuned,
+                          "autotuned": tuned, "batch_block": int(ch.get_params().batch_block),
+                          "persistent": int(ch.get_params().persistent),
                           "edge_pushes": inf["edges_pushed"],
                           "edge_pushes_per_s": inf["edges_pushed"] / (ms / 1e3),
-                          "moves": inf["moves"], "status": inf["status"]}
+                          "moves_max": inf["moves"], "chain_moves": int(mv.sum()), "status": inf["status"],
+                          "roofline": {"bound": "hbm", "kernel": "batch solve (one persistent launch)",
+                                       "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                       "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src,
+                                       "alg_bytes": alg}}
     if "ms" in out.get("link_threshold", {}):
         out["value"] = out["link_threshold"]["chains_per_s"]
         if "ms" in out.get("all_green", {}):
@@ -1155,7 +1211,12 @@ def main(argv=None):
     ap.add_argument("--fixed-moves", type=int, default=0,
                     help="> 0: time this many moves on both precision paths against the oracle's "
                          "same moves instead of the time-to-error run")
+    ap.add_argument("--ingest-ncu", nargs=3, metavar=("CSV", "KEY", "COMMAND"),
+                    help="write profiles/traffic.json[KEY] from an ncu CSV of DRAM byte counts (no GPU)")
     args = ap.parse_args(argv)
+    if args.ingest_ncu:
+        ingest_ncu(*args.ingest_ncu)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -118,7 +118,8 @@ struct rlgl_ctx {
     // solve graph and grid of the all-green (power) sweep
     cudaGraphExec_t power_graph = nullptr;
     int grid_power = 0;
-    int n_hot = 0;  // leading nodes whose in-links the push sums per block
+    int* hubs = nullptr;  // hub table of the push (kHubSlots ids, -1 empty), null when none
+    int n_hubs = 0;
     // profiling
     int profiling = 0;
     std::vector<ProfEv> prof;
@@ -376,12 +377,12 @@ static rlgl_status enqueue_push(Launch L) {
         LAUNCH(L, KC_PUSH,
                (k_push<T, true><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
                    (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
-                   ctx->chunk_row, ctx->st, ctx->n_hot)));
+                   ctx->chunk_row, ctx->st, ctx->n_hubs ? ctx->hubs : nullptr)));
     else
         LAUNCH(L, KC_PUSH,
                (k_push<T, false><<<ctx->grid_push, kThreads, 0, ctx->stream>>>(
                    (T*)ctx->c, ctx->col, ctx->w, ctx->f_eoff, ctx->f_base, (const T*)ctx->f_m,
-                   ctx->chunk_row, ctx->st, ctx->n_hot)));
+                   ctx->chunk_row, ctx->st, ctx->n_hubs ? ctx->hubs : nullptr)));
     return RLGL_OK;
 }
 
@@ -434,6 +435,7 @@ static SweepArgs<T> sweep_args(rlgl_ctx* ctx, const Conds& cd) {
     a.mt = (T*)ctx->mt;
     a.mt2 = (T*)ctx->hsrc;  // free while no re-derivation runs
     a.facc = (T*)ctx->f_m;  // the power sweep clears it at every launch
+    a.pcnt = reinterpret_cast<unsigned int*>(ctx->f_eoff);  // likewise (n counters fit in f_eoff)
     a.f_eoff = ctx->f_eoff;
     a.f_base = ctx->f_base;
     a.f_m = (T*)ctx->f_m;
@@ -454,7 +456,7 @@ static SweepArgs<T> sweep_args(rlgl_ctx* ctx, const Conds& cd) {
     a.use_cond = cd.use;
     a.n = (int)ctx->n;
     a.vec_ok = vec_aligned(ctx);
-    a.n_hot = ctx->n_hot;
+    a.hubs = ctx->n_hubs ? ctx->hubs : nullptr;
     return a;
 }
 
@@ -962,18 +964,84 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
         k_colsum_tiles<false><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
             ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
     CKL(ctx);
-    // Hot targets: the leading nodes (at most kMaxHot) whose in-degree is at
-    // least 8192 and 32 times the mean; the push sums their in-links per block.
+    // Hub targets of the push: the nodes whose in-degree is at least
+    // max(4096, n / 8, 32 x the mean), like the auxiliary node of a PageRank
+    // chain, which every node feeds; up to one per slot of the direct-mapped
+    // table (largest first). Summing a hub's additions per block costs the
+    // push a check per link and a warp reduction per hub link: measured on
+    // R-MAT 20 (per-link threshold, 79 moves), tables of the 64 nodes of
+    // in-degree >= 1024, or of those >= 8192, made the solve 1.7x and 1.4x
+    // slower than no table, so only nodes that a large share of all nodes
+    // feed qualify. A histogram of log2(in-degree) gives the degree above
+    // which at most a few thousand candidates lie; those are sorted here.
     {
-        long long tp[kMaxHot + 1];
-        const long long m = n < kMaxHot ? n : kMaxHot;
-        CK(ctx, cudaMemcpyAsync(tp, ctx->t_ptr, (size_t)(m + 1) * sizeof(long long), cudaMemcpyDeviceToHost,
-                                ctx->stream));
-        CK(ctx, cudaStreamSynchronize(ctx->stream));
         const double mean = (double)nnz / (double)n;
-        int k = 0;
-        while (k < m && (double)(tp[k + 1] - tp[k]) >= (8192.0 > 32.0 * mean ? 8192.0 : 32.0 * mean)) ++k;
-        ctx->n_hot = k;
+        double fl = 32.0 * mean;
+        if (fl < 4096.0) fl = 4096.0;
+        if (fl < (double)n / 8.0) fl = (double)n / 8.0;
+        const long long floor_deg = (long long)fl;
+        unsigned int* hist = nullptr;
+        TRY(dalloc(ctx, &hist, 64 + 1));
+        CK(ctx, cudaMemsetAsync(hist, 0, 65 * sizeof(unsigned int), ctx->stream));
+        k_indeg_log2_hist<<<grid_for(n, kThreads, ctx->sms * 4), kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, hist);
+        CKL(ctx);
+        unsigned int hh[64];
+        CK(ctx, cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        // the lowest power of two with at most 4096 nodes at or above it,
+        // stopping once kHubSlots are there
+        long long above = 0;
+        int bin = 63, tbin = 63;
+        for (; bin >= 0; --bin) {
+            if (above + hh[bin] > 4096) break;
+            above += hh[bin];
+            tbin = bin;
+            if (above >= kHubSlots) break;
+        }
+        long long thr = 1ll << (tbin < 62 ? tbin : 62);
+        if (thr < floor_deg) thr = floor_deg;
+        constexpr int kCap = 8192;
+        int* cid = nullptr;
+        long long* cdeg = nullptr;
+        rlgl_status hs = dalloc(ctx, &cid, kCap);
+        if (hs == RLGL_OK) hs = dalloc(ctx, &cdeg, kCap);
+        if (hs != RLGL_OK) { dfree(ctx, hist); return hs; }
+        CK(ctx, cudaMemsetAsync(hist + 64, 0, sizeof(unsigned int), ctx->stream));
+        k_hub_candidates<<<grid_for(n, kThreads, ctx->sms * 4), kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, thr, kCap,
+                                                                                           cid, cdeg, hist + 64);
+        CKL(ctx);
+        unsigned int nc = 0;
+        CK(ctx, cudaMemcpyAsync(&nc, hist + 64, sizeof nc, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if (nc > (unsigned int)kCap) nc = kCap;
+        std::vector<int> ids(nc);
+        std::vector<long long> dg(nc);
+        if (nc) {
+            CK(ctx, cudaMemcpyAsync(ids.data(), cid, nc * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaMemcpyAsync(dg.data(), cdeg, nc * sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+        dfree(ctx, cid);
+        dfree(ctx, cdeg);
+        dfree(ctx, hist);
+        std::vector<int> order(nc);
+        for (unsigned int k = 0; k < nc; ++k) order[k] = (int)k;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return dg[a] != dg[b] ? dg[a] > dg[b] : ids[a] < ids[b]; });
+        int tab[kHubSlots];
+        for (int t = 0; t < kHubSlots; ++t) tab[t] = -1;
+        int got = 0;
+        for (int k : order) {
+            const int sl = hub_slot(ids[k]);
+            if (tab[sl] < 0) {
+                tab[sl] = ids[k];
+                ++got;
+            }
+        }
+        ctx->n_hubs = got;
+        if (got) {
+            TRY(dalloc(ctx, &ctx->hubs, kHubSlots));
+            CK(ctx, cudaMemcpyAsync(ctx->hubs, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
+        }
     }
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     dfree(ctx, cursor);
@@ -1932,7 +2000,7 @@ void rlgl_destroy(rlgl_ctx* ctx) {
                    ctx->colsum,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
                    ctx->err, ctx->log, ctx->st, ctx->sw, ctx->node_ptr, ctx->chain_of, ctx->cs,
-                   ctx->bsums, ctx->ct_off, ctx->ct_r, ctx->ct_e, ctx->grp, ctx->bq, ctx->q_next};
+                   ctx->bsums, ctx->ct_off, ctx->ct_r, ctx->ct_e, ctx->grp, ctx->bq, ctx->q_next, ctx->hubs};
     for (void* p : dev)
         dfree(ctx, p);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);

@@ -434,7 +434,7 @@ __device__ void batch_chain(const BatchArgs<T>& A, const Control& ctl, BatchSmem
         // -------------------------------------------------------- move
         if (bc.mode == MODE_PUSH)
             push_chunks<T, kHasW, true, kBT>(A.c, A.col, A.w, A.f_eoff + a, A.f_base + a, A.f_m + a,
-                                             A.chunk_row + cbase, bc.edges, bc.green, m, g, sm.push, 0,
+                                             A.chunk_row + cbase, bc.edges, bc.green, m, g, sm.push, nullptr,
                                              g > 1 ? &sl->chunk_next : nullptr);
         else if (bc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true, kBT>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.ct_r + ct0, A.ct_e + ct0, ntk,

@@ -1080,7 +1080,14 @@ __global__ void __launch_bounds__(kThreads) k_select(
 // block-wide running maximum, so every edge costs one shared-memory read;
 // edges are then handled in a coalesced order (slot = thread + q * threads).
 
-constexpr int kMaxHot = 32;  // hot-target slots of the push
+// Hub targets of the push: up to kHubSlots nodes of the largest in-degree,
+// each in the slot hub_slot(id) of a direct-mapped table (-1: empty). The
+// push sums the additions a block makes to each hub in shared memory and
+// adds them to the cash once per block and move: one address takes its
+// additions one after another, so a hub's thousands of in-links a move
+// would otherwise queue on one L2 line.
+constexpr int kHubSlots = 64;
+__host__ __device__ __forceinline__ int hub_slot(int j) { return (int)(((unsigned int)j * 0x9E3779B1u) >> 26); }
 
 // Shared memory of the push chunk loop.
 template <typename T, int kBT = kThreads>
@@ -1089,7 +1096,8 @@ struct PushSmem {
     long long base[kPushChunk + 1];
     T m[kPushChunk + 1];
     int wmax[kBT / 32];
-    double hot[kMaxHot];
+    int hub[kHubSlots];
+    double hot[kHubSlots];
 };
 
 // The chunks of a push over E frontier edges of K frontier rows (see
@@ -1097,11 +1105,11 @@ struct PushSmem {
 // handed out one at a time by that counter (thread 0 asks for the next one
 // while the block works on the current one), so that blocks that meet slow
 // atomics take fewer chunks.
-// Targets j < n_hot (nodes with a very large in-degree placed first, like
-// the auxiliary node of a PageRank chain, which every node feeds) are summed
-// per block in FP64 in shared memory and added to the cash once per block:
-// one global addition per block instead of one per in-link, all of which
-// would queue on one L2 address.
+// Targets in the hub table `hubs` (kHubSlots ids, -1 empty; nullptr: none),
+// like the auxiliary node of a PageRank chain, which every node feeds, are
+// summed per block in FP64 in shared memory and added to the cash once per
+// block: one global addition per block instead of one per in-link, all of
+// which would queue on one L2 address.
 template <typename T, bool kHasW, bool kCg, int kBT = kThreads>
 __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __restrict__ col,
                                             const float* __restrict__ w,
@@ -1110,15 +1118,18 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                                             const T* __restrict__ f_m,
                                             const int* __restrict__ chunk_row, long long E,
                                             long long K, long long first, long long step,
-                                            PushSmem<T, kBT>& sm, int n_hot,
+                                            PushSmem<T, kBT>& sm, const int* __restrict__ hubs,
                                             unsigned long long* next = nullptr) {
     constexpr int kPer = kPushChunk / kBT;  // edge slots per thread
     const long long nchunks = (E + kPushChunk - 1) / kPushChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ long long s_next;
     long long b = first;
-    if (n_hot > 0) {
-        if (threadIdx.x < n_hot) sm.hot[threadIdx.x] = 0.0;
+    if (hubs) {
+        for (int t = threadIdx.x; t < kHubSlots; t += kBT) {
+            sm.hub[t] = __ldg(hubs + t);
+            sm.hot[t] = 0.0;
+        }
         __syncthreads();
     }
     if (next) {
@@ -1180,17 +1191,20 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
                 const int j = __ldg(col + pos);
                 T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
-                if (j >= n_hot) red_add(c + j, val);
-                slot_j[q] = j;
+                const int hs = hub_slot(j);
+                if (hubs && sm.hub[hs] == j) {
+                    slot_j[q] = hs;  // summed below
+                } else {
+                    red_add(c + j, val);
+                }
                 slot_v[q] = val;
             }
         }
-        if (n_hot > 0) {
-            // hot targets: one shared-memory addition per warp and target
+        if (hubs) {
+            // hub targets: one shared-memory addition per warp and hub
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
-                const int le = threadIdx.x + q * kBT;
-                const bool hot = le < ne && slot_j[q] < n_hot;
+                const bool hot = slot_j[q] >= 0;
                 unsigned int m = __ballot_sync(0xffffffffu, hot);
                 while (m) {
                     const int t = __shfl_sync(0xffffffffu, slot_j[q], __ffs(m) - 1);
@@ -1209,9 +1223,10 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             b += step;
         }
     }
-    if (n_hot > 0) {
+    if (hubs) {
         __syncthreads();
-        if (threadIdx.x < n_hot && sm.hot[threadIdx.x] != 0.0) red_add(c + threadIdx.x, (T)sm.hot[threadIdx.x]);
+        for (int t = threadIdx.x; t < kHubSlots; t += kBT)
+            if (sm.hot[t] != 0.0) red_add(c + sm.hub[t], (T)sm.hot[t]);
     }
 }
 
@@ -1219,11 +1234,11 @@ template <typename T, bool kHasW>
 __global__ void __launch_bounds__(kThreads) k_push(
     T* __restrict__ c, const int* __restrict__ col, const float* __restrict__ w,
     const long long* __restrict__ f_eoff, const long long* __restrict__ f_base,
-    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st, int n_hot) {
+    const T* __restrict__ f_m, const int* __restrict__ chunk_row, const DevState* st, const int* hubs) {
     if (st->done || st->skip_move || st->mode != MODE_PUSH) return;
     __shared__ PushSmem<T> sm;
     push_chunks<T, kHasW, false>(c, col, w, f_eoff, f_base, f_m, chunk_row, st->edges, st->green,
-                                 blockIdx.x, gridDim.x, sm, n_hot);
+                                 blockIdx.x, gridDim.x, sm, hubs);
 }
 
 // ------------------------------------------------------ merge-path pull
@@ -1846,6 +1861,38 @@ __global__ void __launch_bounds__(kThreads) k_colsum_tiles(double* __restrict__ 
     __shared__ PullSmem<double> sm;
     pull_tiles<double, double, kHasW, false>(colsum, s, t_ptr, t_src, t_w, tile_r, tile_e, ntiles,
                                              blockIdx.x, gridDim.x, sm);
+}
+
+// Hub candidates: nodes whose in-degree is at least thr, appended to
+// ids/deg (at most cap; *cnt counts every candidate).
+__global__ void k_hub_candidates(const long long* __restrict__ t_ptr, long long n, long long thr, int cap,
+                                 int* __restrict__ ids, long long* __restrict__ deg, unsigned int* cnt) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long d = t_ptr[j + 1] - t_ptr[j];
+        if (d >= thr) {
+            const unsigned int k = atomicAdd(cnt, 1u);
+            if ((int)k < cap) {
+                ids[k] = (int)j;
+                deg[k] = d;
+            }
+        }
+    }
+}
+
+// Histogram of floor(log2(in-degree)) over the nodes (64 bins).
+__global__ void k_indeg_log2_hist(const long long* __restrict__ t_ptr, long long n, unsigned int* hist) {
+    __shared__ unsigned int h[64];
+    for (int b = threadIdx.x; b < 64; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long d = t_ptr[j + 1] - t_ptr[j];
+        if (d > 0) atomicAdd(&h[63 - __clzll(d)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 64; b += blockDim.x)
+        if (h[b]) atomicAdd(hist + b, h[b]);
 }
 
 // Batch: every chain running again (and its tolerance, when tol >= 0).

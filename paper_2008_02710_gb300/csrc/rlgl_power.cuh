@@ -1,32 +1,40 @@
 // The persistent all-green sweep (power iteration, Sec. 2.3.1): the moves
-// of a single-chain all-green solve in one cooperative kernel, two grid
-// barriers a move and one pass over the in-links.
+// of a single-chain all-green solve in one cooperative kernel, one pass over
+// the in-links and one grid barrier a move.
 //
 // With G_t = [N] a move is M_t = C_t, H <- H + C_t, C_{t+1} = M_t P (Eqs.
 // recursion_M, recursion_H, recursion_C; every node's cash leaves it). The
 // general sweep makes it in three phases (statistics, select, pull) with
 // three barriers. Here the select's work is folded into the pull's row
-// epilogue: when the in-link sum of row j is complete, the same thread
-// reads C_t,j, adds it to H_j, stores C_{t+1},j = the sum and the next
-// move's moved cash per weight m~_j = C_{t+1},j s_j, and sums the
-// statistics of C_{t+1} and of M_t. A move is then
-//   pull      : merge-path tiles over the in-links (handed out by a
-//               counter), gathering m~ of the current move; rows that end
-//               in the tile where they began go through the epilogue, the
-//               pieces of rows that cross a tile boundary are added into a
-//               zero-at-rest accumulator;
-//   barrier   ;
-//   fix-up    : the rows that crossed a tile boundary (found from the tile
-//               table: a tile's first row began before the tile and ends in
-//               it) go through the epilogue; block sums of the statistics;
-//   barrier   ; every block takes the same decisions (stop test of Alg. 1,
-//               re-derivation triggers) from the same totals.
+// epilogue: once the in-link sum of row j is complete, one thread reads
+// C_t,j, adds it to H_j, stores C_{t+1},j = the sum and the next move's
+// moved cash per weight m~_j = C_{t+1},j s_j, and sums the statistics of
+// C_{t+1} and of M_t. A move is
+//   pull    : merge-path tiles over the in-links, handed out by a counter,
+//             gathering m~ of the current move. A row that ends in the tile
+//             where it began goes through the epilogue with the tile. A row
+//             whose in-links cross tile boundaries contributes one piece
+//             per tile it spans (added into a zero-at-rest accumulator, then
+//             counted); the piece that arrives last takes the sum and runs
+//             the epilogue. The tiles a row spans follow from its merge
+//             items: its in-links at diagonals t_ptr[j] + j .. t_ptr[j+1] +
+//             j - 1 and its end at t_ptr[j+1] + j.
+//   barrier ; every block takes the same decisions (stop test of Alg. 1,
+//             re-derivation triggers) from the same totals.
+// Measured on R-MAT 20 and symmetrised R-MAT 22 (all-green to a fixed move
+// count): staging the next tile's source indices in shared memory with
+// cp.async, and gathering through L1, each made the pull slower; the
+// gathers read L2 and the tile loads its indices itself.
 // The moved cash alternates between two buffers (mt and the residual
-// source hsrc, free while no re-derivation runs), so that a move gathers
-// m~_t while it writes m~_{t+1}.
+// source hsrc, free while no re-derivation runs). The per-move totals
+// rotate over three slots: the decision of move t reads slot q, move t adds
+// into slot q + 1, and slot q + 2 (read one decision ago) is cleared by
+// block 0 at the decision; no block can reach slot q + 2 again before
+// block 0 has arrived at the next barrier.
 // The moves and their floating-point sums are those of the general sweep's
 // all-green moves: m~ = C s rounded to the cash type, in-link sums in the
-// cash type in merge-path order, H accumulated in FP64.
+// cash type in merge-path order (a split row's pieces added in arrival
+// order), H accumulated in FP64.
 #pragma once
 
 #include "rlgl_sweep.cuh"
@@ -48,12 +56,11 @@ struct PowAcc {
     T a, s, m, ma;
 };
 
-// Row epilogue of an all-green move: row r's in-link sum v is C_{t+1},r.
+// Row epilogue of an all-green move: row r's in-link sum v is C_{t+1},r;
+// old = C_t,r and sc = s_r.
 template <typename T>
-__device__ __forceinline__ void power_row(const SweepArgs<T>& A, T* __restrict__ mt_next, long long r, T v,
-                                          PowAcc<T>& acc) {
-    const T old = __ldcg(A.c + r);  // C_t,r (this kernel stored it one move ago)
-    const T sc = __ldg(row_scale(A.sf, A.s, T(0)) + r);
+__device__ __forceinline__ void power_row_with(const SweepArgs<T>& A, T* __restrict__ mt_next, long long r, T v,
+                                               T old, T sc, PowAcc<T>& acc) {
     A.c[r] = v;
     mt_next[r] = v * sc;
     red_add(A.H + r, (double)old);  // M_t,r joins the history (no load: the L2 adds)
@@ -63,58 +70,153 @@ __device__ __forceinline__ void power_row(const SweepArgs<T>& A, T* __restrict__
     acc.ma += fabs(old);
 }
 
-// One move's pull: the merge-path tiles (as pull_tiles) with the row
-// epilogue; tiles handed out by the counter `next`.
+template <typename T>
+__device__ __forceinline__ void power_row(const SweepArgs<T>& A, T* __restrict__ mt_next, long long r, T v,
+                                          PowAcc<T>& acc) {
+    const T old = __ldcg(A.c + r);  // C_t,r (this kernel stored it one move ago)
+    const T sc = __ldg(row_scale(A.sf, A.s, T(0)) + r);
+    power_row_with<T>(A, mt_next, r, v, old, sc, acc);
+}
+
+__device__ __forceinline__ float atomic_take(float* p) { return atomicExch(p, 0.0f); }
+__device__ __forceinline__ double atomic_take(double* p) {
+    return __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull));
+}
+
+// The pieces of a row whose merge items span several tiles: every piece is
+// added into facc[r] where it is found; at the next tile (after the block's
+// barrier) thread 0 or 1 counts it in pcnt[r] behind a fence, so the fence
+// overlaps that tile's gathers instead of holding up the block. The count
+// that completes the row (its merge items span `pieces` tiles) takes the
+// sum, clearing facc[r] and the count, and runs the row's epilogue.
+struct PowPend {
+    long long r;            // the row (-1: none)
+    unsigned int pieces;    // the tiles its merge items span
+    unsigned int seen;      // the count after this piece
+};
+
+template <typename T>
+__device__ __forceinline__ void power_count(const SweepArgs<T>& A, PowPend& pp) {
+    const long long a = __ldg(A.t_ptr + pp.r) + pp.r, b = __ldg(A.t_ptr + pp.r + 1) + pp.r;
+    __threadfence();  // the block's piece (added before the barrier) before its count
+    pp.pieces = (unsigned int)(b / kMpItems - a / kMpItems + 1);
+    pp.seen = atomicAdd(A.pcnt + pp.r, 1u) + 1u;  // (its value is first used at power_finish)
+}
+
+template <typename T>
+__device__ __forceinline__ void power_finish(const SweepArgs<T>& A, T* __restrict__ mt_next, const PowPend& pp,
+                                             PowAcc<T>& acc) {
+    if (pp.seen == pp.pieces) {
+        __threadfence();  // every counted piece is in facc
+        const T v = atomic_take(A.facc + pp.r);
+        A.pcnt[pp.r] = 0u;
+        power_row<T>(A, mt_next, pp.r, v, acc);
+    }
+}
+
+// Bounds of tile b: first row, first in-link, rows ending in it, in-links.
+struct TileB {
+    long long r0, e0;
+    int nr, ne;
+};
+
+__device__ __forceinline__ TileB tile_bounds(const long long* __restrict__ tile_r,
+                                             const long long* __restrict__ tile_e, long long b) {
+    TileB t;
+    t.r0 = __ldg(tile_r + b);
+    t.e0 = __ldg(tile_e + b);
+    t.nr = (int)(__ldg(tile_r + b + 1) - t.r0);
+    t.ne = (int)(__ldg(tile_e + b + 1) - t.e0);
+    return t;
+}
+
+// One move's pull with the row epilogue; tiles handed out by `next`.
 template <typename T, bool kHasW>
 __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __restrict__ mt_cur,
-                                            T* __restrict__ mt_next, T* __restrict__ facc, PowSmem<T>& sm,
+                                            T* __restrict__ mt_next, PowSmem<T>& sm,
                                             unsigned long long* next, PowAcc<T>& acc) {
     PullSmem<T>& ps = sm.pull;
-    __shared__ long long s_tnext;
-    if (threadIdx.x == 0) s_tnext = (long long)atomicAdd(next, 1ull);
-    __syncthreads();
-    long long b = s_tnext;
-    __syncthreads();
+    __shared__ long long s_b[2];
+    __shared__ TileB s_t[2];
+    __shared__ long long s_pend[2];  // the last tile's pieces: its first row's, its carry-out's
+    if (threadIdx.x < 2) s_pend[threadIdx.x] = -1;
     const long long ntiles = A.ntiles;
-    while (b < ntiles) {
-        if (threadIdx.x == 0) s_tnext = (long long)atomicAdd(next, 1ull);  // read at the end
-        const long long r0 = __ldg(A.tile_r + b), e0 = __ldg(A.tile_e + b);
-        const int nrows = (int)(__ldg(A.tile_r + b + 1) - r0);
-        const int nedges = (int)(__ldg(A.tile_e + b + 1) - e0);
+    const T* __restrict__ scale = row_scale(A.sf, A.s, T(0));
+    // the first tile and the one after it
+    if (threadIdx.x == 0) {
+        const long long b0 = (long long)atomicAdd(next, 1ull);
+        s_b[0] = b0;
+        if (b0 < ntiles) s_t[0] = tile_bounds(A.tile_r, A.tile_e, b0);
+        s_b[1] = (long long)atomicAdd(next, 1ull);
+    }
+    __syncthreads();
+    int cs = 0;  // the current tile's entry in s_b / s_t
+    for (;;) {
+        const long long b = s_b[cs];
+        if (b >= ntiles) break;
+        const TileB t = s_t[cs];
+        // thread 0: the next tile's bounds and the grab after it, in flight
+        // while the block gathers this tile
+        const long long bn = s_b[cs ^ 1];
+        long long bnn = 0;
+        TileB tn{0, 0, 0, 0};
+        if (threadIdx.x == 0) {
+            if (bn < ntiles) {
+                tn = tile_bounds(A.tile_r, A.tile_e, bn);
+                bnn = (long long)atomicAdd(next, 1ull);
+            } else {
+                bnn = ntiles;
+            }
+        }
+        __syncthreads();  // the last tile's pieces are known
+        PowPend pp{-1, 0u, 0u};
+        if (threadIdx.x < 2) pp.r = s_pend[threadIdx.x];
+        T oldv = T(0), scv = T(0);
         {
             int sidx[kMpIpt];
-            float wv[kMpIpt];
             long long re[kMpIpt];
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) {
                 const int k = threadIdx.x + q * kThreads;
-                sidx[q] = (k < nedges) ? __ldg(A.t_src + e0 + k) : -1;
-                if (kHasW) wv[q] = (k < nedges) ? __ldg(A.t_w + e0 + k) : 0.0f;
-                re[q] = (k < nrows) ? __ldg(A.t_ptr + r0 + 1 + k) : 0;
+                sidx[q] = (k < t.ne) ? __ldg(A.t_src + t.e0 + k) : -1;
+                // the weights are read at the store below; their lines are
+                // fetched now (no register holds them across the gathers)
+                if (kHasW && k < t.ne) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.t_w + t.e0 + k));
+                re[q] = (k < t.nr) ? __ldg(A.t_ptr + t.r0 + 1 + k) : 0;
             }
+            // the epilogue's first row of this thread, read with the gathers
+            if ((int)threadIdx.x < t.nr) {
+                oldv = __ldcg(A.c + t.r0 + threadIdx.x);
+                scv = __ldg(scale + t.r0 + threadIdx.x);
+            }
+            // m~ of this move was written by other blocks one move ago: L2
             T v[kMpIpt];
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? __ldcg(mt_cur + sidx[q]) : T(0);
+            if (pp.r >= 0) power_count<T>(A, pp);
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) {
                 const int k = threadIdx.x + q * kThreads;
-                if (k < nedges) ps.val[k] = kHasW ? v[q] * (T)wv[q] : v[q];
-                if (k < nrows) ps.end[k] = (int)(re[q] - e0);
+                if (k < t.ne) ps.val[k] = kHasW ? v[q] * (T)__ldg(A.t_w + t.e0 + k) : v[q];
+                if (k < t.nr) ps.end[k] = (int)(re[q] - t.e0);
             }
         }
         if (threadIdx.x == 0) {
-            ps.end[nrows] = 0x7fffffff;
-            ps.start0 = (int)(__ldg(A.t_ptr + r0) - e0);
+            ps.end[t.nr] = 0x7fffffff;
+            ps.start0 = (int)(__ldg(A.t_ptr + t.r0) - t.e0);
+            s_t[cs ^ 1] = tn;
+            s_b[cs] = bnn;  // the entry after next
         }
-        __syncthreads();
-        const int total = nrows + nedges;
+        __syncthreads();  // the next tile's bounds are known
+        if (threadIdx.x < 2) s_pend[threadIdx.x] = -1;
+        const int total = t.nr + t.ne;
         int d = threadIdx.x * kMpIpt;
         const bool active = d < total;
         long long rowA = -1, rowB = -1;
         T accA = T(0), accB = T(0);
         if (active) {
             const int dend = min(d + kMpIpt, total);
-            int lo = max(0, d - nedges), hi = min(d, nrows);
+            int lo = max(0, d - t.ne), hi = min(d, t.nr);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
                 if (ps.end[mid] >= d - mid) hi = mid; else lo = mid + 1;
@@ -131,7 +233,7 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
                     ++cnt;
                 } else {
                     if (!whole) {
-                        rowA = r0 + i;
+                        rowA = t.r0 + i;
                         accA = s;
                     } else {
                         sm.rsum[i] = s;  // a row with no in-link sums to zero
@@ -143,43 +245,46 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
                 }
             }
             if (cnt > 0 || !whole) {
-                rowB = r0 + i;
+                rowB = t.r0 + i;
                 accB = s;
             }
         }
         const T run = block_segscan<T>(rowB, accB, ps.ckey, ps.cval);
+        const bool first_split = ps.start0 < 0;  // the tile's first row began in an earlier tile
         if (rowA >= 0) {
             T sum = accA;
             if (threadIdx.x > 0 && ps.ckey[threadIdx.x - 1] == rowA) sum += ps.cval[threadIdx.x - 1];
-            // the tile's first row may have begun in an earlier tile
-            if (rowA == r0 && ps.start0 < 0) red_add(facc + rowA, sum);
-            else sm.rsum[rowA - r0] = sum;
+            if (rowA == t.r0 && first_split) {
+                atomicAdd(A.facc + rowA, sum);
+                s_pend[0] = rowA;  // counted at the next tile
+            } else {
+                sm.rsum[rowA - t.r0] = sum;
+            }
         }
         const int last = (total - 1) / kMpIpt;
-        if ((int)threadIdx.x == last && rowB >= 0) red_add(facc + rowB, run);
+        if ((int)threadIdx.x == last && rowB >= 0) {
+            atomicAdd(A.facc + rowB, run);
+            s_pend[1] = rowB;
+        }
         __syncthreads();
         // the rows that end in this tile and began in it
-        for (int k = (ps.start0 < 0 ? 1 : 0) + (int)threadIdx.x; k < nrows; k += blockDim.x)
-            power_row<T>(A, mt_next, r0 + k, sm.rsum[k], acc);
-        b = s_tnext;
-        __syncthreads();  // the tile's shared memory and s_tnext are rewritten next
-    }
-}
-
-// The rows that crossed a tile boundary: tile b's first row r0 began before
-// the tile (t_ptr[r0] < tile_e[b]) and ends in it (tile_r[b+1] > r0). Their
-// pieces are complete in facc once every block has passed the barrier.
-template <typename T>
-__device__ __forceinline__ void power_fixup(const SweepArgs<T>& A, T* __restrict__ mt_next, T* __restrict__ facc,
-                                            PowAcc<T>& acc) {
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < A.ntiles;
-         b += (long long)gridDim.x * blockDim.x) {
-        const long long r0 = __ldg(A.tile_r + b);
-        if (__ldg(A.tile_r + b + 1) > r0 && __ldg(A.t_ptr + r0) < __ldg(A.tile_e + b)) {
-            const T v = __ldcg(facc + r0);
-            facc[r0] = T(0);
-            power_row<T>(A, mt_next, r0, v, acc);
+        {
+            int k = (first_split ? 1 : 0) + (int)threadIdx.x;
+            if (k < t.nr && k == (int)threadIdx.x) {
+                power_row_with<T>(A, mt_next, t.r0 + k, sm.rsum[k], oldv, scv, acc);
+                k += blockDim.x;
+            }
+            for (; k < t.nr; k += blockDim.x) power_row<T>(A, mt_next, t.r0 + k, sm.rsum[k], acc);
         }
+        if (pp.r >= 0) power_finish<T>(A, mt_next, pp, acc);
+        cs ^= 1;
+        __syncthreads();  // the tile's shared memory is rewritten next
+    }
+    // the last tile's pieces (the loop ended on a barrier)
+    if (threadIdx.x < 2 && s_pend[threadIdx.x] >= 0) {
+        PowPend pp{s_pend[threadIdx.x], 0u, 0u};
+        power_count<T>(A, pp);
+        power_finish<T>(A, mt_next, pp, acc);
     }
 }
 
@@ -197,6 +302,8 @@ __device__ __forceinline__ void power_publish(PowAcc<T>& acc, SweepSlot* sl, T* 
     }
     acc.a = acc.s = acc.m = acc.ma = T(0);
 }
+
+__device__ __forceinline__ int rot3(int q) { return q == 2 ? 0 : q + 1; }
 
 template <typename T, bool kHasW>
 __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T> A) {
@@ -235,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         sc.stall_count = st->stall_count;
         const unsigned long long arr = ld_acquire_u64(&sw->bar.arrived);
         sc.target = arr - arr % gridDim.x;
-        sc.p = (int)(sw->bar.parity & 1u);
+        sc.p = (int)(sw->bar.parity % 3u);  // the slot the first decision reads (clear)
         sc.want_refresh = 0;
         sc.have_lag = 0;
     }
@@ -247,16 +354,16 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
     PowAcc<T> acc{T(0), T(0), T(0), T(0)};
 
     // ------------------------------------------------------- prologue
-    // m~ = C s for the first move, the accumulator of split rows cleared,
-    // and the statistics of the cash for the first stop test.
+    // m~ = C s for the first move, the split rows' accumulators and counts
+    // cleared, and the statistics of the cash for the first stop test.
     {
-        if (lead) clear_slot(&sw->slot[sc.p ^ 1]);  // the first move's slot
         const T* scale = row_scale(A.sf, A.s, T(0));
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x) {
             const T v = A.c[i];
             A.mt[i] = v * __ldg(scale + i);
             A.facc[i] = T(0);
+            A.pcnt[i] = 0u;
             acc.a += fabs(v);
             acc.s += v;
         }
@@ -269,8 +376,9 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         // (thread 0 of every block, from the same totals)
         if (threadIdx.x == 0) {
             SweepSlot* sl = &sw->slot[sc.p];
-            const double2 as = ldcg_pair(&sl->a);        // ||C||_1 (and pr, unused)
-            const double2 mm = ldcg_pair(&sl->msum);     // the last move's sum M and sum |M|
+            if (blockIdx.x == 0) clear_slot(&sw->slot[rot3(rot3(sc.p))]);  // read one decision ago
+            const double2 as = ldcg_pair(&sl->a);         // ||C||_1 (and pr, unused)
+            const double2 mm = ldcg_pair(&sl->msum);      // the last move's sum M and sum |M|
             const double2 rts = ldcg_pair(&sl->reserve);  // block 0's timer in .y
             const double sum = __ldcg(&sl->s);
             const double l1 = as.x;
@@ -323,13 +431,13 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
                 st->stall_mark = sc.stall_mark;
                 st->stall_count = sc.stall_count;
                 if (sc.have_lag) {
-                    // the last move's record: H 1 after it and its phase times
+                    // the last move's record: H 1 after it
                     MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
                     rec->hsum = sc.hsum;
                 }
                 if (sc.leave) {
                     st->mode = MODE_NONE;
-                    sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                    sw->bar.parity = (unsigned int)rot3(sc.p);  // clear (cleared one decision ago)
                     if (stop >= 0) {
                         st->done = 1;
                         st->status = stop;
@@ -380,32 +488,24 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         if (sc.leave) return;
 
         // ----------------------------------------------------------- move
-        SweepSlot* nsl = &sw->slot[sc.p ^ 1];  // this move's sums and tile counter
+        SweepSlot* nsl = &sw->slot[rot3(sc.p)];  // this move's sums and tile counter
         if (lead) sc.ts[0] = globaltimer();
-        power_tiles<T, kHasW>(A, mt_cur, mt_nxt, A.facc, sm, &nsl->chunk_next, acc);
-        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr))
-            break;
-        // every block has read this move's decision slot: clear it for the
-        // move after next
-        if (lead) clear_slot(&sw->slot[sc.p]);
-        power_fixup<T>(A, mt_nxt, A.facc, acc);
+        power_tiles<T, kHasW>(A, mt_cur, mt_nxt, sm, &nsl->chunk_next, acc);
         power_publish<T>(acc, nsl, tscratch);
-        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr))
+        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr))
             break;
         if (lead) {
             MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
-            // pull work, wait at its barrier, fix-up work, wait (slots 4, 5, 2, 3)
+            // pull work and the wait at its barrier (slots 4 and 5)
             rec->phase_us[4] = (float)(sc.ts[1] - sc.ts[0]) * 1e-3f;
             rec->phase_us[5] = (float)(sc.ts[2] - sc.ts[1]) * 1e-3f;
-            rec->phase_us[2] = (float)(sc.ts[3] - sc.ts[2]) * 1e-3f;
-            rec->phase_us[3] = (float)(sc.ts[4] - sc.ts[3]) * 1e-3f;
         }
         {
             T* t = mt_cur;
             mt_cur = mt_nxt;
             mt_nxt = t;
         }
-        if (threadIdx.x == 0) sc.p ^= 1;
+        if (threadIdx.x == 0) sc.p = rot3(sc.p);
         __syncthreads();
     }
 aborted:

@@ -79,7 +79,7 @@ __device__ __forceinline__ double2 ldcg_pair(const void* p) {
 
 struct SweepState {
     GridBar bar;
-    SweepSlot slot[2];
+    SweepSlot slot[3];  // the general sweep alternates slots 0 and 1; the all-green sweep rotates all three
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
@@ -170,6 +170,7 @@ struct SweepArgs {
     T* mt;
     T* mt2;      // power sweep: the moved cash of every other move
     T* facc;     // power sweep: sums of rows split across tiles (zero at rest)
+    unsigned int* pcnt;  // power sweep: pieces of each split row arrived (zero at rest)
     long long* f_eoff;
     long long* f_base;
     T* f_m;
@@ -190,7 +191,7 @@ struct SweepArgs {
     int use_cond;
     int n;
     int vec_ok;
-    int n_hot;
+    const int* hubs;  // hub table of the push (nullptr: none)
 };
 
 // Shared cache of the select phase when the chain has at most kIters
@@ -1065,7 +1066,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         if (sc.mode == MODE_PUSH)
             push_chunks<T, kHasW, true>(A.c, A.col, A.w, A.f_eoff, A.f_base, A.f_m, A.chunk_row,
                                         sc.edges, sc.green, blockIdx.x, gridDim.x, sm.push,
-                                        A.n_hot, &sl->chunk_next);
+                                        A.hubs, &sl->chunk_next);
         else if (sc.mode == MODE_PULL)
             pull_tiles<T, T, kHasW, true>(A.c, A.mt, A.t_ptr, A.t_src, A.t_w, A.tile_r, A.tile_e,
                                           A.ntiles, blockIdx.x, gridDim.x, sm.pull, &sl->chunk_next);

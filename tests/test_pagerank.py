@@ -186,3 +186,52 @@ def test_pagerank_hot_node_push_matches_oracle_moves():
             budget = (deg_in + 4) * 2.0 ** -53 * A + 1e-300
             assert np.all(np.abs(c2 - C) <= budget)
     assert hot_moves >= 1  # the auxiliary node was pushed at least once
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_relabelled_hub_push_matches_oracle_moves(persistent):
+    """A hub anywhere in the id range: the PageRank chain's auxiliary node
+    (fed by every node) moved to a random id by a seeded relabelling. Its
+    in-links are summed per block through the push's hub table; FP64 push
+    moves, single steps and persistent sweeps, equal the oracle's moves node
+    by node within the FP64 rounding budget."""
+    from paper_2008_02710_gb300.rlgl import Chain
+    aug = synth.pagerank_chain(synth.rmat_chain(14, 16, seed=3))
+    n = aug.n
+    perm = np.random.default_rng(4).permutation(n)  # old id -> new id
+    rows = np.repeat(np.arange(n), np.diff(aug.row_ptr))
+    src, dst = perm[rows], perm[aug.col]
+    order = np.argsort(src, kind="stable")
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(src, minlength=n), out=row_ptr[1:])
+    g = synth.CSR(n, row_ptr, dst[order].astype(np.int32), aug.w[order])
+    hub = int(perm[0])
+    assert hub > 100
+    deg_in = np.bincount(g.col, minlength=n).astype(float)
+    assert deg_in[hub] == n
+    grow = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    into_hub = g.col == hub
+    p = oracle.transition_probs(g)
+    m0 = np.zeros(n)
+    m0[hub] = 1.0
+    with Chain(g, m0=m0, precision="fp64") as ch:
+        ch.set_params(theta_scale=0.5, pull_crossover=10.0, persistent=persistent)  # always push
+        hub_pushes = 0
+        for _ in range(8):
+            c, h = ch.get_state()
+            if persistent:
+                ch.solve("link_threshold", tol=0.0, max_steps=1, raise_on_noconv=False)
+            else:
+                assert ch.step("link_threshold")["mode"] == 1
+            c2, h2 = ch.get_state()
+            g_ = (h2 != h).astype(np.uint8)
+            hub_pushes += int(g_[grow[into_hub]].sum())  # green rows' links into the hub
+            C, H = c.copy(), h.copy()
+            oracle.move(g, p, g_, C, H)
+            A, HA = np.abs(c), np.zeros(n)
+            oracle.move(g, p, g_, A, HA)
+            budget = (deg_in + 4) * 2.0 ** -53 * A + 1e-300
+            assert np.all(np.abs(c2 - C) <= budget)
+            assert np.array_equal(h2, H)
+    assert hub_pushes > n // 4  # many links into the hub were pushed
