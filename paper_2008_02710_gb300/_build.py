@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "rlgl.cu"), os.path.join(HERE, "csrc", "rlgl_noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "rlgl_kernels.cuh"), os.path.join(HERE, "csrc", "rlgl_sweep.cuh"),
-               os.path.join(HERE, "csrc", "rlgl_power.cuh"),
+               os.path.join(HERE, "csrc", "rlgl_power.cuh"), os.path.join(HERE, "csrc", "rlgl_batch.cuh"),
                os.path.join(ROOT, "include", "rlgl.h")]
 LIB = os.path.join(HERE, "librlgl.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
