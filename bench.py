@@ -481,6 +481,34 @@ class GpuRun:
             if i >= warmup:
                 times.append(t1 - t0)
                 pushes.append(info["edges_pushed"])
+        # one more step, untimed, with a synchronisation after each part: where
+        # the end-to-end time goes (upload alone, create, solve, estimate, destroy)
+        dev = {k: torch.empty(getattr(pinned, k).numel(), dtype=getattr(pinned, k).dtype, device=self.device)
+               for k in ("row_ptr", "col")}
+        parts = {}
+        torch.cuda.synchronize(self.device)
+        t = time.perf_counter()
+        with torch.cuda.stream(self.stream):
+            for k, v in dev.items():
+                v.copy_(getattr(pinned, k), non_blocking=True)
+        self.stream.synchronize()
+        parts["upload_only"] = time.perf_counter() - t
+        del dev
+        t = time.perf_counter()
+        ch = Chain(pinned, m0=m0, precision=self.wl["precision"], stream=self.stream)
+        ch.set_params(theta_scale=theta_scale, r=r, theta_lag=theta_lag)
+        self.stream.synchronize()
+        parts["create"] = time.perf_counter() - t
+        t = time.perf_counter()
+        ch.solve(sched, theta, tol=0.0, max_steps=tstar, raise_on_noconv=False)
+        parts["solve"] = time.perf_counter() - t
+        t = time.perf_counter()
+        ch.estimate(pi_host)
+        parts["estimate"] = time.perf_counter() - t
+        t = time.perf_counter()
+        ch.close()
+        parts["destroy"] = time.perf_counter() - t
+        self.e2e_parts_ms = {k: round(1e3 * v, 3) for k, v in parts.items()}
         return times, pushes, h2d, csr.n * 8
 
 
@@ -886,7 +914,7 @@ def run_gpu(args):
         "phase_kernel_ms": {k: v[0] for k, v in kt.items() if k != "sweep"},
         "phase_kernel_launches": {k: v[1] for k, v in kt.items() if k != "sweep"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1e3 * e2e_t / len(et)},
+                "ms_per_step": 1e3 * e2e_t / len(et), "parts_ms": getattr(g, "e2e_parts_ms", None)},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -1021,39 +1049,64 @@ def run_batch(args):
 
 
 def run_serving(args):
-    """Poisson stream of chain-solve requests through the continuous-batching
-    server, against one-at-a-time all-green solves of the same stream.
-    Requests draw their chain from a pool of R-MAT graphs with log-uniform
-    sizes 1e3..4e6 (each graph is generated once)."""
+    """Poisson stream of chain-solve requests (the serving recipe): every
+    request has its own R-MAT graph (log-uniform 1e3..4e6 nodes, edge factor
+    16, cycle and self-loops), drawn on the device before the stream starts
+    and resident there, and a tolerance from {1e-4, 1e-6, 1e-8}. The stream
+    is served three ways under the same HBM budget: one solve at a time with
+    the whole GPU (a large request alone through the persistent sweep, the
+    small ones queued meanwhile in one persistent batch launch), one context
+    and stream per request (up to --slots side by side, phase kernels), and
+    one request at a time with all-green solves (the baseline). Each is run
+    twice: in real time (arrivals at their Poisson times: p50/p99 latency)
+    and saturated (every request queued at the start: solves/s at capacity)."""
+    import torch
     from paper_2008_02710_gb300 import synth
-    from paper_2008_02710_gb300.serve import Request, Server, summary
+    from paper_2008_02710_gb300.serve import BatchServer, Request, Server, summary
+    torch.cuda.set_device(0)
     rng = np.random.default_rng(5)
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(4e6), args.pool)).astype(np.int64)
-    t = time.time()
-    pool = [synth.rmat_chain_n(int(n), seed=1000 + k) for k, n in enumerate(sizes)]
-    gen_s = time.time() - t
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(4e6), args.requests)).astype(np.int64)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, args.requests))
-    picks = rng.integers(0, args.pool, args.requests)
     tols = rng.choice([1e-4, 1e-6, 1e-8], args.requests)
+    t = time.time()
+    graphs = [synth.rmat_chain_n_device(int(n), seed=1000 + k, device="cuda") for k, n in enumerate(sizes)]
+    torch.cuda.synchronize()
+    gen_s = time.time() - t
+    resident = sum(g.row_ptr.numel() * 8 + g.col.numel() * 4 for g in graphs)
 
-    def stream_of(schedule):
-        return [Request(i, float(arrivals[i]), pool[picks[i]], float(tols[i]), schedule=schedule)
+    def stream_of(schedule, realtime):
+        # saturated: every request is there at the start (latency from 0)
+        return [Request(i, float(arrivals[i]) if realtime else 0.0, graphs[i], float(tols[i]), schedule=schedule)
                 for i in range(args.requests)]
 
-    out = {"metric": "serving: p50/p99 latency and solves/s (Poisson stream)", "unit": "solves/s",
-           "workload": f"{args.requests} requests at {args.rate}/s, pool of {args.pool} R-MAT graphs "
-                       f"(n {int(sizes.min())}..{int(sizes.max())}), tol in {{1e-4,1e-6,1e-8}}, "
-                       f"HBM budget {args.budget_gb} GB", "gen_s": gen_s}
-    srv = Server(args.budget_gb * 1e9, max_active=args.slots, precision="mixed",
-                 theta_scale=args.theta_scale, keep_pi=False)
-    res = srv.run(stream_of("link_threshold"), realtime=True)
-    out["ours"] = dict(summary(res), **srv.stats)
-    base = Server(args.budget_gb * 1e9, max_active=1, precision="mixed", keep_pi=False)
-    resb = base.run(stream_of("all_green"), realtime=True)
-    out["one_at_a_time_all_green"] = summary(resb)
-    out["value"] = out["ours"]["solves_per_s"]
-    print(json.dumps(out), flush=True)
+    def serve(make, schedule):
+        rec = {}
+        for how, realtime in (("realtime", True), ("saturated", False)):
+            srv = make()
+            res = srv.run(stream_of(schedule, realtime), realtime=realtime)
+            rec[how] = dict(summary(res), **srv.stats)
+        return rec
 
+    out = {"metric": "serving: p50/p99 latency and solves/s (Poisson stream)", "unit": "solves/s",
+           "workload": f"{args.requests} requests at {args.rate}/s, a graph per request (n "
+                       f"{int(sizes.min())}..{int(sizes.max())}, {int(sizes.sum())} nodes in all), "
+                       f"tol in {{1e-4,1e-6,1e-8}}, HBM budget {args.budget_gb} GB",
+           "gen_s": gen_s, "graphs_resident_bytes": resident}
+    out["one_solve_at_a_time"] = serve(
+        lambda: BatchServer(args.budget_gb * 1e9, max_chains=args.batch_chains, precision="mixed",
+                            theta_scale=args.theta_scale, keep_pi=False, alone_nodes=args.alone_nodes),
+        "link_threshold")
+    out["per_request"] = serve(
+        lambda: Server(args.budget_gb * 1e9, max_active=args.slots, precision="mixed",
+                       theta_scale=args.theta_scale, keep_pi=False), "link_threshold")
+    out["one_at_a_time_all_green"] = serve(
+        lambda: Server(args.budget_gb * 1e9, max_active=1, precision="mixed", keep_pi=False), "all_green")
+    ours = out["one_solve_at_a_time"]
+    out["value"] = ours["saturated"]["solves_per_s"]
+    out["speedup_vs_one_at_a_time_all_green"] = {
+        how: ours[how]["solves_per_s"] / out["one_at_a_time_all_green"][how]["solves_per_s"]
+        for how in ("realtime", "saturated")}
+    print(json.dumps(out), flush=True)
 
 def run_reference(args):
     """The FP64 CPU oracle timed on the host cores on the same workload,
@@ -1178,7 +1231,9 @@ def main(argv=None):
     ap.add_argument("--chains", type=int, default=4096, help="batch: number of chains")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
-    ap.add_argument("--pool", type=int, default=32, help="serving: distinct graphs drawn from")
+    ap.add_argument("--batch-chains", type=int, default=1024, help="serving: most requests in one batch")
+    ap.add_argument("--alone-nodes", type=int, default=1 << 17,
+                    help="serving: requests of at least this many nodes are solved alone")
     ap.add_argument("--slots", type=int, default=32, help="serving: concurrent solves")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM budget")
     ap.add_argument("--sched", choices=["link_threshold", "threshold", "topfrac", "all_green"],

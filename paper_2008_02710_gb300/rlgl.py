@@ -214,7 +214,7 @@ class Chain:
         out = _VP()
         self.nchains = 1
         if node_ptr is not None:
-            npp, _, k6 = _ptr(node_ptr, cv(np.int64))
+            npp, _, k6 = _ptr(_like(node_ptr, csr.row_ptr), cv(np.int64))
             self.nchains = int(len(node_ptr)) - 1
             st = self.lib.rlgl_batch_create(self.nchains, npp, self.n, self.nnz, rp, cp, wp, prec, sp,
                                             sptr, ctypes.byref(out))
@@ -403,6 +403,11 @@ def _stream_ptr(stream):
 
 def _sched(s) -> int:
     return SCHEDULES[s] if isinstance(s, str) else int(s)
+
+
+def status_name(code: int) -> str:
+    """The rlgl_status name of a status code (a chain's, from Chain.chains())."""
+    return _STATUS.get(code, str(code))
 
 
 def footprint(n: int, nnz: int, weighted: bool, precision="mixed", n_chains: int = 1) -> int:

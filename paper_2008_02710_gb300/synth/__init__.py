@@ -18,6 +18,12 @@ graphs of 1e5..1e6 nodes with heavy-tailed degrees, Sec. 6, Table 1):
   two-wheels figure (Sec. 6).
 * dense fixtures for the mean-field stochastic block models (Sec. 4, 5) and
   doubly-stochastic permutation mixtures.
+* ``rmat_chain_n_device``: the same R-MAT recipe at any size drawn on a CUDA
+  device with PyTorch's seeded generator (a stream of requests needs
+  thousands of graphs of up to millions of nodes; the host generator takes
+  about a microsecond per node). Its graphs are not those of
+  ``rmat_chain_n`` for the same seed: the device generator is its own
+  seeded stream.
 
 The C part (``synth.c``) uses a counter-based generator, so every graph is a
 pure function of (sizes, seed) on any machine.
@@ -375,3 +381,65 @@ def pagerank_chain(csr: CSR, c_num: int = 17, c_den: int = 20) -> CSR:
     col[body] = csr.col + 1
     w[body] = float(c_num)
     return CSR(n + 1, row_ptr, col, w)
+
+
+def rmat_chain_n_device(n: int, edge_factor: int = 16, seed: int = 1, a: float = 0.57, b: float = 0.19,
+                        c: float = 0.19, device="cuda") -> CSR:
+    """R-MAT chain on n nodes drawn on a CUDA device: edge_factor * n R-MAT
+    edges at scale ceil(log2 n) (one quadrant per bit, endpoints outside
+    [0, n) drawn again), a seeded relabelling, then the cycle i -> i+1 and
+    self-loops; unit weights. Returns a CSR of device tensors (row_ptr int64,
+    col int32), in node order by source, stable in the draw order."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    m = int(edge_factor) * int(n)
+    scale = max(1, int(np.ceil(np.log2(max(n, 2)))))
+
+    def draw(k):
+        src = torch.zeros(k, dtype=torch.int64, device=device)
+        dst = torch.zeros(k, dtype=torch.int64, device=device)
+        for level in range(scale):
+            r = torch.rand(k, generator=g, device=device)
+            bit = 1 << (scale - 1 - level)
+            src += (r >= a + b).to(torch.int64) * bit
+            dst += (((r >= a) & (r < a + b)) | (r >= a + b + c)).to(torch.int64) * bit
+        return src, dst
+
+    src, dst = draw(m)
+    for _ in range(64):
+        bad = (src >= n) | (dst >= n)
+        k = int(bad.sum().item())
+        if k == 0:
+            break
+        s2, d2 = draw(k)
+        src[bad] = s2
+        dst[bad] = d2
+    else:
+        keep = (src < n) & (dst < n)
+        src, dst = src[keep], dst[keep]
+    perm = torch.randperm(n, generator=g, device=device)
+    src, dst = perm[src], perm[dst]
+    ids = torch.arange(n, dtype=torch.int64, device=device)
+    src = torch.cat([src, ids, ids])
+    dst = torch.cat([dst, (ids + 1) % n, ids])
+    order = torch.argsort(src, stable=True)
+    col = dst[order].to(torch.int32)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(torch.bincount(src, minlength=n), 0)
+    return CSR(int(n), row_ptr, col, None)
+
+
+def stack_chains_device(chains):
+    """Block-diagonal stack of several chains of device (or host) tensors:
+    returns (CSR of device tensors, node_ptr int64 numpy [k+1]). Unit
+    weights only."""
+    import torch
+    dev = chains[0].row_ptr.device if hasattr(chains[0].row_ptr, "device") else torch.device("cuda")
+    n_off = np.cumsum([0] + [c.n for c in chains]).astype(np.int64)
+    e_off = np.cumsum([0] + [int(c.row_ptr[-1]) for c in chains]).astype(np.int64)
+    rp = [torch.as_tensor(c.row_ptr, device=dev)[:-1] + int(e_off[k]) for k, c in enumerate(chains)]
+    rp.append(torch.tensor([int(e_off[-1])], dtype=torch.int64, device=dev))
+    col = [(torch.as_tensor(c.col, device=dev).to(torch.int64) + int(n_off[k])).to(torch.int32)
+           for k, c in enumerate(chains)]
+    return CSR(int(n_off[-1]), torch.cat(rp), torch.cat(col), None), n_off

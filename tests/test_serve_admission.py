@@ -89,3 +89,65 @@ def test_request_above_the_whole_budget_is_refused(fake):
     srv = serve.Server(hbm_budget_bytes=1000 * 100)
     with pytest.raises(ValueError):
         srv.run([_req(0, 101, 0.0)], realtime=False)
+
+
+class FakeBatch:
+    """A batch context stand-in: completes after two queries."""
+    made = []
+
+    def __init__(self, csr, precision="mixed", node_ptr=None):
+        self.csr = csr
+        self.k = 1 if node_ptr is None else len(node_ptr) - 1
+        self.polls = 2
+        FakeBatch.made.append(self.k)
+
+    def set_params(self, **kw):
+        pass
+
+    def set_chain_tol(self, tol):
+        assert len(tol) == self.k
+
+    def solve_async(self, schedule, theta, tol, max_steps):
+        pass
+
+    def query(self):
+        self.polls -= 1
+        return self.polls <= 0
+
+    def wait(self, raise_on_noconv=True):
+        return {"status": "RLGL_OK", "moves": 4, "edges_pushed": 0}
+
+    def chains(self):
+        return np.zeros(self.k, np.int32), np.full(self.k, 4, np.int64), np.zeros(self.k)
+
+    def estimate(self):
+        return np.ones(self.csr.n)
+
+    def close(self):
+        pass
+
+
+def test_batch_server_budget_cap_and_batches(monkeypatch):
+    FakeBatch.made = []
+    monkeypatch.setattr(serve.rlgl, "load", lambda *a, **k: None)
+    monkeypatch.setattr(serve.rlgl, "Chain", FakeBatch)
+    monkeypatch.setattr(serve.rlgl, "release_retired", lambda: None)
+    monkeypatch.setattr(serve.rlgl, "footprint", lambda n, nnz, weighted, precision: 1000 * n)
+    sizes = [50, 300, 120, 700, 90, 410, 60, 250, 330, 80, 500, 40]
+    reqs = [_req(i, n, 0.0) for i, n in enumerate(sizes)]
+    srv = serve.BatchServer(hbm_budget_bytes=1000 * 1000, max_chains=4, alone_nodes=600)
+    res = srv.run(reqs, realtime=False)
+    assert sorted(r.id for r in res) == list(range(len(sizes)))
+    assert all(r.status == "RLGL_OK" and len(r.pi) == sizes[r.id] for r in res)
+    assert srv.stats["max_used_bytes"] <= 1000 * 1000 and srv.stats["max_chains"] <= 4
+    # the oldest request decides: a large one (>= 600 nodes) runs alone; a
+    # small one opens a batch of every queued small request that fits the
+    # budget (1000 nodes) and the cap (4 chains), in arrival order
+    assert FakeBatch.made == [4, 1, 4, 3]
+    assert srv.stats["batches"] == 3 and srv.stats["alone"] == 1
+    # a batch's requests retire together; the large request retires alone
+    fin = {}
+    for r in res:
+        fin.setdefault(r.finish, []).append(sizes[r.id])
+    assert sorted(sorted(v) for v in fin.values()) == [[40, 330, 500], [50, 90, 120, 300], [60, 80, 250, 410],
+                                                        [700]]

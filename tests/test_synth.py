@@ -3,6 +3,7 @@ promises (these hold none of the method's arithmetic)."""
 import hashlib
 
 import numpy as np
+import pytest
 
 from paper_2008_02710_gb300 import synth
 
@@ -70,3 +71,26 @@ def test_powerlaw_chain():
     deg = g.degrees() - 2
     assert abs(deg.mean() - 8.0) < 0.5
     assert g.col.max() < 2000
+
+
+def test_device_rmat_generator_on_cpu_tensors():
+    """The device R-MAT generator (run here on CPU tensors): a valid CSR of
+    n nodes, 18 n links (16 n R-MAT + cycle + self-loops), every node with
+    its cycle edge and self-loop, skewed in-degrees, seeded."""
+    torch = pytest.importorskip("torch")
+    n = 5000
+    a = synth.rmat_chain_n_device(n, seed=3, device="cpu")
+    b = synth.rmat_chain_n_device(n, seed=3, device="cpu")
+    c = synth.rmat_chain_n_device(n, seed=4, device="cpu")
+    rp, col = a.row_ptr.numpy(), a.col.numpy()
+    assert a.n == n and rp[0] == 0 and rp[-1] == 18 * n and np.all(np.diff(rp) >= 2)
+    assert col.dtype == np.int32 and col.min() >= 0 and col.max() < n
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all(np.bincount(rows[col == rows], minlength=n) >= 1)  # self-loops
+    assert np.all(np.bincount(rows[col == (rows + 1) % n], minlength=n) >= 1)  # cycle
+    indeg = np.bincount(col, minlength=n)
+    assert indeg.max() > 20 * indeg.mean() / 2
+    assert np.array_equal(a.col.numpy(), b.col.numpy()) and not np.array_equal(a.col.numpy(), c.col.numpy())
+    stacked, node_ptr = synth.stack_chains_device([a, c])
+    assert stacked.n == 2 * n and int(stacked.row_ptr[-1]) == 36 * n
+    assert list(node_ptr) == [0, n, 2 * n] and int(stacked.col[-1]) >= n
