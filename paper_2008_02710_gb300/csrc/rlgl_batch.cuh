@@ -235,15 +235,26 @@ __device__ void batch_chain(const BatchArgs<T>& A, const Control& ctl, BatchSmem
         // ------------------------------------------------------ stats
         {
             T sa = T(0), ss = T(0), spr = T(0);
-            for (long long i = lo + threadIdx.x; i < hi; i += kBT) {
-                const T v = __ldcg(A.c + i);
-                const T av = fabs(v);
-                sa += av;
-                ss += v;
-                const T tv = link ? av * A.ideg[i] : av;
-                if (link && r == 1) spr += tv;
-                else if (r == 2) spr += tv * tv;
-                else if (r > 2) spr += pow_r(tv, r);
+            // kNodesPerThread nodes a thread, all loads issued before any sum
+            constexpr long long kUnit = (long long)kBT * kNodesPerThread;
+            for (long long it0 = lo; it0 < hi; it0 += kUnit) {
+                T v[kNodesPerThread], idg[kNodesPerThread];
+#pragma unroll
+                for (int q = 0; q < kNodesPerThread; ++q) {
+                    const long long i = it0 + q * kBT + threadIdx.x;
+                    v[q] = i < hi ? __ldcg(A.c + i) : T(0);
+                    idg[q] = (link && i < hi) ? __ldg(A.ideg + i) : T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < kNodesPerThread; ++q) {
+                    const T av = fabs(v[q]);
+                    sa += av;
+                    ss += v[q];
+                    const T tv = link ? av * idg[q] : av;
+                    if (link && r == 1) spr += tv;
+                    else if (r == 2) spr += tv * tv;
+                    else if (r > 2) spr += pow_r(tv, r);
+                }
             }
             T v3[4] = {sa, ss, spr, T(0)};
             block_sum_n<T, 4>(v3, tscratch);
@@ -333,14 +344,16 @@ __device__ void batch_chain(const BatchArgs<T>& A, const Control& ctl, BatchSmem
             for (long long it0 = lo; it0 < hi; it0 += (long long)kBT * kNodesPerThread) {
                 long long rb[kNodesPerThread];
                 int rdeg[kNodesPerThread];
-                T val[kNodesPerThread];
+                T val[kNodesPerThread], sc[kNodesPerThread];
                 bool gq[kNodesPerThread];
                 unsigned long long mine = 0ull;
+                // every load of the range before the first red_add below
 #pragma unroll
                 for (int q = 0; q < kNodesPerThread; ++q) {
                     const long long i = it0 + q * kBT + threadIdx.x;
                     const bool in = i < hi;
                     val[q] = in ? __ldcg(A.c + i) : T(0);
+                    sc[q] = in ? __ldg(scale + i) : T(0);
                     rb[q] = (in && !dense) ? __ldg(A.row_ptr + i) : 0;
                     rdeg[q] = (in && !dense) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
                     const T idg = (in && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
@@ -357,7 +370,7 @@ __device__ void batch_chain(const BatchArgs<T>& A, const Control& ctl, BatchSmem
                         red_add(A.H + i, (double)v);
                         msum += v;
                         mabs += fabs(v);
-                        A.mt[i] = v * __ldg(scale + i);
+                        A.mt[i] = v * sc[q];
                     }
                     continue;
                 }
@@ -374,7 +387,7 @@ __device__ void batch_chain(const BatchArgs<T>& A, const Control& ctl, BatchSmem
                     if (i >= hi) continue;
                     if (gq[q]) {
                         const T v = val[q];
-                        const T mtil = v * __ldg(scale + i);
+                        const T mtil = v * sc[q];
                         A.c[i] = T(0);
                         red_add(A.H + i, (double)v);
                         msum += v;

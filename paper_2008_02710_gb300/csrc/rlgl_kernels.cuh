@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
     for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
          it0 += (long long)gridDim.x * kNodesPerIter) {
         int idx[kNodesPerThread];
-        T val[kNodesPerThread];
+        T val[kNodesPerThread], scv[kNodesPerThread];
         long long rb[kNodesPerThread];
         int rdeg[kNodesPerThread];
         bool g[kNodesPerThread];
@@ -914,6 +914,8 @@ __global__ void __launch_bounds__(kThreads) k_select(
             idx[q] = (int)i;
             g[q] = false;
             val[q] = T(0);
+            // s_i now: red_add below orders every later load after it
+            scv[q] = (i < n) ? moved_per_weight(T(1), s, sf, i) : T(0);
             if (i < n) {
                 T v = c[i];
                 val[q] = v;
@@ -939,7 +941,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
                 red_add(H + i, (double)v);  // no load: the L2 adds
                 msum += v;
                 mabs += fabs(v);
-                mt[i] = moved_per_weight(v, s, sf, i);
+                mt[i] = v * scv[q];
             }
             continue;
         }
@@ -956,7 +958,7 @@ __global__ void __launch_bounds__(kThreads) k_select(
             if (i >= n) continue;
             if (g[q]) {
                 const T v = val[q];
-                const T mtil = moved_per_weight(v, s, sf, i);
+                const T mtil = v * scv[q];
                 c[i] = T(0);
                 red_add(H + i, (double)v);  // no load: the L2 adds
                 if (kBatch && uni < 0) {
@@ -1178,6 +1180,9 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
 #pragma unroll
         for (int q = 0; q < kPer; ++q) sm.row[threadIdx.x * kPer + q] = max(v[q], before);
         __syncthreads();
+        // every slot's target and amount first, then the additions: red_add
+        // is ordered with the thread's other memory accesses, so a load
+        // placed after one would wait for it, one round trip per slot
         int slot_j[kPer];
         T slot_v[kPer];
 #pragma unroll
@@ -1188,16 +1193,22 @@ __device__ __forceinline__ void push_chunks(T* __restrict__ c, const int* __rest
             if (le < ne) {
                 const int r = sm.row[le];
                 const long long pos = sm.base[r] + e0 + le;
-                const int j = __ldg(col + pos);
+                slot_j[q] = __ldg(col + pos);
                 T val = sm.m[r];
                 if (kHasW) val = val * (T)__ldg(w + pos);
-                const int hs = hub_slot(j);
-                if (hubs && sm.hub[hs] == j) {
-                    slot_j[q] = hs;  // summed below
-                } else {
-                    red_add(c + j, val);
-                }
                 slot_v[q] = val;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int j = slot_j[q];
+            if (j < 0) continue;
+            const int hs = hub_slot(j);
+            if (hubs && sm.hub[hs] == j) {
+                slot_j[q] = hs;  // summed below
+            } else {
+                red_add(c + j, slot_v[q]);
+                slot_j[q] = -1;
             }
         }
         if (hubs) {

@@ -338,17 +338,26 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
         // every node moves; the pull needs no frontier
         for (long long it0 = (long long)blockIdx.x * kNodesPerIter; it0 < n;
              it0 += (long long)gridDim.x * kNodesPerIter) {
+            // every load of the range first: red_add orders later loads after it
+            T val[kNodesPerThread], idg[kNodesPerThread], scv[kNodesPerThread];
+#pragma unroll
+            for (int q = 0; q < kNodesPerThread; ++q) {
+                const long long i = it0 + q * kThreads + threadIdx.x;
+                val[q] = i < n ? __ldcg(A.c + i) : T(0);
+                idg[q] = (i < n && link) ? __ldg(A.ideg + i) : T(0);
+                scv[q] = i < n ? moved_per_weight(T(1), A.s, A.sf, i) : T(0);
+            }
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
                 const long long i = it0 + q * kThreads + threadIdx.x;
                 if (i >= n) continue;
-                const T v = __ldcg(A.c + i);
-                if (acc_stats) stat(v, link ? __ldg(A.ideg + i) : T(0));
+                const T v = val[q];
+                if (acc_stats) stat(v, idg[q]);
                 A.c[i] = T(0);
                 red_add(A.H + i, (double)v);  // no load: the L2 adds
                 msum += v;
                 mabs += fabs(v);
-                A.mt[i] = moved_per_weight(v, A.s, A.sf, i);
+                A.mt[i] = v * scv[q];
             }
         }
         finish();
@@ -498,7 +507,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
              it0 += (long long)gridDim.x * kNodesPerIter) {
             long long rb[kNodesPerThread];
             int rdeg[kNodesPerThread];
-            T val[kNodesPerThread], idg[kNodesPerThread];
+            T val[kNodesPerThread], idg[kNodesPerThread], scv[kNodesPerThread];
             bool g[kNodesPerThread];
 #pragma unroll
             for (int q = 0; q < kNodesPerThread; ++q) {
@@ -507,6 +516,8 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 rdeg[q] = (i < n) ? (int)(__ldg(A.row_ptr + i + 1) - rb[q]) : 0;
                 val[q] = (i < n) ? __ldcg(A.c + i) : T(0);
                 idg[q] = (i < n && sched == SCHED_LINK) ? __ldg(A.ideg + i) : T(0);
+                // s_i now: red_add below orders every later load after it
+                scv[q] = (i < n) ? moved_per_weight(T(1), A.s, A.sf, i) : T(0);
             }
             unsigned long long mine = 0ull;
 #pragma unroll
@@ -529,7 +540,7 @@ __device__ __forceinline__ void sweep_select(const SweepArgs<T>& A, int sched, T
                 if (i >= n) continue;
                 if (g[q]) {
                     const T v = val[q];
-                    const T mtil = moved_per_weight(v, A.s, A.sf, i);
+                    const T mtil = v * scv[q];
                     A.c[i] = T(0);
                     red_add(A.H + i, (double)v);  // no load: the L2 adds
                     msum += v;
