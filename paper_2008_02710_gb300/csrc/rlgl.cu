@@ -777,8 +777,7 @@ static rlgl_status device_inclusive_scan(rlgl_ctx* ctx, long long* x, long long 
     CKL(ctx);
     k_scan_add<<<(unsigned)nb, kThreads, 0, ctx->stream>>>(x, m, tot);
     CKL(ctx);
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    dfree(ctx, tot);
+    dfree(ctx, tot);  // stream-ordered
     return RLGL_OK;
 }
 
@@ -823,9 +822,14 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
     return RLGL_OK;
 }
 
+static rlgl_status build_sweep_graph(rlgl_ctx* ctx, bool power);
+
+// eager_graph: build the single-chain sweep's solve graph on the host while
+// the device builds the in-link copy (the graph holds no parameter, only the
+// context's buffers and grids).
 static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
                                  const float* w, rlgl_precision prec, rlgl_memspace src,
-                                 void* stream, rlgl_ctx** out) {
+                                 void* stream, rlgl_ctx** out, bool eager_graph = false) {
     if (!out) return fail(nullptr, RLGL_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || n >= (1ll << kCountBits)) return fail(nullptr, RLGL_EINVAL, "n=%lld out of range [1, 2^27)", (long long)n);
@@ -944,26 +948,6 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     if (sc != RLGL_OK) { dfree(ctx, cursor); return sc; }
     CK(ctx, cudaMemcpyAsync(cursor, ctx->t_ptr, ((size_t)n + 1) * sizeof(long long),
                             cudaMemcpyDeviceToDevice, ctx->stream));
-    // edge-balanced scatter (a warp per row would leave one warp with every
-    // edge of a hub row)
-    const long long nch = (nnz + kPushChunk - 1) / kPushChunk;
-    k_chunk_rows<<<grid_for(nch + 1, kThreads, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
-        ctx->row_ptr, n, nnz, ctx->chunk_row);
-    k_csc_scatter<<<grid_for(nch, 1, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
-        ctx->row_ptr, ctx->col, ctx->w, nnz, ctx->chunk_row, cursor, ctx->t_src, ctx->t_w);
-    CKL(ctx);
-    const int gt = grid_for(ctx->ntiles + 1, kThreads, ctx->sms * 16);
-    k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
-                                                      ctx->tile_e);
-    CKL(ctx);
-    CK(ctx, cudaMemsetAsync(ctx->colsum, 0, (size_t)n * sizeof(double), ctx->stream));
-    if (ctx->has_w)
-        k_colsum_tiles<true><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
-    else
-        k_colsum_tiles<false><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
-    CKL(ctx);
     // Hub targets of the push: the nodes whose in-degree is at least
     // max(4096, n / 8, 32 x the mean), like the auxiliary node of a PageRank
     // chain, which every node feeds; up to one per slot of the direct-mapped
@@ -1043,6 +1027,31 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
             CK(ctx, cudaMemcpyAsync(ctx->hubs, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
         }
     }
+    // edge-balanced scatter (a warp per row would leave one warp with every
+    // edge of a hub row)
+    const long long nch = (nnz + kPushChunk - 1) / kPushChunk;
+    k_chunk_rows<<<grid_for(nch + 1, kThreads, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, n, nnz, ctx->chunk_row);
+    k_csc_scatter<<<grid_for(nch, 1, ctx->sms * 8), kThreads, 0, ctx->stream>>>(
+        ctx->row_ptr, ctx->col, ctx->w, nnz, ctx->chunk_row, cursor, ctx->t_src, ctx->t_w);
+    CKL(ctx);
+    const int gt = grid_for(ctx->ntiles + 1, kThreads, ctx->sms * 16);
+    k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
+                                                      ctx->tile_e);
+    CKL(ctx);
+    CK(ctx, cudaMemsetAsync(ctx->colsum, 0, (size_t)n * sizeof(double), ctx->stream));
+    if (ctx->has_w)
+        k_colsum_tiles<true><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
+    else
+        k_colsum_tiles<false><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
+            ctx->colsum, ctx->s, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles);
+    CKL(ctx);
+    if (eager_graph && ctx->params.persistent && build_sweep_graph(ctx, false) != RLGL_OK) {
+        // (the first solve tries again and falls back to the phase kernels)
+        cudaGetLastError();
+        ctx->err_msg[0] = '\0';
+    }
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     dfree(ctx, cursor);
     return RLGL_OK;
@@ -1075,7 +1084,7 @@ rlgl_status rlgl_create(int64_t n, int64_t nnz, const int64_t* row_ptr, const in
                         const float* w, const double* m0, rlgl_precision prec, rlgl_memspace src,
                         void* stream, rlgl_ctx** out) {
     rlgl_ctx* ctx = nullptr;
-    rlgl_status s = create_common(n, nnz, row_ptr, col, w, prec, src, stream, &ctx);
+    rlgl_status s = create_common(n, nnz, row_ptr, col, w, prec, src, stream, &ctx, true);
     if (s == RLGL_OK) s = set_step0(ctx, m0, src);
     if (s != RLGL_OK) {
         if (ctx) snprintf(g_thread_err, sizeof g_thread_err, "%s", ctx->err_msg);
