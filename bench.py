@@ -1006,7 +1006,7 @@ def run_batch(args):
                 # untimed: the fastest theta scale / r / crossover at this tolerance
                 from paper_2008_02710_gb300 import autotune
                 res = autotune.autotune(ch, sched, tol=tol, max_steps=20000,
-                                        grid={"theta_scale": (0.25, 0.5, 1.0), "r": (1, 2),
+                                        grid={"theta_scale": (0.0625, 0.25, 0.5, 1.0), "r": (1, 2),
                                               "pull_crossover": (0.25, 0.9),
                                               "batch_block": (128, 256, 512)})
                 tuned = res["best"]
