@@ -1047,6 +1047,18 @@ def run_batch(args):
                                        "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                        "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src,
                                        "alg_bytes": alg}}
+    # the random-access ceilings of this GPU (cash in L2): a pulled link
+    # costs one scattered gather, a pushed link one scattered add
+    scat, gath = random_access_peaks(1 << 20)
+    out["random_access"] = {"scatter_peak_gops": scat, "gather_peak_gops": gath,
+                            "probe": "4M random 4-byte accesses into 1048576 words"}
+    for sched, rate, how in (("link_threshold", scat, "every link pushed at the scattered-add rate"),
+                             ("all_green", gath, "every link pulled at the scattered-gather rate")):
+        if "ms" in out.get(sched, {}):
+            fl = out[sched]["edge_pushes"] / (rate * 1e9) * 1e3
+            out[sched]["random_access_floor_ms"] = fl
+            out[sched]["random_access_floor"] = how
+            out[sched]["over_floor"] = out[sched]["ms"] / fl
     if "ms" in out.get("link_threshold", {}):
         out["value"] = out["link_threshold"]["chains_per_s"]
         if "ms" in out.get("all_green", {}):
