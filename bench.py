@@ -713,6 +713,46 @@ def beyond_l2_record(args, device, peak, peak_src):
     return out
 
 
+def seeds_record(args, device, head, scale, r, lag, first):
+    """The headline workload drawn with seeds 2..args.seeds (seed 1 is the
+    timed run): each seed's time to L1 1e-6 of the headline schedule and of
+    all-green (T* calibrated per seed against that seed's oracle law; three
+    timed solves after one warm-up, L2 flushed before each), and the median
+    and spread over all seeds."""
+    import torch
+    per = [first]
+    for seed in range(2, args.seeds + 1):
+        csr, wl = make_workload(args.workload, seed=seed, precision=args.precision)
+        ref, _ = oracle_reference(csr, undirected=wl.get("undirected", False))
+        ref_dev = torch.from_numpy(ref).to(device)
+        g = GpuRun(csr, wl, device)
+        rec = {"seed": seed}
+        try:
+            for key, sched, sc, rr, lg in (("", head, scale, r, lag), ("all_green_", "all_green", 1.0, 1, 0)):
+                g.chain.set_params(theta_scale=sc, r=rr, theta_lag=lg, persistent=args.persistent)
+                tstar, e, _ = g.calibrate(sched, 0.0, ref_dev, max_moves=args.max_moves)
+                rec[key + "tstar"] = tstar
+                rec[key + "ms"] = None
+                if tstar:
+                    ts, _ = g.timed_solves(sched, 0.0, tstar, 3, 1)
+                    rec[key + "ms"] = float(np.median(ts))
+        finally:
+            g.chain.close()
+            del g
+            torch.cuda.empty_cache()
+        per.append(rec)
+
+    def spread(key):
+        v = [p[key] for p in per if p.get(key)]
+        return {"median": float(np.median(v)), "min": float(np.min(v)), "max": float(np.max(v))} if v else None
+
+    sp = [p["all_green_ms"] / p["ms"] for p in per if p.get("ms") and p.get("all_green_ms")]
+    return {"workload": args.workload, "seeds": len(per), "per_seed": per, "ms": spread("ms"),
+            "all_green_ms": spread("all_green_ms"), "tstar": spread("tstar"),
+            "speedup_vs_all_green": {"median": float(np.median(sp)), "min": float(np.min(sp)),
+                                     "max": float(np.max(sp))} if sp else None}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -840,9 +880,11 @@ def run_gpu(args):
     torch.cuda.synchronize(device)
     clk = clocks.stop()
     barrier(dist)
-    # final error of the timed run's estimate
+    # final error of the timed run's estimate, and the FP64 invariant
+    # residual ||C - H (P - I)||_1 of its state (Eq. recursion_H_res)
     with torch.cuda.stream(g.stream):
         final_err = float((g.pi_dev - ref_dev).abs().sum().item())
+    inv_resid = g.chain.invariant_residual()
     total_ms = float(np.sum(times))
     total_ms_max = max_over_ranks(dist, total_ms, device)
     pushes = float(sum(i["edges_pushed"] for i in infos))
@@ -911,6 +953,7 @@ def run_gpu(args):
         "compare": {k: {kk: vv for kk, vv in v.items() if kk in ("roofline", "sweep_phase_us_per_move")}
                     for k, v in compare.items() if "roofline" in v},
         "final_l1_err": final_err,
+        "invariant_residual_l1": inv_resid,
         "reference": ref_info,
         "roofline": roof,
         "random_access": {"scatter_peak_gops": scat_peak, "gather_peak_gops": gath_peak,
@@ -932,6 +975,12 @@ def run_gpu(args):
     g.chain.close()
     del g
     torch.cuda.empty_cache()
+    if ws == 1 and args.seeds > 1:
+        nvtx.range_push("seeds")
+        out["seeds"] = seeds_record(args, device, head, plan[head][2], r_of[head], lag_of[head],
+                                    {"seed": 1, "tstar": tstar, "ms": ms_per_step,
+                                     "all_green_tstar": ag.get("tstar"), "all_green_ms": ag.get("ms")})
+        nvtx.range_pop()
     if ws == 1 and args.beyond_l2 != "none":
         nvtx.range_push("beyond_l2")
         out["beyond_l2"] = beyond_l2_record(args, device, peak, peak_src)
@@ -1279,6 +1328,8 @@ def main(argv=None):
     ap.add_argument("--skip-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--seeds", type=int, default=5,
+                    help="draw the workload with seeds 1..N and report the median and spread (1: off)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-moves", type=int, default=2)
     ap.add_argument("--fixed-moves", type=int, default=0,
