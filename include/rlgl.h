@@ -110,10 +110,11 @@ typedef struct {
     int64_t rr_blocks;      /* BLOCK_RR: number of blocks K (default 8) */
     double pc_frac;         /* PC: expected green fraction k / N before capping (default 0.05) */
     uint64_t seed;          /* PC: seed of the counter-based draws (default 0) */
-    int32_t persistent;     /* 1 (default): a single-chain solve with any schedule but TOPFRAC runs
-                               as one persistent cooperative kernel per stretch between FP64
+    int32_t persistent;     /* 1 (default): a single-chain solve with any schedule runs as one
+                               persistent cooperative kernel per stretch between FP64
                                re-derivations of the cash, with grid barriers between the phases
-                               of a move; 0: one kernel per phase. Same moves either way. */
+                               of a move (TOPFRAC: one more per radix pass of its threshold);
+                               0: one kernel per phase. Same moves either way. */
     double barrier_limit_s; /* persistent sweep: longest wait at a grid barrier (default 2,
                                at most 60); a wait that runs out ends the solve with
                                RLGL_ETIMEOUT and leaves the context usable */
@@ -325,7 +326,8 @@ rlgl_status rlgl_profile_moves(rlgl_ctx* ctx, rlgl_schedule sched, double theta,
  * made as a solve with tol 0 and max_steps = moves, the sweep launched
  * eagerly with a CUDA event pair around each launch (class 6) and around
  * each FP64 re-derivation kernel (class 5). EINVAL when the sweep does not
- * serve the context (batch) or the schedule (TOPFRAC). Synchronises; the
+ * serve the context (batch) or the setting (TOPFRAC with theta_lag).
+ * Synchronises; the
  * solve ends with status ENOCONV on the device, which this call does not
  * report. */
 rlgl_status rlgl_profile_sweep(rlgl_ctx* ctx, rlgl_schedule sched, double theta, int64_t moves);

@@ -625,7 +625,8 @@ static int power_grid(rlgl_ctx* ctx) {
 
 // Whether a solve with this schedule runs as the persistent sweep.
 static bool use_sweep(const rlgl_ctx* ctx, int sched) {
-    return ctx->params.persistent && ctx->nchains <= 1 && sched != RLGL_TOPFRAC && ctx->grid_sweep > 0;
+    return ctx->params.persistent && ctx->nchains <= 1 && ctx->grid_sweep > 0 &&
+           !(sched == RLGL_TOPFRAC && ctx->params.theta_lag);
 }
 
 // Whether it runs as the all-green (power) sweep: all-green with the plain
@@ -1624,7 +1625,9 @@ static rlgl_status solve_launch(rlgl_ctx* ctx, rlgl_schedule sched, double theta
         cudaGetLastError();
     }
     if (!sweep && ctx->params.theta_lag)
-        return fail(ctx, RLGL_EINVAL, "theta_lag needs the persistent sweep (not TOPFRAC, batches or persistent = 0)");
+        return fail(ctx, RLGL_EINVAL,
+                    "theta_lag needs the persistent sweep and a threshold schedule (not TOPFRAC, batches or "
+                    "persistent = 0)");
     const bool bsweep = use_bsweep(ctx, sched);
     if (bsweep) {
         TRY(batch_prepare(ctx));

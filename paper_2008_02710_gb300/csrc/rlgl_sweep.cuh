@@ -70,6 +70,7 @@ struct alignas(128) GridBar {
     unsigned long long arrived;  // arrivals since the solve began (grid size per barrier)
     unsigned int abort;          // a wait gave up: every block leaves
     unsigned int parity;         // slot of the next move (kept across launches)
+    unsigned int tk_pass;        // top-k radix passes made so far (kept across launches)
 };
 
 // The two 8-byte fields at p (16-byte aligned), read from L2 in one request.
@@ -80,6 +81,11 @@ __device__ __forceinline__ double2 ldcg_pair(const void* p) {
 struct SweepState {
     GridBar bar;
     SweepSlot slot[3];  // the general sweep alternates slots 0 and 1; the all-green sweep rotates all three
+    // TOPFRAC: the radix passes' digit histograms (zero at rest), three in
+    // rotation: pass q adds into q mod 3, every block reads it after the
+    // pass's barrier, and block 0 then clears (q + 2) mod 3, which every
+    // block read before that barrier and pass q + 2 will fill after the next.
+    unsigned int tk_hist[3][kRadixBins];
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
@@ -688,7 +694,85 @@ union SweepSmem {
     PushSmem<T> push;
     PullSmem<T> pull;
     SelSmem<T> sel;
+    unsigned int hist[kRadixBins];  // TOPFRAC: the block's digit histogram
 };
+
+// TOPFRAC inside the sweep: one pass of the exact k-th largest |C| by radix
+// select over the IEEE bit patterns of |C| (the phase form is k_radix_pass).
+// The block counts the digit at `shift` (`width` bits) of the keys that
+// match `prefix` above it, over its grid-stride share of the nodes (equal
+// digits of a warp merged with __match_any_sync, one shared-memory add per
+// distinct digit), and adds its nonzero counts to the pass's histogram.
+template <typename T>
+__device__ __forceinline__ void sweep_radix_count(const T* c, int n, unsigned int* ghist, unsigned long long prefix,
+                                                  int shift, int width, unsigned int* h) {
+    const int nbins = 1 << width;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const int hi_shift = shift + width;
+    const unsigned long long mask = (unsigned long long)(nbins - 1);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const long long i = base + lane;
+        int digit = -1;
+        if (i < n) {
+            // the cash other blocks moved last move: from L2
+            const unsigned long long k = (unsigned long long)KeyOf<T>::key(__ldcg(c + i));
+            const bool match = (hi_shift >= KeyOf<T>::bits) || ((k >> hi_shift) == (prefix >> hi_shift));
+            if (match) digit = (int)((k >> shift) & mask);
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, digit);
+        if (digit >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[digit], (unsigned int)__popc(peers));
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (h[b]) atomicAdd(&ghist[b], h[b]);
+}
+
+// After the pass's barrier: the bucket of the remaining k-th largest key,
+// the same in every block (the same counts, the same scan). Thread t owns 8
+// bins counted from the top; thread 0 gets the new prefix and remainder.
+__device__ __forceinline__ void sweep_radix_pick(const unsigned int* ghist, int shift, int width,
+                                                 unsigned long long& prefix, long long& remain) {
+    __shared__ int found;
+    __shared__ long long above_found;
+    if (threadIdx.x == 0) found = -1;
+    constexpr int per = kRadixBins / kThreads;  // 8
+    const int nbins = 1 << width;
+    const int top = nbins - 1 - (int)threadIdx.x * per;
+    unsigned long long mine = 0;
+    unsigned int hb[per];
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int b = top - q;
+        hb[q] = (b >= 0) ? __ldcg(&ghist[b]) : 0u;
+        mine += hb[q];
+    }
+    unsigned long long total;
+    const unsigned long long above = block_exscan(mine, &total);
+    const long long rem = remain;
+    if ((long long)above < rem && (long long)(above + mine) >= rem) {
+        long long cum = (long long)above;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+            const int b = top - q;
+            if (b >= 0 && cum + (long long)hb[q] >= rem) {
+                found = b;
+                above_found = cum;
+                break;
+            }
+            cum += hb[q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int digit = found >= 0 ? found : 0;
+        const long long cum = found >= 0 ? above_found : 0;
+        prefix |= (unsigned long long)digit << shift;
+        remain = rem - cum;
+    }
+}
 
 // The evolving scalars of the solve, one copy per block in shared memory,
 // kept by the block's thread 0. Every block's copy goes through the same
@@ -718,6 +802,10 @@ struct SweepCtl {
     int stop_after;    // status to stop with after this move (-1: none)
     int lag_stop;      // stale threshold: the next move's stop before it selects (-1: none)
     int pre_done;      // the next move's decisions are taken (sweep_lag_control)
+    // TOPFRAC: this move's radix select
+    unsigned long long tk_prefix;
+    long long tk_remain;
+    unsigned int tk_pass;  // passes made by the solve so far (histogram rotation)
 };
 
 // This move's schedule, threshold and schedule constants from the
@@ -816,6 +904,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         const unsigned long long arr = ld_acquire_u64(&sw->bar.arrived);
         sc.target = arr - arr % gridDim.x;
         sc.p = (int)(sw->bar.parity & 1u);
+        sc.tk_pass = sw->bar.tk_pass;
         sc.have_lag = 0;
         sc.stop_after = -1;
         sc.pre_done = 0;
@@ -907,6 +996,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 if (sc.leave) {
                     st->mode = MODE_NONE;
                     sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                    sw->bar.tk_pass = sc.tk_pass;
                     if (stop >= 0) {
                         st->done = 1;
                         st->status = stop;
@@ -937,6 +1027,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 st->iters = sc.iters;
                 st->mode = MODE_NONE;
                 sw->bar.parity = (unsigned int)sc.p;
+                sw->bar.tk_pass = sc.tk_pass;
                 st->done = 1;
                 st->status = stop;
                 if (A.use_cond) {
@@ -947,6 +1038,42 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
         }
         __syncthreads();
         if (sc.leave) return;
+        }
+
+        // ------------------------------------------------ top-k threshold
+        // TOPFRAC: theta = the exact k-th largest |C| (k = ceil(f N)), one
+        // radix pass and one grid barrier per digit
+        if (sc.sched == SCHED_TOPFRAC) {
+            if (threadIdx.x == 0) {
+                const double f = (ctl.theta_arg > 0.0 && ctl.theta_arg <= 1.0) ? ctl.theta_arg : ctl.top_frac;
+                long long k = (long long)ceil(f * (double)n);
+                if (k < 1) k = 1;
+                if (k > n) k = n;
+                sc.tk_prefix = 0ull;
+                sc.tk_remain = k;
+            }
+            __syncthreads();
+            bool bar_ok = true;
+            for (int hi = KeyOf<T>::bits; hi > 0; hi -= kRadixBits) {
+                const int width = hi >= kRadixBits ? kRadixBits : hi;
+                const int shift = hi - width;
+                const unsigned int q = sc.tk_pass;
+                sweep_radix_count<T>(A.c, n, sw->tk_hist[q % 3u], sc.tk_prefix, shift, width, sm.hist);
+                if (!(bar_ok = grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns))) break;
+                if (blockIdx.x == 0) {
+                    unsigned int* old = sw->tk_hist[(q + 2u) % 3u];
+                    for (int b = threadIdx.x; b < kRadixBins; b += blockDim.x) old[b] = 0u;
+                }
+                sweep_radix_pick(sw->tk_hist[q % 3u], shift, width, sc.tk_prefix, sc.tk_remain);
+                if (threadIdx.x == 0) sc.tk_pass = q + 1u;
+                __syncthreads();
+            }
+            if (!bar_ok) break;
+            if (threadIdx.x == 0) {
+                sc.theta = KeyOf<T>::value(sc.tk_prefix);
+                sc.theta_f = __double2float_ru(sc.theta);
+            }
+            __syncthreads();
         }
 
         // --------------------------------------------------------- select
@@ -1099,6 +1226,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
                 st->status = sc.stop_after;
                 st->mode = MODE_NONE;
                 sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                sw->bar.tk_pass = sc.tk_pass;
                 if (A.use_cond) {
                     cudaGraphSetConditional(A.cond_loop, 0u);
                     if (ctl.mixed) cudaGraphSetConditional(A.cond_refresh, 0u);
@@ -1110,6 +1238,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_sweep(SweepArgs<T
             if (lead) {
                 st->want_refresh = 1;
                 sw->bar.parity = (unsigned int)(sc.p ^ 1);
+                sw->bar.tk_pass = sc.tk_pass;
                 if (A.use_cond) cudaGraphSetConditional(A.cond_refresh, 1u);
             }
             return;

@@ -117,16 +117,58 @@ def test_profile_sweep_times_the_kernel(weighted):
     assert np.abs(ha - hb).sum() <= 1e-6 * np.abs(hb).sum()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["weighted", "unweighted"])
+def test_sweep_topfrac_threshold_is_the_kth_largest(request, which, prec):
+    """TOPFRAC in the sweep (radix passes with a grid barrier each): move
+    after move, theta is exactly the k-th largest |C| of the state before
+    the move (k = ceil(f N)), and the green set is every nonzero node at or
+    above it, ties included."""
+    csr = request.getfixturevalue(which)
+    f = 0.05
+    k = int(np.ceil(f * csr.n))
+    with Chain(csr, precision=prec) as ch:
+        for m in range(12):
+            c, _ = ch.get_state()
+            ac = np.abs(c)
+            kth = np.sort(ac)[::-1][k - 1]
+            green = int(((ac >= kth) & (c != 0)).sum())
+            ch.solve("topfrac", f, tol=0.0, max_steps=1, raise_on_noconv=False)
+            assert ch.get_params().persistent == 1
+            rec = ch.move_log(1)[-1]
+            assert rec["theta"] == kth, (m, rec["theta"], kth)
+            assert rec["green"] == green, (m, rec["green"], green)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sweep_topfrac_solves_like_phase_kernels(weighted, prec):
+    """The same TOPFRAC solve through the sweep and through the phase
+    kernels: both stop, a few moves apart at most, at the same law."""
+    tol = 1e-11 if prec == "fp64" else 1e-8
+    with Chain(weighted, precision=prec) as a, Chain(weighted, precision=prec) as b:
+        b.set_params(persistent=0)
+        ia = a.solve("topfrac", 0.05, tol=tol, max_steps=100000)
+        ib = b.solve("topfrac", 0.05, tol=tol, max_steps=100000)
+        pa, pb = a.estimate(), b.estimate()
+    assert ia["status"] == ib["status"] == "RLGL_OK"
+    # ties at the k-th value split differently once rounding differs, so
+    # the two trajectories part after a few moves
+    assert abs(ia["moves"] - ib["moves"]) <= max(3, ib["moves"] // 20)
+    assert np.abs(pa - pb).sum() <= (1e-9 if prec == "fp64" else 2e-6)
+
+
 def test_sweep_not_used_where_it_does_not_apply(weighted):
-    """TOPFRAC and batches keep the one-kernel-per-phase path; asking to
-    profile the sweep there is an error."""
+    """The stale threshold does not apply to TOPFRAC, and batches keep their
+    own launch: asking for either is an error."""
     from paper_2008_02710_gb300.rlgl import RLGLError
     with Chain(weighted) as ch:
-        info = ch.solve("topfrac", 0.05, tol=1e-10, max_steps=100000)
-        assert info["status"] == "RLGL_OK"
+        ch.set_params(theta_lag=1)
         with pytest.raises(RLGLError) as e:
-            ch.profile_sweep("topfrac", 0.05, 5)
+            ch.solve("topfrac", 0.05, tol=1e-10, max_steps=100000)
         assert e.value.name == "RLGL_EINVAL"
+        ch.set_params(theta_lag=0)
+        kt = ch.profile_sweep("topfrac", 0.05, 5)
+        assert kt["sweep"][1] >= 1
     big, node_ptr = synth.stack_chains([synth.tiny_chain(300, seed=s) for s in (1, 2, 3)])
     with Chain(big, node_ptr=node_ptr) as ch:
         with pytest.raises(RLGLError):
