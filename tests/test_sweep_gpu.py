@@ -218,18 +218,23 @@ def test_sweep_large_chain_single_pass_select():
     assert abs(info["edges_pushed"] - info_or["pushes"]) <= 1e-4 * info_or["pushes"]
 
 
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("theta_lag", [0, 1])
-def test_sweep_large_chain_mixed_pipelined_select(theta_lag):
+def test_sweep_large_chain_mixed_pipelined_select(theta_lag, weighted):
     """MIXED cash on more nodes than the select cache covers (n > blocks x
     2048): node ranges stream through the two shared-memory stages, handed
-    out by a counter after the first two per block. After 25 moves (no
-    re-derivation yet) the FP32 cash has drifted from the oracle's FP64
-    trajectory by rounding only (~1e-6 relative per node); a range skipped or
-    moved twice would leave ~2e-4 of the mass out. Without the stale
-    threshold the sweep also agrees with the one-kernel-per-phase path (both
-    FP32) move by move."""
+    out by a counter after the first two per block (with weights, s_i is
+    staged beside 1/d). After 25 moves (no re-derivation yet) the FP32 cash
+    has drifted from the oracle's FP64 trajectory by rounding only (~1e-6
+    relative per node); a range skipped or moved twice would leave ~2e-4 of
+    the mass out. Without the stale threshold the sweep also agrees with the
+    one-kernel-per-phase path (both FP32) move by move."""
     import oracle
     csr = synth.rmat_chain_n((1 << 21) + 54321, 3, seed=12)
+    if weighted:
+        rng = np.random.default_rng(12)
+        w = (rng.integers(1, 1 << 24, csr.nnz) * 2.0 ** -24).astype(np.float32)
+        csr = synth.CSR(csr.n, csr.row_ptr, csr.col, w)
     p = oracle.transition_probs(csr)
     C, H = oracle.initial_step(csr, p)
     info_or = oracle.solve(csr, p, C, H, sched=oracle.LINK_THRESHOLD, theta_scale=0.5, tol=0.0,
