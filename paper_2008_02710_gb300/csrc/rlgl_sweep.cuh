@@ -8,6 +8,8 @@
 //             statistic in the move's slot;
 //   barrier ; every block reads the totals and takes the same decisions
 //             (stop, re-derivation, theta) from the same numbers;
+//   [top-k] : TOPFRAC only: the radix passes of the exact k-th largest |C|,
+//             each a count over the block's nodes and a barrier;
 //   select  : its node ranges, staged in shared memory by asynchronous
 //             copies (the same compaction as k_select);
 //   barrier ; every block reads the frontier size and picks push or pull;
