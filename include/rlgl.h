@@ -341,9 +341,8 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
  * ||C - C_0 - H (P - I)||_1 for a state held in the caller's own device
  * buffers, computed without allocating any device memory. The paper has no
  * counterpart: this entry point exists for callers that may not call
- * cudaMalloc or cudaFree, for example while recording a CUDA stream capture,
- * or inside a service whose device memory belongs to a framework's pool
- * (cudaFree also synchronises the whole device).
+ * cudaMalloc or cudaFree, for example a service whose device memory belongs
+ * to a framework's pool (cudaFree also synchronises the whole device).
  *   n, nnz, row_ptr, col, w : the chain as for rlgl_create, all DEVICE
  *              pointers (w may be NULL: unit weights).
  *   c, h     : device double [n], the cash C_t and history H_t.
@@ -360,8 +359,7 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
  * when a launch fails, or, with nothing queued, when an error of earlier
  * work is already pending on the calling thread (that error is left pending
  * for its owner, not cleared). The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress), so make it before any stream
- * capture. All calls on a device share the array and each one clears it
+ * device address (cudaGetSymbolAddress). All calls on a device share the array and each one clears it
  * first, so calls whose work overlaps on the GPU (two streams, or two
  * threads) race and give wrong results; serialise them.
  */

@@ -3,10 +3,10 @@
 // device allocation at all.
 //
 // Who needs this: code that may not call cudaMalloc or cudaFree. Examples are
-// a caller recording a CUDA stream capture, a service whose device memory is
-// handed out by a framework's own pool (cudaFree also synchronises the whole
-// device, stalling every other stream), or a process that has already
-// reserved all of the GPU's memory for its pools. Such code can still run
+// a service whose device memory is handed out by a framework's own pool
+// (cudaFree also synchronises the whole device, stalling every other
+// stream), or a process that has already reserved all of the GPU's memory
+// for its pools. Such code can still run
 // this check on a state it holds in its own buffers.
 //
 // The scratch lives in one file-scope __device__ array of fixed size, so the

@@ -1,6 +1,6 @@
 """rlgl_invariant_residual_noalloc: the cash-balance residual for callers
-that may not allocate device memory (a stream capture in progress, or device
-memory owned by another framework's pool). It is called here through the C
+that may not allocate device memory (device memory owned by another
+framework's pool, for example). It is called here through the C
 ABI on plain device buffers and checked against the oracle's residual
 ||C - C_0 - H (P - I)||_1 (Eq. recursion_H_res) and against the context's
 own rlgl_invariant_residual, on calls in a row on different chains (a call
