@@ -358,9 +358,10 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
  * RLGL_EINVAL beyond that, for NULL pointers, or for n or nnz < 1. RLGL_ECUDA
  * when a launch fails, or, with nothing queued, when an error of earlier
  * work is already pending on the calling thread (that error is left pending
- * for its owner, not cleared). The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress). All calls on a device share the array and each one clears it
- * first, so calls whose work overlaps on the GPU (two streams, or two
+ * for its owner, not cleared). The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress). All calls on a device share
+ * the array and each one clears it first, so calls whose work overlaps on
+ * the GPU (two streams, or two
  * threads) race and give wrong results; serialise them.
  */
 rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr,
