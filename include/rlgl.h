@@ -361,8 +361,8 @@ rlgl_status rlgl_move_log(rlgl_ctx* ctx, rlgl_move_record* out, int64_t count, i
  * for its owner, not cleared). The first call on each device looks up that
  * array's device address (cudaGetSymbolAddress). All calls on a device share
  * the array and each one clears it first, so calls whose work overlaps on
- * the GPU (two streams, or two
- * threads) race and give wrong results; serialise them.
+ * the GPU (two streams, or two threads) race and give wrong results;
+ * serialise them.
  */
 rlgl_status rlgl_invariant_residual_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr,
                                             const int32_t* col, const float* w, const double* c,
