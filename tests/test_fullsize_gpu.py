@@ -1,8 +1,10 @@
-"""Full-size parity on R-MAT scale 20 (N = 2^20, nnz = 18,874,368), in the
-launch configuration the bench times (device-loop solve, MIXED precision):
-the estimate against the oracle's reference law, one move against the
-oracle's move of the same state, and the symmetrised graph against the
-closed form pi_i = d_i / sum d."""
+"""Full-size parity in the launch configurations the bench times
+(device-loop solves, MIXED precision). R-MAT scale 20 (N = 2^20, nnz =
+18,874,368): the estimate against the oracle's reference law, one move
+against the oracle's move of the same state, and the symmetrised graph
+against the closed form pi_i = d_i / sum d. Symmetrised R-MAT 24 (beyond
+L2) against the same closed form, and the 4096-chain batch in one launch
+against the oracle's law of every chain."""
 import os
 
 import numpy as np
@@ -111,3 +113,43 @@ def test_rmat20_undirected_degree_law(prec, bound):
         pi = ch.estimate()
     assert info["status"] == "RLGL_OK"
     assert np.abs(pi - d / d.sum()).sum() <= bound
+
+
+def test_rmat24_symmetrised_headline_path_against_degree_law():
+    """Beyond L2, at the full size of the symmetrised R-MAT 24 workload
+    (N = 2^24, 587 M links; CSR and CSC take 4.8 GB): the headline path
+    (MIXED, persistent sweep, per-link threshold at scale 1/2 with the stale
+    threshold), a fixed 900 moves from step 0 as the bench runs it (its
+    calibration needs 839), against the closed form pi_i = d_i / sum d."""
+    csr = synth.rmat_chain(24, 16, seed=1, undirected=True)
+    d = csr.degrees().astype(np.float64)
+    with Chain(csr, precision="mixed") as ch:
+        ch.set_params(theta_scale=0.5, theta_lag=1)
+        info = ch.solve("link_threshold", 0.0, tol=0.0, max_steps=900, raise_on_noconv=False)
+        pi = ch.estimate()
+    assert info["moves"] == 900
+    assert np.abs(pi - d / d.sum()).sum() <= 1e-6
+    assert abs(pi.sum() - 1.0) < 1e-12
+
+
+def test_batch_4096_chains_one_launch_against_oracle():
+    """The batch workload at full size (4096 power-law chains, 59.5 M nodes,
+    1.18 G links) in one persistent launch, MIXED: every chain reaches L1
+    error 1e-6 against its own law, the oracle's power iteration over the
+    whole block-diagonal chain normalised per chain."""
+    csr, node_ptr = synth.powerlaw_batch(4096, seed=1)
+    p = oracle.transition_probs(csr)
+    ref, _, _ = oracle.power_iteration(csr, p, tol=1e-11, maxit=20000, nthreads=THREADS)
+    del p
+    seg = np.repeat(np.arange(4096), np.diff(node_ptr))
+    ref = ref / np.bincount(seg, weights=ref, minlength=4096)[seg]
+    with Chain(csr, precision="mixed", node_ptr=node_ptr) as ch:
+        ch.set_params(theta_scale=0.0625, batch_block=256)
+        assert ch.get_params().persistent == 1
+        info = ch.solve("link_threshold", 0.0, tol=1e-7, max_steps=20000)
+        st, mv, _ = ch.chains()
+        pi = ch.estimate()
+    assert info["status"] == "RLGL_OK" and np.all(st == 0)
+    err = np.bincount(seg, weights=np.abs(pi - ref), minlength=4096)
+    assert err.max() <= 1e-6, (int(err.argmax()), float(err.max()))
+    assert np.all(mv > 0)
