@@ -276,6 +276,29 @@ def oracle_mt_time_to_err(csr, ref, nthreads):
 
 # ------------------------------------------------------------------ GPU
 
+def move_alg_bytes(sched, log, n, nnz, cash, weighted, sweep=False):
+    """Algorithmic bytes per kernel class of the logged moves (the byte model
+    of GpuRun.alg_bytes) for a chain of n nodes and nnz links, cash of
+    `cash` bytes."""
+    wb = 4 if weighted else 0
+    alg = {k: 0.0 for k in KERNEL_CLASSES}
+    for rec in log:
+        E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
+        if not (sweep and rec["phase_us"][0] == 0.0 and rec["phase_us"][1] == 0.0):
+            alg["stats"] += n * cash
+        dense = sched == "all_green" or (mode == 2 and G == n)
+        if not dense:
+            alg["select"] += n * cash
+        if mode == 2:
+            alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash + 16)
+        elif mode == 1:
+            alg["select"] += G * (8 + 8 + 2 * cash + 16 + 4)
+            alg["push"] += E * (4 + wb + cash) + G * 4
+        if sched == "topfrac":
+            alg["topk"] += (3 if cash == 4 else 6) * n * cash
+    return alg
+
+
 class GpuRun:
     def __init__(self, csr, wl, device):
         import torch
@@ -415,25 +438,8 @@ class GpuRun:
         On the sweep, a move of the stale threshold has no statistics pass
         (its log entry has no statistics time)."""
         csr = self.csr
-        n, nnz = csr.n, csr.nnz
         cash = 4 if self.wl["precision"] == "mixed" else 8
-        wb = 4 if csr.w is not None else 0
-        alg = {k: 0.0 for k in KERNEL_CLASSES}
-        for rec in log:
-            E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
-            if not (sweep and rec["phase_us"][0] == 0.0 and rec["phase_us"][1] == 0.0):
-                alg["stats"] += n * cash
-            dense = sched == "all_green" or (mode == 2 and G == n)
-            if not dense:
-                alg["select"] += n * cash
-            if mode == 2:
-                alg["pull"] += nnz * (4 + wb + cash) + n * (8 + 2 * cash + 16)
-            elif mode == 1:
-                alg["select"] += G * (8 + 8 + 2 * cash + 16 + 4)
-                alg["push"] += E * (4 + wb + cash) + G * 4
-            if sched == "topfrac":
-                alg["topk"] += (3 if cash == 4 else 6) * n * cash
-        return alg
+        return move_alg_bytes(sched, log, csr.n, csr.nnz, cash, csr.w is not None, sweep)
 
     def sweep_profile(self, sched, theta, tstar):
         """T* moves of the persistent sweep launched eagerly, each launch
@@ -1268,15 +1274,9 @@ def run_fixed(args):
             pi = ch.estimate()
             log = ch.move_log(T)
         cash = 4 if prec == "mixed" else 8
-        wb = 4 if csr.w is not None else 0
-        alg = 0.0
-        for rec in log:
-            E, G, mode = rec["edges_pushed"], rec["green"], rec["mode"]
-            alg += csr.n * (cash + 4) + csr.n * (2 * cash + 4) + G * (cash + 16 + 8 + 16 + 16 + cash)
-            if mode == 1:
-                alg += E * (4 + wb + cash) + G * (16 + cash)
-            elif mode == 2:
-                alg += csr.nnz * (4 + wb + cash) + csr.n * (8 + 2 * cash)
+        # the byte model of the main record (sweep moves with a statistics pass)
+        alg = sum(move_alg_bytes(sched, log, csr.n, csr.nnz, cash, csr.w is not None,
+                                 sweep=args.persistent == 1).values())
         ms = float(np.median(times))
         out[prec] = {"ms": ms, "edge_pushes": info["edges_pushed"],
                      "edge_pushes_per_s": info["edges_pushed"] / (ms / 1e3),

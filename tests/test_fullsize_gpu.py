@@ -153,3 +153,26 @@ def test_batch_4096_chains_one_launch_against_oracle():
     err = np.bincount(seg, weights=np.abs(pi - ref), minlength=4096)
     assert err.max() <= 1e-6, (int(err.argmax()), float(err.max()))
     assert np.all(mv > 0)
+
+
+def test_rmat24_weighted_fp64_and_mixed_against_oracle_moves():
+    """The weighted R-MAT 24 workload at full size (N = 2^24, 302 M links,
+    U(0,1] weights): 12 moves of the per-link threshold from step 0 on the
+    FP64 path and on the MIXED path (FP32 cash, FP64 history) against the
+    oracle's 12 moves of the same chain (its relaxation time puts L1 1e-6
+    out of reach of every schedule, so the paths are compared at equal
+    moves)."""
+    csr = synth.rmat_chain(24, 16, seed=1, weighted=True)
+    p = oracle.transition_probs(csr)
+    C, H = oracle.initial_step(csr, p)
+    oracle.solve(csr, p, C, H, sched=oracle.LINK_THRESHOLD, theta_scale=0.5, tol=0.0, max_steps=12,
+                 check_every=-1)
+    pi_or = oracle.estimate(H)
+    del p, C, H
+    for prec, bound in (("fp64", 1e-12), ("mixed", 2e-6)):
+        with Chain(csr, precision=prec) as ch:
+            ch.set_params(theta_scale=0.5)
+            info = ch.solve("link_threshold", 0.0, tol=0.0, max_steps=12, raise_on_noconv=False)
+            pi = ch.estimate()
+        assert info["moves"] == 12
+        assert np.abs(pi - pi_or).sum() <= bound, (prec, float(np.abs(pi - pi_or).sum()))
