@@ -63,6 +63,9 @@ struct rlgl_ctx {
     long long* tile_r = nullptr;
     long long* tile_e = nullptr;
     long long ntiles = 0;
+    long long* wtile_r = nullptr;  // the same split at warp tiles (the power sweep)
+    long long* wtile_e = nullptr;
+    long long nwtiles = 0;
     // state and scratch
     void* c = nullptr;       // cash, float (MIXED) or double (FP64)
     double* H = nullptr;
@@ -448,6 +451,9 @@ static SweepArgs<T> sweep_args(rlgl_ctx* ctx, const Conds& cd) {
     a.tile_r = ctx->tile_r;
     a.tile_e = ctx->tile_e;
     a.ntiles = ctx->ntiles;
+    a.wtile_r = ctx->wtile_r;
+    a.wtile_e = ctx->wtile_e;
+    a.nwtiles = ctx->nwtiles;
     a.st = ctx->st;
     a.sw = ctx->sw;
     a.log = ctx->log;
@@ -881,6 +887,9 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;  // (grid_pull above uses the same count)
     TRY(dalloc(ctx, &ctx->tile_r, (size_t)ctx->ntiles + 1));
     TRY(dalloc(ctx, &ctx->tile_e, (size_t)ctx->ntiles + 1));
+    ctx->nwtiles = (n + nnz + kWItems - 1) / kWItems;
+    TRY(dalloc(ctx, &ctx->wtile_r, (size_t)ctx->nwtiles + 1));
+    TRY(dalloc(ctx, &ctx->wtile_e, (size_t)ctx->nwtiles + 1));
     TRY(dalloc_bytes(ctx, &ctx->c, (size_t)n * cs));
     TRY(dalloc(ctx, &ctx->H, (size_t)n));
     TRY(dalloc_bytes(ctx, &ctx->mt, (size_t)n * cs));
@@ -1037,8 +1046,11 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
         ctx->row_ptr, ctx->col, ctx->w, nnz, ctx->chunk_row, cursor, ctx->t_src, ctx->t_w);
     CKL(ctx);
     const int gt = grid_for(ctx->ntiles + 1, kThreads, ctx->sms * 16);
-    k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, ctx->tile_r,
+    k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, kMpItems, ctx->tile_r,
                                                       ctx->tile_e);
+    const int gw = grid_for(ctx->nwtiles + 1, kThreads, ctx->sms * 16);
+    k_mp_partition<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->nwtiles, kWItems, ctx->wtile_r,
+                                                      ctx->wtile_e);
     CKL(ctx);
     CK(ctx, cudaMemsetAsync(ctx->colsum, 0, (size_t)n * sizeof(double), ctx->stream));
     if (ctx->has_w)
@@ -1965,10 +1977,11 @@ int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision 
     if (n < 1 || nnz < 1) return -1;
     const int64_t cs = prec == RLGL_MIXED ? 4 : 8;
     const int64_t ntiles = (n + nnz + kMpItems - 1) / kMpItems;
+    const int64_t nwtiles = (n + nnz + kWItems - 1) / kWItems;
     int64_t b = 0;
     b += 2 * ((n + 1) * 8 + nnz * 4 + (weighted ? nnz * 4 : 0));  // CSR and CSC
     b += n * (8 + (prec == RLGL_MIXED ? 4 : 0) + cs);                // s, sf, 1/deg
-    b += 2 * (ntiles + 1) * 8;                                       // merge-path tiles
+    b += 2 * (ntiles + 1) * 8 + 2 * (nwtiles + 1) * 8;               // merge-path tiles (block, warp)
     b += n * (cs + 8 + cs + 8 + 8 + 8 + 8 + cs + 8);                 // c H mt y hsrc f_eoff f_base f_m colsum
     b += (nnz / kPushChunk + 2) * 4;                                 // chunk index
     b += (4 * kMaxGrid + 8) * 8 + 8 + (int64_t)kLogCap * (int64_t)sizeof(MoveRecord) +
@@ -2008,7 +2021,7 @@ void rlgl_destroy(rlgl_ctx* ctx) {
         if (ctx->batch_graph) g_retired.push_back(ctx->batch_graph);
     }
     void* dev[] = {ctx->row_ptr, ctx->col, ctx->w, ctx->s, ctx->sf, ctx->ideg, ctx->t_ptr, ctx->t_src, ctx->t_w,
-                   ctx->tile_r, ctx->tile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
+                   ctx->tile_r, ctx->tile_e, ctx->wtile_r, ctx->wtile_e, ctx->c, ctx->H, ctx->mt, ctx->y, ctx->hsrc, ctx->c0,
                    ctx->colsum,
                    ctx->f_eoff, ctx->f_base, ctx->f_m, ctx->chunk_row, ctx->part, ctx->masks,
                    ctx->err, ctx->log, ctx->st, ctx->sw, ctx->node_ptr, ctx->chain_of, ctx->cs,

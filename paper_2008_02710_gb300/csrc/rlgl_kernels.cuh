@@ -1992,13 +1992,13 @@ __global__ void k_scan_add(long long* x, long long m, const long long* tot) {
         if (base + q < m) x[base + q] += off;
 }
 
-// Merge-path split of each tile boundary: for diagonal d = b * kMpItems,
-// the number of rows ended before it (smallest i with t_ptr[i+1] >= d - i).
+// Merge-path split of each tile boundary: for diagonal d = b * items, the
+// number of rows ended before it (smallest i with t_ptr[i+1] >= d - i).
 __global__ void k_mp_partition(const long long* __restrict__ t_ptr, long long n, long long nnz,
-                               long long ntiles, long long* tile_r, long long* tile_e) {
+                               long long ntiles, int items, long long* tile_r, long long* tile_e) {
     for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b <= ntiles;
          b += (long long)gridDim.x * blockDim.x) {
-        long long d = min(b * (long long)kMpItems, n + nnz);
+        long long d = min(b * (long long)items, n + nnz);
         long long lo = max(0ll, d - nnz), hi = min(d, n);
         while (lo < hi) {
             long long mid = (lo + hi) >> 1;

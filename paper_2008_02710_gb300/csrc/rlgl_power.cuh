@@ -10,21 +10,22 @@
 // C_t,j, adds it to H_j, stores C_{t+1},j = the sum and the next move's
 // moved cash per weight m~_j = C_{t+1},j s_j, and sums the statistics of
 // C_{t+1} and of M_t. A move is
-//   pull    : merge-path tiles over the in-links, handed out by a counter,
-//             gathering m~ of the current move. A row that ends in the tile
-//             where it began goes through the epilogue with the tile. A row
-//             whose in-links cross tile boundaries contributes one piece
-//             per tile it spans (added into a zero-at-rest accumulator, then
-//             counted); the piece that arrives last takes the sum and runs
-//             the epilogue. The tiles a row spans follow from its merge
-//             items: its in-links at diagonals t_ptr[j] + j .. t_ptr[j+1] +
-//             j - 1 and its end at t_ptr[j+1] + j.
+//   pull    : merge-path tiles over the in-links, one warp per tile (the
+//             warp's lanes meet only at __syncwarp, never at a block-wide
+//             barrier), gathering m~ of the current move. A row that ends
+//             in the tile where it began goes through the epilogue with the
+//             tile. A row whose in-links cross tile boundaries contributes
+//             one piece per tile it spans (added into a zero-at-rest
+//             accumulator, then counted); the piece that arrives last takes
+//             the sum and runs the epilogue. The tiles a row spans follow
+//             from its merge items: its in-links at diagonals t_ptr[j] + j
+//             .. t_ptr[j+1] + j - 1 and its end at t_ptr[j+1] + j.
 //   barrier ; every block takes the same decisions (stop test of Alg. 1,
 //             re-derivation triggers) from the same totals.
 // Measured on R-MAT 20 and symmetrised R-MAT 22 (all-green to a fixed move
-// count): staging the next tile's source indices in shared memory with
-// cp.async, and gathering through L1, each made the pull slower; the
-// gathers read L2 and the tile loads its indices itself.
+// count, block-wide tiles): staging the next tile's source indices in
+// shared memory with cp.async, and gathering through L1, each made the pull
+// slower; the gathers read L2 and the tile loads its indices itself.
 // The moved cash alternates between two buffers (mt and the residual
 // source hsrc, free while no re-derivation runs). The per-move totals
 // rotate over three slots: the decision of move t reads slot q, move t adds
@@ -32,21 +33,28 @@
 // block 0 at the decision; no block can reach slot q + 2 again before
 // block 0 has arrived at the next barrier.
 // The moves and their floating-point sums are those of the general sweep's
-// all-green moves: m~ = C s rounded to the cash type, in-link sums in the
-// cash type in merge-path order (a split row's pieces added in arrival
-// order), H accumulated in FP64.
+// all-green moves up to the order of the in-link sums: m~ = C s rounded to
+// the cash type, in-link sums in the cash type in merge-path order over warp
+// tiles (a split row's pieces added in arrival order), H accumulated in
+// FP64.
 #pragma once
 
 #include "rlgl_sweep.cuh"
 
 namespace rlgl {
 
-// Shared memory of the power sweep: the merge-path tile and each row's
-// in-link sum (local row index).
+// Merge-path items of a warp tile: 32 lanes, kMpIpt items each.
+constexpr int kWItems = 32 * kMpIpt;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+// Shared memory of one warp of the power sweep: its merge-path tile (the
+// gathered in-link values, the row ends) and each row's in-link sum (local
+// row index).
 template <typename T>
-struct PowSmem {
-    PullSmem<T> pull;
-    T rsum[kMpItems];
+struct PowWarp {
+    T val[kWItems];
+    int end[kWItems + 1];
+    T rsum[kWItems];
 };
 
 // Per-thread sums of a move: ||C_{t+1}||_1, sum C_{t+1}, sum M_t, sum |M_t|
@@ -83,12 +91,12 @@ __device__ __forceinline__ double atomic_take(double* p) {
     return __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull));
 }
 
-// The pieces of a row whose merge items span several tiles: every piece is
-// added into facc[r] where it is found; at the next tile (after the block's
-// barrier) thread 0 or 1 counts it in pcnt[r] behind a fence, so the fence
-// overlaps that tile's gathers instead of holding up the block. The count
-// that completes the row (its merge items span `pieces` tiles) takes the
-// sum, clearing facc[r] and the count, and runs the row's epilogue.
+// The pieces of a row whose merge items span several warp tiles: every
+// piece is added into facc[r] where it is found; at the warp's next tile
+// (after a __syncwarp) lane 0 or 1 counts it in pcnt[r] behind a fence, so
+// that the fence overlaps that tile's gathers. The count that completes the
+// row (its merge items span `pieces` tiles) takes the sum, clearing facc[r]
+// and the count, and runs the row's epilogue.
 struct PowPend {
     long long r;            // the row (-1: none)
     unsigned int pieces;    // the tiles its merge items span
@@ -98,8 +106,8 @@ struct PowPend {
 template <typename T>
 __device__ __forceinline__ void power_count(const SweepArgs<T>& A, PowPend& pp) {
     const long long a = __ldg(A.t_ptr + pp.r) + pp.r, b = __ldg(A.t_ptr + pp.r + 1) + pp.r;
-    __threadfence();  // the block's piece (added before the barrier) before its count
-    pp.pieces = (unsigned int)(b / kMpItems - a / kMpItems + 1);
+    __threadfence();  // the warp's piece (added before its __syncwarp) before its count
+    pp.pieces = (unsigned int)(b / kWItems - a / kWItems + 1);
     pp.seen = atomicAdd(A.pcnt + pp.r, 1u) + 1u;  // (its value is first used at power_finish)
 }
 
@@ -130,115 +138,112 @@ __device__ __forceinline__ TileB tile_bounds(const long long* __restrict__ tile_
     return t;
 }
 
-// One move's pull with the row epilogue; tiles handed out by `next`.
+// Segmented inclusive scan over the lanes of a warp: the running sum of val
+// restarts wherever key changes (keys >= 0 form contiguous runs).
+template <typename T>
+__device__ __forceinline__ T warp_segscan(long long key, T val) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, val, o);
+        const long long ky = __shfl_up_sync(0xffffffffu, key, o);
+        if (lane >= o && ky == key) val += y;
+    }
+    return val;
+}
+
+// One move's pull with the row epilogue, a warp per merge-path tile of
+// kWItems items: the warps of the grid take the tiles w, w + W, w + 2W, ...
+// for all but the last two rounds, and the rest one at a time from the
+// counter `next` (lane 0 asks for the next one while the warp works on the
+// current one), so that warps end within about one tile of one another. No
+// block-wide barrier: a warp's lanes meet only at __syncwarp.
 template <typename T, bool kHasW>
 __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __restrict__ mt_cur,
-                                            T* __restrict__ mt_next, PowSmem<T>& sm,
+                                            T* __restrict__ mt_next, PowWarp<T>& ws,
                                             unsigned long long* next, PowAcc<T>& acc) {
-    PullSmem<T>& ps = sm.pull;
-    __shared__ long long s_b[2];
-    __shared__ TileB s_t[2];
-    __shared__ long long s_pend[2];  // the last tile's pieces: its first row's, its carry-out's
-    if (threadIdx.x < 2) s_pend[threadIdx.x] = -1;
-    const long long ntiles = A.ntiles;
+    const int lane = threadIdx.x & 31;
+    const long long ntiles = A.nwtiles;
+    const long long nw = (long long)gridDim.x * kWarpsPerBlock;
+    const long long w = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const long long rounds = ntiles / nw > 2 ? ntiles / nw - 2 : 0;  // tiles taken in turn
+    const long long dyn0 = rounds * nw;                              // the first handed-out tile
     const T* __restrict__ scale = row_scale(A.sf, A.s, T(0));
-    // the first tile and the one after it
-    if (threadIdx.x == 0) {
-        const long long b0 = (long long)atomicAdd(next, 1ull);
-        s_b[0] = b0;
-        if (b0 < ntiles) s_t[0] = tile_bounds(A.tile_r, A.tile_e, b0);
-        s_b[1] = (long long)atomicAdd(next, 1ull);
-    }
-    __syncthreads();
-    int cs = 0;  // the current tile's entry in s_b / s_t
-    for (;;) {
-        const long long b = s_b[cs];
+    PowPend pp{-1, 0u, 0u};  // lanes 0 and 1: a piece of the warp's last tile
+    unsigned long long grab = 0;
+    if (rounds == 0 && lane == 0) grab = atomicAdd(next, 1ull);
+    for (long long s = 0;; ++s) {
+        const long long b = s < rounds ? w + s * nw : dyn0 + (long long)__shfl_sync(0xffffffffu, grab, 0);
         if (b >= ntiles) break;
-        const TileB t = s_t[cs];
-        // thread 0: the next tile's bounds and the grab after it, in flight
-        // while the block gathers this tile
-        const long long bn = s_b[cs ^ 1];
-        long long bnn = 0;
-        TileB tn{0, 0, 0, 0};
-        if (threadIdx.x == 0) {
-            if (bn < ntiles) {
-                tn = tile_bounds(A.tile_r, A.tile_e, bn);
-                bnn = (long long)atomicAdd(next, 1ull);
-            } else {
-                bnn = ntiles;
-            }
-        }
-        __syncthreads();  // the last tile's pieces are known
-        PowPend pp{-1, 0u, 0u};
-        if (threadIdx.x < 2) pp.r = s_pend[threadIdx.x];
+        if (s + 1 >= rounds && lane == 0) grab = atomicAdd(next, 1ull);  // the next tile, in flight
+        const TileB t = tile_bounds(A.wtile_r, A.wtile_e, b);
         T oldv = T(0), scv = T(0);
+        int start0;
         {
             int sidx[kMpIpt];
-            long long re[kMpIpt];
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) {
-                const int k = threadIdx.x + q * kThreads;
+                const int k = lane + q * 32;
                 sidx[q] = (k < t.ne) ? __ldg(A.t_src + t.e0 + k) : -1;
                 // the weights are read at the store below; their lines are
                 // fetched now (no register holds them across the gathers)
                 if (kHasW && k < t.ne) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.t_w + t.e0 + k));
-                re[q] = (k < t.nr) ? __ldg(A.t_ptr + t.r0 + 1 + k) : 0;
             }
-            // the epilogue's first row of this thread, read with the gathers
-            if ((int)threadIdx.x < t.nr) {
-                oldv = __ldcg(A.c + t.r0 + threadIdx.x);
-                scv = __ldg(scale + t.r0 + threadIdx.x);
+            int re[kMpIpt];
+#pragma unroll
+            for (int q = 0; q < kMpIpt; ++q) {
+                const int k = lane + q * 32;
+                re[q] = (k < t.nr) ? (int)(__ldg(A.t_ptr + t.r0 + 1 + k) - t.e0) : 0;
             }
-            // m~ of this move was written by other blocks one move ago: L2
+            start0 = (int)(__ldg(A.t_ptr + t.r0) - t.e0);
+            // the epilogue's first row of this lane, read with the gathers
+            if (lane < t.nr) {
+                oldv = __ldcg(A.c + t.r0 + lane);
+                scv = __ldg(scale + t.r0 + lane);
+            }
+            // m~ of this move was written by other warps one move ago: L2
             T v[kMpIpt];
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? __ldcg(mt_cur + sidx[q]) : T(0);
             if (pp.r >= 0) power_count<T>(A, pp);
 #pragma unroll
             for (int q = 0; q < kMpIpt; ++q) {
-                const int k = threadIdx.x + q * kThreads;
-                if (k < t.ne) ps.val[k] = kHasW ? v[q] * (T)__ldg(A.t_w + t.e0 + k) : v[q];
-                if (k < t.nr) ps.end[k] = (int)(re[q] - t.e0);
+                const int k = lane + q * 32;
+                if (k < t.ne) ws.val[k] = kHasW ? v[q] * (T)__ldg(A.t_w + t.e0 + k) : v[q];
+                if (k < t.nr) ws.end[k] = re[q];
             }
         }
-        if (threadIdx.x == 0) {
-            ps.end[t.nr] = 0x7fffffff;
-            ps.start0 = (int)(__ldg(A.t_ptr + t.r0) - t.e0);
-            s_t[cs ^ 1] = tn;
-            s_b[cs] = bnn;  // the entry after next
-        }
-        __syncthreads();  // the next tile's bounds are known
-        if (threadIdx.x < 2) s_pend[threadIdx.x] = -1;
+        if (lane == 0) ws.end[t.nr] = 0x7fffffff;
+        __syncwarp();
         const int total = t.nr + t.ne;
-        int d = threadIdx.x * kMpIpt;
-        const bool active = d < total;
+        int d = lane * kMpIpt;
         long long rowA = -1, rowB = -1;
         T accA = T(0), accB = T(0);
-        if (active) {
+        if (d < total) {
             const int dend = min(d + kMpIpt, total);
             int lo = max(0, d - t.ne), hi = min(d, t.nr);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
-                if (ps.end[mid] >= d - mid) hi = mid; else lo = mid + 1;
+                if (ws.end[mid] >= d - mid) hi = mid; else lo = mid + 1;
             }
             int i = lo, j = d - lo;
-            const int row_start = (i == 0) ? ps.start0 : ps.end[i - 1];
-            bool whole = (j == row_start);  // no in-link of row i before this thread
-            T s = T(0);
+            const int row_start = (i == 0) ? start0 : ws.end[i - 1];
+            bool whole = (j == row_start);  // no in-link of row i before this lane
+            T sum = T(0);
             int cnt = 0;
             for (; d < dend; ++d) {
-                if (j < ps.end[i]) {
-                    s += ps.val[j];
+                if (j < ws.end[i]) {
+                    sum += ws.val[j];
                     ++j;
                     ++cnt;
                 } else {
                     if (!whole) {
                         rowA = t.r0 + i;
-                        accA = s;
+                        accA = sum;
                     } else {
-                        sm.rsum[i] = s;  // a row with no in-link sums to zero
+                        ws.rsum[i] = sum;  // a row with no in-link sums to zero
                     }
-                    s = T(0);
+                    sum = T(0);
                     cnt = 0;
                     ++i;
                     whole = true;
@@ -246,43 +251,43 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
             }
             if (cnt > 0 || !whole) {
                 rowB = t.r0 + i;
-                accB = s;
+                accB = sum;
             }
         }
-        const T run = block_segscan<T>(rowB, accB, ps.ckey, ps.cval);
-        const bool first_split = ps.start0 < 0;  // the tile's first row began in an earlier tile
+        const T run = warp_segscan<T>(rowB, accB);
+        const long long pkey = __shfl_up_sync(0xffffffffu, rowB, 1);
+        const T pval = __shfl_up_sync(0xffffffffu, run, 1);
+        const bool first_split = start0 < 0;  // the tile's first row began in an earlier tile
         if (rowA >= 0) {
             T sum = accA;
-            if (threadIdx.x > 0 && ps.ckey[threadIdx.x - 1] == rowA) sum += ps.cval[threadIdx.x - 1];
-            if (rowA == t.r0 && first_split) {
-                atomicAdd(A.facc + rowA, sum);
-                s_pend[0] = rowA;  // counted at the next tile
-            } else {
-                sm.rsum[rowA - t.r0] = sum;
-            }
+            if (lane > 0 && pkey == rowA) sum += pval;
+            if (rowA == t.r0 && first_split)
+                atomicAdd(A.facc + rowA, sum);  // counted at the next tile
+            else
+                ws.rsum[rowA - t.r0] = sum;
         }
         const int last = (total - 1) / kMpIpt;
-        if ((int)threadIdx.x == last && rowB >= 0) {
-            atomicAdd(A.facc + rowB, run);
-            s_pend[1] = rowB;
-        }
-        __syncthreads();
+        if (lane == last && rowB >= 0) atomicAdd(A.facc + rowB, run);
+        const long long tail = __shfl_sync(0xffffffffu, rowB, last);  // the row left open (or -1)
+        __syncwarp();
         // the rows that end in this tile and began in it
-        {
-            int k = (first_split ? 1 : 0) + (int)threadIdx.x;
-            if (k < t.nr && k == (int)threadIdx.x) {
-                power_row_with<T>(A, mt_next, t.r0 + k, sm.rsum[k], oldv, scv, acc);
-                k += blockDim.x;
-            }
-            for (; k < t.nr; k += blockDim.x) power_row<T>(A, mt_next, t.r0 + k, sm.rsum[k], acc);
+        for (int k = lane; k < t.nr; k += 32) {
+            if (k == 0 && first_split) continue;
+            if (k == lane)
+                power_row_with<T>(A, mt_next, t.r0 + k, ws.rsum[k], oldv, scv, acc);
+            else
+                power_row<T>(A, mt_next, t.r0 + k, ws.rsum[k], acc);
         }
         if (pp.r >= 0) power_finish<T>(A, mt_next, pp, acc);
-        cs ^= 1;
-        __syncthreads();  // the tile's shared memory is rewritten next
+        // this tile's pieces: its first row (begun earlier, ended here) and
+        // the row it leaves open
+        pp.r = -1;
+        if (lane == 0 && first_split && t.nr > 0) pp.r = t.r0;
+        if (lane == 1) pp.r = tail;
+        __syncwarp();  // the warp's shared memory is rewritten next
     }
-    // the last tile's pieces (the loop ended on a barrier)
-    if (threadIdx.x < 2 && s_pend[threadIdx.x] >= 0) {
-        PowPend pp{s_pend[threadIdx.x], 0u, 0u};
+    // the last tile's pieces
+    if (pp.r >= 0) {
         power_count<T>(A, pp);
         power_finish<T>(A, mt_next, pp, acc);
     }
@@ -314,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         if (A.use_cond && lead) cudaGraphSetConditional(A.cond_loop, 0u);
         return;
     }
-    __shared__ PowSmem<T> sm;
+    __shared__ PowWarp<T> sm[kWarpsPerBlock];
     __shared__ T tscratch[4 * 32];
     __shared__ SweepCtl sc;
     __shared__ Control ctl;
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         // ----------------------------------------------------------- move
         SweepSlot* nsl = &sw->slot[rot3(sc.p)];  // this move's sums and tile counter
         if (lead) sc.ts[0] = globaltimer();
-        power_tiles<T, kHasW>(A, mt_cur, mt_nxt, sm, &nsl->chunk_next, acc);
+        power_tiles<T, kHasW>(A, mt_cur, mt_nxt, sm[threadIdx.x >> 5], &nsl->chunk_next, acc);
         power_publish<T>(acc, nsl, tscratch);
         if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr))
             break;

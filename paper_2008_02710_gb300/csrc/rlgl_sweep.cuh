@@ -191,6 +191,9 @@ struct SweepArgs {
     const long long* tile_r;
     const long long* tile_e;
     long long ntiles;
+    const long long* wtile_r;  // power sweep: merge-path tiles of a warp
+    const long long* wtile_e;
+    long long nwtiles;
     DevState* st;
     SweepState* sw;
     MoveRecord* log;
