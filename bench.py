@@ -616,7 +616,16 @@ def build_probe(force: bool = False) -> str:
     return PROBE_LIB
 
 
-def random_access_peaks(n_words, m=1 << 22):
+PROBE_M = 1 << 26      # random accesses per probe launch (steady state)
+PROBE_GRID = 32 * 152  # blocks of 256 threads
+
+
+def probe_desc(n_words):
+    return (f"{PROBE_M >> 20}M random 4-byte accesses into {n_words} words, {PROBE_GRID} blocks, "
+            "8 independent accesses per thread and pass; best of 5")
+
+
+def random_access_peaks(n_words, m=PROBE_M):
     """Scatter (red.global.add.f32) and gather rates, G ops/s, of m random
     4-byte accesses into n_words words on this GPU: the ceiling of the push
     and the pull when the cash sits in L2."""
@@ -624,8 +633,7 @@ def random_access_peaks(n_words, m=1 << 22):
     lib = ctypes.CDLL(build_probe())
     lib.l2_probe_rate.restype = ctypes.c_double
     lib.l2_probe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
-    grid = 8 * 152
-    return lib.l2_probe_rate(0, n_words, m, grid, 5), lib.l2_probe_rate(1, n_words, m, grid, 5)
+    return lib.l2_probe_rate(0, n_words, m, PROBE_GRID, 5), lib.l2_probe_rate(1, n_words, m, PROBE_GRID, 5)
 
 
 def measured_peaks():
@@ -963,7 +971,7 @@ def run_gpu(args):
         "reference": ref_info,
         "roofline": roof,
         "random_access": {"scatter_peak_gops": scat_peak, "gather_peak_gops": gath_peak,
-                          "probe": f"4M random 4-byte accesses into {csr.n} words, 1216 blocks",
+                          "probe": probe_desc(csr.n),
                           "push_phase_gops": push_rate if sweep_on else None,
                           "push_frac_of_scatter_peak": (push_rate / scat_peak) if (sweep_on and push_rate and scat_peak > 0) else None},
         "phase_kernel_ms": {k: v[0] for k, v in kt.items() if k != "sweep"},
@@ -1106,7 +1114,7 @@ def run_batch(args):
     # costs one scattered gather, a pushed link one scattered add
     scat, gath = random_access_peaks(1 << 20)
     out["random_access"] = {"scatter_peak_gops": scat, "gather_peak_gops": gath,
-                            "probe": "4M random 4-byte accesses into 1048576 words"}
+                            "probe": probe_desc(1 << 20)}
     for sched, rate, how in (("link_threshold", scat, "every link pushed at the scattered-add rate"),
                              ("all_green", gath, "every link pulled at the scattered-gather rate")):
         if "ms" in out.get(sched, {}):

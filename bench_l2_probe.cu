@@ -4,7 +4,10 @@
 // reductions (push) or loads (pull) the memory system completes per second.
 // These two kernels do nothing else: m updates or loads at pseudo-random
 // indices of an n-word array (indices from a xorshift sequence, all in
-// range), grid-stride, 256 threads per block.
+// range), grid-stride, 256 threads per block, each thread issuing eight
+// independent accesses per pass. m must be large enough for the rate to be
+// the steady state: with 4 M accesses (about 20 us) the launch's ramp and
+// tail took a quarter of the time (210 G gathers/s against 290 G/s at 64 M).
 //
 // Built by bench.py into libbench_l2_probe.so beside it: measurement only,
 // not part of the RLGL library.
@@ -14,18 +17,38 @@
 
 namespace {
 
+constexpr int kU = 8;  // independent accesses per thread and pass
+
 __global__ void probe_scatter(float* __restrict__ c, const int* __restrict__ idx, long long m) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
-         k += (long long)gridDim.x * blockDim.x)
-        asm volatile("red.global.add.f32 [%0], %1;" ::"l"(c + idx[k]), "f"(1.0f) : "memory");
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; k + (kU - 1) * stride < m; k += kU * stride) {
+        int j[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) j[u] = __ldcs(idx + k + u * stride);
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            asm volatile("red.global.add.f32 [%0], %1;" ::"l"(c + j[u]), "f"(1.0f) : "memory");
+    }
+    for (; k < m; k += stride) asm volatile("red.global.add.f32 [%0], %1;" ::"l"(c + idx[k]), "f"(1.0f) : "memory");
 }
 
 __global__ void probe_gather(const float* __restrict__ c, const int* __restrict__ idx, long long m,
                              float* __restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float s = 0.f;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
-         k += (long long)gridDim.x * blockDim.x)
-        s += __ldcg(c + idx[k]);
+    for (; k + (kU - 1) * stride < m; k += kU * stride) {
+        int j[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) j[u] = __ldcs(idx + k + u * stride);
+        float v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) v[u] = __ldcg(c + j[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) s += v[u];
+    }
+    for (; k < m; k += stride) s += __ldcg(c + idx[k]);
     if (s == -1.f) out[0] = s;  // keeps the loads
 }
 

@@ -438,7 +438,6 @@ static SweepArgs<T> sweep_args(rlgl_ctx* ctx, const Conds& cd) {
     a.mt = (T*)ctx->mt;
     a.mt2 = (T*)ctx->hsrc;  // free while no re-derivation runs
     a.facc = (T*)ctx->f_m;  // the power sweep clears it at every launch
-    a.pcnt = reinterpret_cast<unsigned int*>(ctx->f_eoff);  // likewise (n counters fit in f_eoff)
     a.f_eoff = ctx->f_eoff;
     a.f_base = ctx->f_base;
     a.f_m = (T*)ctx->f_m;
@@ -887,7 +886,8 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     ctx->ntiles = (n + nnz + kMpItems - 1) / kMpItems;  // (grid_pull above uses the same count)
     TRY(dalloc(ctx, &ctx->tile_r, (size_t)ctx->ntiles + 1));
     TRY(dalloc(ctx, &ctx->tile_e, (size_t)ctx->ntiles + 1));
-    ctx->nwtiles = (n + nnz + kWItems - 1) / kWItems;
+    const long long witems = 32 * power_ipt((int)cs);
+    ctx->nwtiles = (n + nnz + witems - 1) / witems;
     TRY(dalloc(ctx, &ctx->wtile_r, (size_t)ctx->nwtiles + 1));
     TRY(dalloc(ctx, &ctx->wtile_e, (size_t)ctx->nwtiles + 1));
     TRY(dalloc_bytes(ctx, &ctx->c, (size_t)n * cs));
@@ -1049,7 +1049,8 @@ static rlgl_status create_common(int64_t n, int64_t nnz, const int64_t* row_ptr,
     k_mp_partition<<<gt, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->ntiles, kMpItems, ctx->tile_r,
                                                       ctx->tile_e);
     const int gw = grid_for(ctx->nwtiles + 1, kThreads, ctx->sms * 16);
-    k_mp_partition<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->nwtiles, kWItems, ctx->wtile_r,
+    k_mp_partition<<<gw, kThreads, 0, ctx->stream>>>(ctx->t_ptr, n, nnz, ctx->nwtiles,
+                                                      32 * power_ipt((int)cash_size(ctx)), ctx->wtile_r,
                                                       ctx->wtile_e);
     CKL(ctx);
     CK(ctx, cudaMemsetAsync(ctx->colsum, 0, (size_t)n * sizeof(double), ctx->stream));
@@ -1977,7 +1978,8 @@ int64_t rlgl_footprint(int64_t n, int64_t nnz, int32_t weighted, rlgl_precision 
     if (n < 1 || nnz < 1) return -1;
     const int64_t cs = prec == RLGL_MIXED ? 4 : 8;
     const int64_t ntiles = (n + nnz + kMpItems - 1) / kMpItems;
-    const int64_t nwtiles = (n + nnz + kWItems - 1) / kWItems;
+    const int64_t witems = 32 * power_ipt((int)cs);
+    const int64_t nwtiles = (n + nnz + witems - 1) / witems;
     int64_t b = 0;
     b += 2 * ((n + 1) * 8 + nnz * 4 + (weighted ? nnz * 4 : 0));  // CSR and CSC
     b += n * (8 + (prec == RLGL_MIXED ? 4 : 0) + cs);                // s, sf, 1/deg

@@ -1,6 +1,6 @@
 // The persistent all-green sweep (power iteration, Sec. 2.3.1): the moves
 // of a single-chain all-green solve in one cooperative kernel, one pass over
-// the in-links and one grid barrier a move.
+// the in-links and two grid barriers a move.
 //
 // With G_t = [N] a move is M_t = C_t, H <- H + C_t, C_{t+1} = M_t P (Eqs.
 // recursion_M, recursion_H, recursion_C; every node's cash leaves it). The
@@ -12,20 +12,27 @@
 // C_{t+1} and of M_t. A move is
 //   pull    : merge-path tiles over the in-links, one warp per tile (the
 //             warp's lanes meet only at __syncwarp, never at a block-wide
-//             barrier), gathering m~ of the current move. A row that ends
-//             in the tile where it began goes through the epilogue with the
-//             tile. A row whose in-links cross tile boundaries contributes
-//             one piece per tile it spans (added into a zero-at-rest
-//             accumulator, then counted); the piece that arrives last takes
-//             the sum and runs the epilogue. The tiles a row spans follow
-//             from its merge items: its in-links at diagonals t_ptr[j] + j
-//             .. t_ptr[j+1] + j - 1 and its end at t_ptr[j+1] + j.
+//             barrier), gathering m~ of the current move; the next tile's
+//             bounds and in-link sources are loaded while the warp works on
+//             the current one. A row that ends in the tile where it began
+//             goes through the epilogue with the tile. A row whose in-links
+//             cross tile boundaries adds one piece per tile it spans into a
+//             zero-at-rest accumulator.
+//   barrier
+//   split   : each row that crossed a tile boundary (one per tile whose
+//             first row ends in it but began in an earlier tile) takes its
+//             sum from the accumulator and goes through the epilogue.
 //   barrier ; every block takes the same decisions (stop test of Alg. 1,
 //             re-derivation triggers) from the same totals.
 // Measured on R-MAT 20 and symmetrised R-MAT 22 (all-green to a fixed move
-// count, block-wide tiles): staging the next tile's source indices in
-// shared memory with cp.async, and gathering through L1, each made the pull
-// slower; the gathers read L2 and the tile loads its indices itself.
+// count; 8.60 ms and 91.9 ms with the pieces counted as they arrived and the
+// row finished by its last piece, within the pull, one fence per piece):
+// finishing the split rows after a barrier instead, 7.40 / 79.6 ms; loading
+// the next tile's bounds and sources ahead, at three blocks an SM (the
+// registers it needs), 7.03 / 77.5 ms; warp tiles of 384 rather than 256
+// items (FP32), 6.99 / 72.7 ms. Gathering m~ into shared memory with
+// cp.async (two tiles ahead, the warp's operands staged in dynamic shared
+// memory) was slower than loading it: 10.9 ms on R-MAT 20.
 // The moved cash alternates between two buffers (mt and the residual
 // source hsrc, free while no re-derivation runs). The per-move totals
 // rotate over three slots: the decision of move t reads slot q, move t adds
@@ -43,18 +50,23 @@
 
 namespace rlgl {
 
-// Merge-path items of a warp tile: 32 lanes, kMpIpt items each.
-constexpr int kWItems = 32 * kMpIpt;
 constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kPowerMinBlocks = 3;  // blocks per SM (launch bounds: up to 85 registers a thread)
+
+// Merge-path items per lane of a warp tile: 12 for FP32 cash (384-item
+// tiles), 8 for FP64 (256-item tiles, so that a block's static shared
+// memory stays within 48 KB).
+__host__ __device__ constexpr int power_ipt(int cash_bytes) { return cash_bytes == 4 ? 12 : 8; }
 
 // Shared memory of one warp of the power sweep: its merge-path tile (the
 // gathered in-link values, the row ends) and each row's in-link sum (local
 // row index).
 template <typename T>
 struct PowWarp {
-    T val[kWItems];
-    int end[kWItems + 1];
-    T rsum[kWItems];
+    static constexpr int kItems = 32 * power_ipt((int)sizeof(T));
+    T val[kItems];
+    int end[kItems + 1];
+    T rsum[kItems];
 };
 
 // Per-thread sums of a move: ||C_{t+1}||_1, sum C_{t+1}, sum M_t, sum |M_t|
@@ -84,42 +96,6 @@ __device__ __forceinline__ void power_row(const SweepArgs<T>& A, T* __restrict__
     const T old = __ldcg(A.c + r);  // C_t,r (this kernel stored it one move ago)
     const T sc = __ldg(row_scale(A.sf, A.s, T(0)) + r);
     power_row_with<T>(A, mt_next, r, v, old, sc, acc);
-}
-
-__device__ __forceinline__ float atomic_take(float* p) { return atomicExch(p, 0.0f); }
-__device__ __forceinline__ double atomic_take(double* p) {
-    return __longlong_as_double((long long)atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull));
-}
-
-// The pieces of a row whose merge items span several warp tiles: every
-// piece is added into facc[r] where it is found; at the warp's next tile
-// (after a __syncwarp) lane 0 or 1 counts it in pcnt[r] behind a fence, so
-// that the fence overlaps that tile's gathers. The count that completes the
-// row (its merge items span `pieces` tiles) takes the sum, clearing facc[r]
-// and the count, and runs the row's epilogue.
-struct PowPend {
-    long long r;            // the row (-1: none)
-    unsigned int pieces;    // the tiles its merge items span
-    unsigned int seen;      // the count after this piece
-};
-
-template <typename T>
-__device__ __forceinline__ void power_count(const SweepArgs<T>& A, PowPend& pp) {
-    const long long a = __ldg(A.t_ptr + pp.r) + pp.r, b = __ldg(A.t_ptr + pp.r + 1) + pp.r;
-    __threadfence();  // the warp's piece (added before its __syncwarp) before its count
-    pp.pieces = (unsigned int)(b / kWItems - a / kWItems + 1);
-    pp.seen = atomicAdd(A.pcnt + pp.r, 1u) + 1u;  // (its value is first used at power_finish)
-}
-
-template <typename T>
-__device__ __forceinline__ void power_finish(const SweepArgs<T>& A, T* __restrict__ mt_next, const PowPend& pp,
-                                             PowAcc<T>& acc) {
-    if (pp.seen == pp.pieces) {
-        __threadfence();  // every counted piece is in facc
-        const T v = atomic_take(A.facc + pp.r);
-        A.pcnt[pp.r] = 0u;
-        power_row<T>(A, mt_next, pp.r, v, acc);
-    }
 }
 
 // Bounds of tile b: first row, first in-link, rows ending in it, in-links.
@@ -152,16 +128,18 @@ __device__ __forceinline__ T warp_segscan(long long key, T val) {
     return val;
 }
 
-// One move's pull with the row epilogue, a warp per merge-path tile of
-// kWItems items: the warps of the grid take the tiles w, w + W, w + 2W, ...
-// for all but the last two rounds, and the rest one at a time from the
-// counter `next` (lane 0 asks for the next one while the warp works on the
-// current one), so that warps end within about one tile of one another. No
-// block-wide barrier: a warp's lanes meet only at __syncwarp.
+// One move's pull with the row epilogue, a warp per merge-path tile: the
+// warps of the grid take the tiles w, w + W, w + 2W, ... for all but the
+// last two rounds, and the rest one at a time from the counter `next` (lane
+// 0 asks one turn ahead), so that warps end within about one tile of one
+// another. While a warp sums a tile, the next tile's bounds and in-link
+// sources are in flight. No block-wide barrier: a warp's lanes meet only at
+// __syncwarp. The pieces of rows that cross tile boundaries go into facc.
 template <typename T, bool kHasW>
 __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __restrict__ mt_cur,
                                             T* __restrict__ mt_next, PowWarp<T>& ws,
                                             unsigned long long* next, PowAcc<T>& acc) {
+    constexpr int kPowIpt = power_ipt((int)sizeof(T));
     const int lane = threadIdx.x & 31;
     const long long ntiles = A.nwtiles;
     const long long nw = (long long)gridDim.x * kWarpsPerBlock;
@@ -169,29 +147,47 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
     const long long rounds = ntiles / nw > 2 ? ntiles / nw - 2 : 0;  // tiles taken in turn
     const long long dyn0 = rounds * nw;                              // the first handed-out tile
     const T* __restrict__ scale = row_scale(A.sf, A.s, T(0));
-    PowPend pp{-1, 0u, 0u};  // lanes 0 and 1: a piece of the warp's last tile
-    unsigned long long grab = 0;
-    if (rounds == 0 && lane == 0) grab = atomicAdd(next, 1ull);
-    for (long long s = 0;; ++s) {
-        const long long b = s < rounds ? w + s * nw : dyn0 + (long long)__shfl_sync(0xffffffffu, grab, 0);
-        if (b >= ntiles) break;
-        if (s + 1 >= rounds && lane == 0) grab = atomicAdd(next, 1ull);  // the next tile, in flight
-        const TileB t = tile_bounds(A.wtile_r, A.wtile_e, b);
+    unsigned long long grab = 0, g0 = 0;
+    if (lane == 0) {
+        if (rounds < 1) g0 = atomicAdd(next, 1ull);
+        if (rounds < 2) grab = atomicAdd(next, 1ull);  // turn 1
+    }
+    long long b = rounds > 0 ? w : dyn0 + (long long)__shfl_sync(0xffffffffu, g0, 0);
+    TileB t{0, 0, 0, 0};
+    int sidx[kPowIpt];
+    if (b < ntiles) t = tile_bounds(A.wtile_r, A.wtile_e, b);
+#pragma unroll
+    for (int q = 0; q < kPowIpt; ++q) {
+        const int k = lane + q * 32;
+        sidx[q] = (b < ntiles && k < t.ne) ? __ldg(A.t_src + t.e0 + k) : -1;
+    }
+    for (long long s = 0; b < ntiles; ++s) {
         T oldv = T(0), scv = T(0);
         int start0;
+        TileB tn{0, 0, 0, 0};
+        long long bn;
         {
-            int sidx[kMpIpt];
+            // m~ of this move was written by other warps one move ago: L2
+            T v[kPowIpt];
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) {
+            for (int q = 0; q < kPowIpt; ++q) v[q] = (sidx[q] >= 0) ? __ldcg(mt_cur + sidx[q]) : T(0);
+#pragma unroll
+            for (int q = 0; q < kPowIpt; ++q) {
                 const int k = lane + q * 32;
-                sidx[q] = (k < t.ne) ? __ldg(A.t_src + t.e0 + k) : -1;
-                // the weights are read at the store below; their lines are
-                // fetched now (no register holds them across the gathers)
                 if (kHasW && k < t.ne) asm volatile("prefetch.global.L1 [%0];" ::"l"(A.t_w + t.e0 + k));
             }
-            int re[kMpIpt];
+            // the next tile's bounds and sources, in flight over this tile
+            bn = s + 1 < rounds ? w + (s + 1) * nw : dyn0 + (long long)__shfl_sync(0xffffffffu, grab, 0);
+            if (bn < ntiles && s + 2 >= rounds && lane == 0) grab = atomicAdd(next, 1ull);
+            if (bn < ntiles) tn = tile_bounds(A.wtile_r, A.wtile_e, bn);
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) {
+            for (int q = 0; q < kPowIpt; ++q) {
+                const int k = lane + q * 32;
+                sidx[q] = (bn < ntiles && k < tn.ne) ? __ldg(A.t_src + tn.e0 + k) : -1;
+            }
+            int re[kPowIpt];
+#pragma unroll
+            for (int q = 0; q < kPowIpt; ++q) {
                 const int k = lane + q * 32;
                 re[q] = (k < t.nr) ? (int)(__ldg(A.t_ptr + t.r0 + 1 + k) - t.e0) : 0;
             }
@@ -201,13 +197,8 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
                 oldv = __ldcg(A.c + t.r0 + lane);
                 scv = __ldg(scale + t.r0 + lane);
             }
-            // m~ of this move was written by other warps one move ago: L2
-            T v[kMpIpt];
 #pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) v[q] = (sidx[q] >= 0) ? __ldcg(mt_cur + sidx[q]) : T(0);
-            if (pp.r >= 0) power_count<T>(A, pp);
-#pragma unroll
-            for (int q = 0; q < kMpIpt; ++q) {
+            for (int q = 0; q < kPowIpt; ++q) {
                 const int k = lane + q * 32;
                 if (k < t.ne) ws.val[k] = kHasW ? v[q] * (T)__ldg(A.t_w + t.e0 + k) : v[q];
                 if (k < t.nr) ws.end[k] = re[q];
@@ -216,11 +207,11 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
         if (lane == 0) ws.end[t.nr] = 0x7fffffff;
         __syncwarp();
         const int total = t.nr + t.ne;
-        int d = lane * kMpIpt;
+        int d = lane * kPowIpt;
         long long rowA = -1, rowB = -1;
         T accA = T(0), accB = T(0);
         if (d < total) {
-            const int dend = min(d + kMpIpt, total);
+            const int dend = min(d + kPowIpt, total);
             int lo = max(0, d - t.ne), hi = min(d, t.nr);
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
@@ -266,9 +257,8 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
             else
                 ws.rsum[rowA - t.r0] = sum;
         }
-        const int last = (total - 1) / kMpIpt;
+        const int last = (total - 1) / kPowIpt;
         if (lane == last && rowB >= 0) atomicAdd(A.facc + rowB, run);
-        const long long tail = __shfl_sync(0xffffffffu, rowB, last);  // the row left open (or -1)
         __syncwarp();
         // the rows that end in this tile and began in it
         for (int k = lane; k < t.nr; k += 32) {
@@ -278,18 +268,24 @@ __device__ __forceinline__ void power_tiles(const SweepArgs<T>& A, const T* __re
             else
                 power_row<T>(A, mt_next, t.r0 + k, ws.rsum[k], acc);
         }
-        if (pp.r >= 0) power_finish<T>(A, mt_next, pp, acc);
-        // this tile's pieces: its first row (begun earlier, ended here) and
-        // the row it leaves open
-        pp.r = -1;
-        if (lane == 0 && first_split && t.nr > 0) pp.r = t.r0;
-        if (lane == 1) pp.r = tail;
         __syncwarp();  // the warp's shared memory is rewritten next
+        b = bn;
+        t = tn;
     }
-    // the last tile's pieces
-    if (pp.r >= 0) {
-        power_count<T>(A, pp);
-        power_finish<T>(A, mt_next, pp, acc);
+}
+
+// The rows whose in-links cross warp tiles, once every piece is in facc
+// (after the move's first grid barrier): the row that ends in tile b began
+// in an earlier tile when t_ptr[r0] < e0. Each such row ends in one tile.
+template <typename T>
+__device__ __forceinline__ void power_split_rows(const SweepArgs<T>& A, T* __restrict__ mt_next, PowAcc<T>& acc) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < A.nwtiles;
+         b += (long long)gridDim.x * blockDim.x) {
+        const long long r0 = __ldg(A.wtile_r + b);
+        if (__ldg(A.wtile_r + b + 1) == r0 || __ldg(A.t_ptr + r0) >= __ldg(A.wtile_e + b)) continue;
+        const T v = __ldcg(A.facc + r0);
+        A.facc[r0] = T(0);
+        power_row<T>(A, mt_next, r0, v, acc);
     }
 }
 
@@ -311,7 +307,7 @@ __device__ __forceinline__ void power_publish(PowAcc<T>& acc, SweepSlot* sl, T* 
 __device__ __forceinline__ int rot3(int q) { return q == 2 ? 0 : q + 1; }
 
 template <typename T, bool kHasW>
-__global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T> A) {
+__global__ void __launch_bounds__(kThreads, kPowerMinBlocks) k_power(SweepArgs<T> A) {
     DevState* st = A.st;
     SweepState* sw = A.sw;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -359,8 +355,8 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
     PowAcc<T> acc{T(0), T(0), T(0), T(0)};
 
     // ------------------------------------------------------- prologue
-    // m~ = C s for the first move, the split rows' accumulators and counts
-    // cleared, and the statistics of the cash for the first stop test.
+    // m~ = C s for the first move, the split rows' accumulators cleared, and
+    // the statistics of the cash for the first stop test.
     {
         const T* scale = row_scale(A.sf, A.s, T(0));
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -368,7 +364,6 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
             const T v = A.c[i];
             A.mt[i] = v * __ldg(scale + i);
             A.facc[i] = T(0);
-            A.pcnt[i] = 0u;
             acc.a += fabs(v);
             acc.s += v;
         }
@@ -496,14 +491,18 @@ __global__ void __launch_bounds__(kThreads, kSweepMinBlocks) k_power(SweepArgs<T
         SweepSlot* nsl = &sw->slot[rot3(sc.p)];  // this move's sums and tile counter
         if (lead) sc.ts[0] = globaltimer();
         power_tiles<T, kHasW>(A, mt_cur, mt_nxt, sm[threadIdx.x >> 5], &nsl->chunk_next, acc);
-        power_publish<T>(acc, nsl, tscratch);
         if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 1 : nullptr))
+            break;
+        power_split_rows<T>(A, mt_nxt, acc);
+        power_publish<T>(acc, nsl, tscratch);
+        if (!grid_barrier(&sw->bar, sc.target, ctl.barrier_limit_ns, blockIdx.x == 0 ? sc.ts + 3 : nullptr))
             break;
         if (lead) {
             MoveRecord* rec = A.log + ((sc.moves - 1) % kLogCap);
-            // pull work and the wait at its barrier (slots 4 and 5)
-            rec->phase_us[4] = (float)(sc.ts[1] - sc.ts[0]) * 1e-3f;
-            rec->phase_us[5] = (float)(sc.ts[2] - sc.ts[1]) * 1e-3f;
+            // the move's work (pull, then the split rows) and the waits at its
+            // two barriers (slots 4 and 5)
+            rec->phase_us[4] = (float)((sc.ts[1] - sc.ts[0]) + (sc.ts[3] - sc.ts[2])) * 1e-3f;
+            rec->phase_us[5] = (float)((sc.ts[2] - sc.ts[1]) + (sc.ts[4] - sc.ts[3])) * 1e-3f;
         }
         {
             T* t = mt_cur;

@@ -178,7 +178,6 @@ struct SweepArgs {
     T* mt;
     T* mt2;      // power sweep: the moved cash of every other move
     T* facc;     // power sweep: sums of rows split across tiles (zero at rest)
-    unsigned int* pcnt;  // power sweep: pieces of each split row arrived (zero at rest)
     long long* f_eoff;
     long long* f_base;
     T* f_m;

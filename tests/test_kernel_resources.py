@@ -1,7 +1,9 @@
 """Resource budget of the persistent sweeps, from the compiler's own report
-(nvcc -Xptxas -v, no GPU): four 256-thread blocks must fit on an SM, so
-k_sweep and k_power (the all-green sweep) may use at most 64 registers a
-thread and 48 KB of static shared memory a block, and the FP32 (MIXED)
+(nvcc -Xptxas -v, no GPU): four 256-thread blocks of k_sweep must fit on an
+SM, so it may use at most 64 registers a thread; k_power (the all-green
+sweep) runs three blocks an SM (the registers that hold the next warp
+tile's bounds and sources), so it may use at most 85. Both keep their
+shared memory static, within 48 KB a block, and the FP32 (MIXED) unit-weight
 instantiations, those of the timed path, must not spill."""
 import os
 import re
@@ -67,12 +69,12 @@ def test_mixed_sweep_does_not_spill(ptxas_report):
         assert spill == 0, (name, spill)
 
 
-def test_power_sweep_fits_four_blocks_per_sm(ptxas_report):
+def test_power_sweep_fits_three_blocks_per_sm(ptxas_report):
     ent = _entries(ptxas_report, "_ZN4rlgl7k_power")
     assert len(ent) == 4
     for name, regs, spill, smem in ent:
-        assert regs is not None and regs <= 64, (name, regs)
-        assert smem is not None and smem <= 48 * 1024, (name, smem)
+        assert regs is not None and regs <= 85, (name, regs)
+        assert smem is not None and 3 * smem <= 227 * 1024 and smem <= 48 * 1024, (name, smem)
     for name, regs, spill, smem in ent:
         # the unit-weight FP32 instantiation (the timed all-green path) does
         # not spill; the weighted one may spill a few words
