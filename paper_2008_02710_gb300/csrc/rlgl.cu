@@ -296,6 +296,28 @@ struct Launch {
         if (!(L).capture) TRY(prof_end((L).ctx, &ev_));       \
     } while (0)
 
+static int grid_for(long long work, int per_block, int cap);
+
+// The FP64 residual pull (rlgl_power.cuh, warp tiles of the context's cash
+// type) into y, guarded on the device like the rest of the re-derivation.
+template <bool kHasW, int kIpt>
+static void launch_rederive_pull_t(rlgl_ctx* ctx) {
+    const int grid = grid_for(ctx->nwtiles, kWarpsPerBlock, ctx->sms * kPowerMinBlocks);
+    k_rederive_pull<kHasW, kIpt><<<grid, kThreads, 0, ctx->stream>>>(
+        ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->wtile_r, ctx->wtile_e, ctx->nwtiles, ctx->st);
+}
+
+static void launch_rederive_pull(rlgl_ctx* ctx) {
+    constexpr int kF = power_ipt(4), kD = power_ipt(8);
+    if (ctx->prec == RLGL_MIXED) {
+        if (ctx->has_w) launch_rederive_pull_t<true, kF>(ctx);
+        else launch_rederive_pull_t<false, kF>(ctx);
+    } else {
+        if (ctx->has_w) launch_rederive_pull_t<true, kD>(ctx);
+        else launch_rederive_pull_t<false, kD>(ctx);
+    }
+}
+
 template <typename T>
 static rlgl_status enqueue_refresh(Launch L) {
     rlgl_ctx* ctx = L.ctx;
@@ -303,16 +325,7 @@ static rlgl_status enqueue_refresh(Launch L) {
     LAUNCH(L, KC_REFRESH,
            (k_refresh_src<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, ctx->s, n,
                                                                           ctx->hsrc, ctx->st)));
-    if (ctx->has_w)
-        LAUNCH(L, KC_REFRESH,
-               (k_pull<double, double, true, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-                   ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e,
-                   ctx->ntiles, ctx->st)));
-    else
-        LAUNCH(L, KC_REFRESH,
-               (k_pull<double, double, false, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-                   ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e,
-                   ctx->ntiles, ctx->st)));
+    LAUNCH(L, KC_REFRESH, launch_rederive_pull(ctx));
     LAUNCH(L, KC_REFRESH,
            (k_refresh_apply<T><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
                (T*)ctx->c, ctx->H, ctx->y, ctx->c0, n, ctx->st, ctx->part)));
@@ -1144,12 +1157,7 @@ rlgl_status rlgl_create_from_state(int64_t n, int64_t nnz, const int64_t* row_pt
     // y = H P by the residual pull (forced, measuring), then C_0 and C.
     k_set_refresh_flags<<<1, 1, 0, ctx->stream>>>(ctx->st, 1, 0);
     k_refresh_src<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, ctx->s, (int)n, ctx->hsrc, ctx->st);
-    if (ctx->has_w)
-        k_pull<double, double, true, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-            ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles, ctx->st);
-    else
-        k_pull<double, double, false, 1><<<ctx->grid_pull, kThreads, 0, ctx->stream>>>(
-            ctx->y, ctx->hsrc, ctx->t_ptr, ctx->t_src, ctx->t_w, ctx->tile_r, ctx->tile_e, ctx->ntiles, ctx->st);
+    launch_rederive_pull(ctx);
     if (ctx->prec == RLGL_MIXED)
         k_record_c0<float><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->c0, ctx->H, ctx->y, (float*)ctx->c, (int)n, ctx->st);
     else

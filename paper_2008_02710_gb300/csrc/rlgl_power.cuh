@@ -289,6 +289,124 @@ __device__ __forceinline__ void power_split_rows(const SweepArgs<T>& A, T* __res
     }
 }
 
+// The FP64 residual pull of a re-derivation (Eq. recursion_H_res), y_j +=
+// sum over the in-links e of row j of hsrc[t_src[e]] (* t_w[e]), over the
+// same warp tiles as the all-green sweep (kIpt items a lane: the tiles'
+// size for the context's cash type) and with the same load order: the next
+// tile's bounds and sources are in flight while a warp sums the current
+// one. A row's sum goes into y with one reduction where it ends in the tile
+// and began in it; a row that crosses a lane or tile boundary adds a piece
+// per tile (lanes joined by a segmented scan), so y (zero at rest) holds
+// every row's sum once the kernel has ended. Same guard as the block-tile
+// pull of kind 1.
+template <bool kHasW, int kIpt>
+struct RederiveWarp {
+    double val[32 * kIpt];
+    int end[32 * kIpt + 1];
+};
+
+template <bool kHasW, int kIpt>
+__global__ void __launch_bounds__(kThreads, kPowerMinBlocks)
+    k_rederive_pull(double* __restrict__ y, const double* __restrict__ hsrc, const long long* __restrict__ t_ptr,
+                    const int* __restrict__ t_src, const float* __restrict__ t_w,
+                    const long long* __restrict__ wtile_r, const long long* __restrict__ wtile_e, long long ntiles,
+                    const DevState* st) {
+    if (!(st->force_refresh || (st->want_refresh && !st->done))) return;
+    __shared__ RederiveWarp<kHasW, kIpt> sm[kWarpsPerBlock];
+    RederiveWarp<kHasW, kIpt>& ws = sm[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kWarpsPerBlock;
+    long long b = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    TileB t{0, 0, 0, 0};
+    int sidx[kIpt];
+    if (b < ntiles) t = tile_bounds(wtile_r, wtile_e, b);
+#pragma unroll
+    for (int q = 0; q < kIpt; ++q) {
+        const int k = lane + q * 32;
+        sidx[q] = (b < ntiles && k < t.ne) ? __ldg(t_src + t.e0 + k) : -1;
+    }
+    while (b < ntiles) {
+        const long long bn = b + nw;
+        TileB tn{0, 0, 0, 0};
+        int start0;
+        {
+            double v[kIpt];
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) v[q] = (sidx[q] >= 0) ? __ldcg(hsrc + sidx[q]) : 0.0;
+            // the next tile's bounds and sources, in flight over this tile
+            if (bn < ntiles) tn = tile_bounds(wtile_r, wtile_e, bn);
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) {
+                const int k = lane + q * 32;
+                sidx[q] = (bn < ntiles && k < tn.ne) ? __ldg(t_src + tn.e0 + k) : -1;
+            }
+            int re[kIpt];
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) {
+                const int k = lane + q * 32;
+                re[q] = (k < t.nr) ? (int)(__ldg(t_ptr + t.r0 + 1 + k) - t.e0) : 0;
+            }
+            start0 = (int)(__ldg(t_ptr + t.r0) - t.e0);
+#pragma unroll
+            for (int q = 0; q < kIpt; ++q) {
+                const int k = lane + q * 32;
+                if (k < t.ne) ws.val[k] = kHasW ? v[q] * (double)__ldg(t_w + t.e0 + k) : v[q];
+                if (k < t.nr) ws.end[k] = re[q];
+            }
+        }
+        if (lane == 0) ws.end[t.nr] = 0x7fffffff;
+        __syncwarp();
+        const int total = t.nr + t.ne;
+        int d = lane * kIpt;
+        long long rowA = -1, rowB = -1;
+        double accA = 0.0, accB = 0.0;
+        if (d < total) {
+            const int dend = min(d + kIpt, total);
+            int lo = max(0, d - t.ne), hi = min(d, t.nr);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ws.end[mid] >= d - mid) hi = mid; else lo = mid + 1;
+            }
+            int i = lo, j = d - lo;
+            const int row_start = (i == 0) ? start0 : ws.end[i - 1];
+            bool whole = (j == row_start);  // no in-link of row i before this lane
+            double sum = 0.0;
+            int cnt = 0;
+            for (; d < dend; ++d) {
+                if (j < ws.end[i]) {
+                    sum += ws.val[j];
+                    ++j;
+                    ++cnt;
+                } else {
+                    if (!whole) {
+                        rowA = t.r0 + i;
+                        accA = sum;
+                    } else if (cnt > 0) {
+                        red_add(y + (t.r0 + i), sum);
+                    }
+                    sum = 0.0;
+                    cnt = 0;
+                    ++i;
+                    whole = true;
+                }
+            }
+            if (cnt > 0 || !whole) {
+                rowB = t.r0 + i;
+                accB = sum;
+            }
+        }
+        const double run = warp_segscan<double>(rowB, accB);
+        const long long pkey = __shfl_up_sync(0xffffffffu, rowB, 1);
+        const double pval = __shfl_up_sync(0xffffffffu, run, 1);
+        if (rowA >= 0) red_add(y + rowA, accA + ((lane > 0 && pkey == rowA) ? pval : 0.0));
+        const int last = (total - 1) / kIpt;
+        if (lane == last && rowB >= 0) red_add(y + rowB, run);
+        __syncwarp();  // the warp's shared memory is rewritten next
+        b = bn;
+        t = tn;
+    }
+}
+
 // Block sums of the per-thread move sums into the slot (thread 0; FP64).
 template <typename T>
 __device__ __forceinline__ void power_publish(PowAcc<T>& acc, SweepSlot* sl, T* scratch) {
