@@ -817,7 +817,9 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
         TRY(upload(ctx, ctx->H, m0, (size_t)n * sizeof(double), sp));
         CK(ctx, cudaMemsetAsync(ctx->c, 0, (size_t)n * cash_size(ctx), ctx->stream));
         TRY(forced_refresh(ctx, true));
+        k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
     } else {
+        // (also sums H into the state, as k_hist_sums does)
         const int* chain_of = ctx->nchains > 1 ? ctx->chain_of : nullptr;
         const long long* node_ptr = ctx->nchains > 1 ? ctx->node_ptr : nullptr;
         if (ctx->prec == RLGL_MIXED)
@@ -826,9 +828,7 @@ static rlgl_status set_step0(rlgl_ctx* ctx, const double* m0, rlgl_memspace sp) 
         else
             k_step0_uniform<double><<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(
                 (double*)ctx->c, ctx->H, ctx->colsum, (int)n, chain_of, node_ptr, ctx->st, ctx->part);
-        CKL(ctx);
     }
-    k_hist_sums<<<ctx->grid_nodes, kThreads, 0, ctx->stream>>>(ctx->H, (int)n, ctx->st, ctx->part, 1);
     CKL(ctx);
     if (ctx->nchains > 1) {
         const BatchView bv{ctx->chain_of, ctx->cs, ctx->nchains};

@@ -1550,7 +1550,8 @@ __global__ void __launch_bounds__(kThreads) k_hist_sums(const double* __restrict
 // Step 0 from the uniform M_0 (Eq. init): H = M_0 = 1/N (1/N_k within chain
 // k of a batch) and C_1 = M_0 (P - I), i.e. C_j = (colsum_j - 1) / N, in FP64
 // and then rounded to the cash type; ||C_1||_1 of the stored cash goes to
-// l1_refresh (the cash is exact: a fresh state).
+// l1_refresh (the cash is exact: a fresh state), and sum H and sum |H| to
+// the state, so that no separate pass over H follows.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step0_uniform(T* __restrict__ c, double* __restrict__ H,
                                                             const double* __restrict__ colsum, int n,
@@ -1558,7 +1559,7 @@ __global__ void __launch_bounds__(kThreads) k_step0_uniform(T* __restrict__ c, d
                                                             const long long* __restrict__ node_ptr,
                                                             DevState* st, double* part) {
     __shared__ double scratch[32];
-    double a = 0.0;
+    double a = 0.0, hs = 0.0, ha = 0.0;
     const double inv_n = 1.0 / (double)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double inv = inv_n;
@@ -1570,13 +1571,27 @@ __global__ void __launch_bounds__(kThreads) k_step0_uniform(T* __restrict__ c, d
         const T v = (T)(colsum[i] * inv - inv);
         c[i] = v;
         a += fabs((double)v);
+        hs += inv;
+        ha += fabs(inv);
     }
     a = block_sum(a, scratch);
-    if (threadIdx.x == 0) part[blockIdx.x] = a;
-    if (!last_block(&st->ticket)) return;
-    double tot[1];
-    reduce_partials<1>(part, gridDim.x, tot);
+    hs = block_sum(hs, scratch);
+    ha = block_sum(ha, scratch);
     if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = a;
+        part[3 * blockIdx.x + 1] = hs;
+        part[3 * blockIdx.x + 2] = ha;
+    }
+    if (!last_block(&st->ticket)) return;
+    double tot[3];
+    reduce_partials<3>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+        // sum H and sum |H| as k_hist_sums would find them (the same grid,
+        // loop and reduction order per sum)
+        st->hsum = tot[1];
+        st->habs = tot[2];
+        part[2 * kMaxGrid] = tot[1];
+        part[2 * kMaxGrid + 1] = tot[2];
         st->l1_refresh = tot[0];
         st->resid_l1 = 0.0;
         st->fresh = 1;
