@@ -63,7 +63,7 @@ struct rlgl_ctx {
     long long* tile_r = nullptr;
     long long* tile_e = nullptr;
     long long ntiles = 0;
-    long long* wtile_r = nullptr;  // the same split at warp tiles (the power sweep)
+    long long* wtile_r = nullptr;  // the same split at warp tiles (power sweep, FP64 residual pull)
     long long* wtile_e = nullptr;
     long long nwtiles = 0;
     // state and scratch
