@@ -278,7 +278,7 @@ def oracle_mt_time_to_err(csr, ref, nthreads):
 
 def move_alg_bytes(sched, log, n, nnz, cash, weighted, sweep=False):
     """Algorithmic bytes per kernel class of the logged moves (the byte model
-    of GpuRun.alg_bytes) for a chain of n nodes and nnz links, cash of
+    of GpuBench.alg_bytes) for a chain of n nodes and nnz links, cash of
     `cash` bytes."""
     wb = 4 if weighted else 0
     alg = {k: 0.0 for k in KERNEL_CLASSES}
@@ -299,7 +299,7 @@ def move_alg_bytes(sched, log, n, nnz, cash, weighted, sweep=False):
     return alg
 
 
-class GpuRun:
+class GpuBench:
     def __init__(self, csr, wl, device):
         import torch
         from paper_2008_02710_gb300.rlgl import Chain
@@ -699,7 +699,7 @@ def beyond_l2_record(args, device, peak, peak_src):
     gen_s = time.time() - t0
     ref, ref_info = oracle_reference(csr, undirected=wl.get("undirected", False))
     ref_dev = torch.from_numpy(ref).to(device)
-    g = GpuRun(csr, wl, device)
+    g = GpuBench(csr, wl, device)
     out = {"workload": name, "desc": wl["desc"], "n": csr.n, "nnz": csr.nnz, "gen_s": gen_s,
            "reference": ref_info, "timed": "3 solves after 1 warm-up, L2 flushed before each"}
     try:
@@ -739,7 +739,7 @@ def seeds_record(args, device, head, scale, r, lag, first):
         csr, wl = make_workload(args.workload, seed=seed, precision=args.precision)
         ref, _ = oracle_reference(csr, undirected=wl.get("undirected", False))
         ref_dev = torch.from_numpy(ref).to(device)
-        g = GpuRun(csr, wl, device)
+        g = GpuBench(csr, wl, device)
         rec = {"seed": seed}
         try:
             for key, sched, sc, rr, lg in (("", head, scale, r, lag), ("all_green_", "all_green", 1.0, 1, 0)):
@@ -777,7 +777,7 @@ def run_gpu(args):
     # oracle leg: reference stationary law (host cores)
     ref, ref_info = oracle_reference(csr, undirected=wl.get("undirected", False))
     ref_dev = torch.from_numpy(ref).to(device)
-    g = GpuRun(csr, wl, device)
+    g = GpuBench(csr, wl, device)
     # schedule -> (library schedule, theta argument, theta_scale, move cap)
     plan = {
         "link_threshold": ("link_threshold", 0.0, args.theta_scale, args.max_moves),

@@ -101,7 +101,7 @@ def test_sweep_bytes_skip_the_statistics_pass_of_stale_moves():
     import numpy as np
     import bench
     from paper_2008_02710_gb300 import synth
-    g = bench.GpuRun.__new__(bench.GpuRun)
+    g = bench.GpuBench.__new__(bench.GpuBench)
     g.csr = synth.CSR(4, np.array([0, 1, 2, 3, 4], np.int64), np.array([1, 2, 3, 0], np.int32), None)
     g.wl = {"precision": "mixed"}
     rec = lambda st: {"edges_pushed": 2, "green": 2, "mode": 1, "phase_us": [st, st, 1.0, 1.0, 1.0, 1.0]}
