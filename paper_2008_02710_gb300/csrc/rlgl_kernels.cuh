@@ -1444,7 +1444,8 @@ __device__ __forceinline__ void pull_tiles(TO* __restrict__ out, const TV* __res
 }
 
 // kind 0: cash pull (guarded by mode == PULL); kind 1: FP64 residual pull
-// into y (guarded by want_refresh / force_refresh).
+// into y (guarded by want_refresh / force_refresh). The library launches
+// kind 0 only: the residual pull runs over warp tiles (k_rederive_pull).
 template <typename TV, typename TO, bool kHasW, int kKind>
 __global__ void __launch_bounds__(kThreads) k_pull(
     TO* __restrict__ out, const TV* __restrict__ src, const long long* __restrict__ t_ptr,
